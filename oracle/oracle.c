@@ -1,0 +1,538 @@
+/*
+ * Plain FP64 CPU oracle of the implicit photochemical-kinetics step
+ * (Ghosh et al., XODIAC; Sec. 2.1 continuity and transport, Sec. 2.3 rate
+ * coefficients, Sec. 2.5 boundaries, Appendix A thermochemistry).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline leg of the benchmark, never by the product path.  Straight loops in
+ * the order the paper states the method, no blocking, no fusion.
+ *
+ * Readings where the paper is silent or garbled (each one also in the design
+ * notes):
+ *  - Eulerian backward-Euler discretisation of Eq. 1 with the flux of Eq. 2 in
+ *    conservative form on a hydrostatic grid; interface values are arithmetic
+ *    means (the "k +- 1/2" convention stated with Eq. 3); the eddy term is
+ *    written in mixing-ratio form, which is what the n_gas ratios of Eq. 3 are.
+ *  - molecular diffusion D_y = b_y T^0.75 / n_gas (binary-mixture form; the
+ *    coefficients are inputs).
+ *  - K_c from the Gibbs energy of reaction in concentration units:
+ *    ln K_c = -sum nu G/RT + dnu ln(p0 / (k_B T)), p0 = 1 bar (Sec. 2.3.4).
+ *  - three-body fall-off: Lindemann (Sec. 2.3.2) times the Troe broadening
+ *    factor when a Troe set is given; [M] = n_gas.
+ *  - photolysis: direct beam only, optical depth to the layer midpoint,
+ *    rates lagged (evaluated at the start of a step, not differentiated);
+ *    photolysis is irreversible.
+ *  - zero-flux top and bottom boundaries (Sec. 2.5).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_KB 1.380649e-16        /* erg / K */
+#define ORA_AMU 1.66053906660e-24  /* g */
+#define ORA_P0 1.0e6               /* 1 bar in dyn / cm^2 */
+
+/* ------------------------------------------------------------------ grid */
+
+void ora_grid(const ora_problem *p, double *ngas, double *z, double *dz, double *dzi)
+{
+    int L = p->L;
+    for (int k = 0; k < L; ++k)
+        ngas[k] = p->P_bar[k] * 1.0e6 / (ORA_KB * p->T[k]);
+    /* hydrostatic balance: dz = H ln(P_k / P_{k+1}), H = k_B T / (mbar g) at the interface */
+    z[0] = 0.0;
+    for (int k = 0; k + 1 < L; ++k) {
+        double Th = 0.5 * (p->T[k] + p->T[k + 1]);
+        double H = ORA_KB * Th / (p->mbar * ORA_AMU * p->g);
+        z[k + 1] = z[k] + H * log(p->P_bar[k] / p->P_bar[k + 1]);
+    }
+    for (int k = 0; k + 1 < L; ++k)
+        dzi[k] = z[k + 1] - z[k];
+    if (L == 1) {
+        dz[0] = 1.0;
+        return;
+    }
+    dz[0] = z[1] - z[0];
+    dz[L - 1] = z[L - 1] - z[L - 2];
+    for (int k = 1; k + 1 < L; ++k)
+        dz[k] = 0.5 * (z[k + 1] - z[k - 1]);
+}
+
+/* ------------------------------------------------------------ thermo */
+
+static const double *nasa_set(const double *nasa15, double T)
+{
+    /* low set below T_mid, high set at and above it */
+    return (T < nasa15[0]) ? nasa15 + 1 : nasa15 + 8;
+}
+
+double ora_gibbs_rt(const double *nasa15, double T)
+{
+    const double *a = nasa_set(nasa15, T);
+    return a[0] * (1.0 - log(T)) - a[1] * T / 2.0 - a[2] * T * T / 6.0
+         - a[3] * T * T * T / 12.0 - a[4] * T * T * T * T / 20.0 + a[5] / T - a[6];
+}
+
+double ora_cp_r(const double *nasa15, double T)
+{
+    const double *a = nasa_set(nasa15, T);
+    return a[0] + a[1] * T + a[2] * T * T + a[3] * T * T * T + a[4] * T * T * T * T;
+}
+
+static double ln_kc(const ora_problem *p, int r, double T, const double *grt)
+{
+    double dG = 0.0;
+    int dnu = 0;
+    for (int s = 0; s < 3; ++s) {
+        int i = p->reac[3 * r + s];
+        if (i >= 0) { dG -= grt[i]; dnu -= 1; }
+        int j = p->prod[3 * r + s];
+        if (j >= 0) { dG += grt[j]; dnu += 1; }
+    }
+    return -dG + dnu * log(ORA_P0 / (ORA_KB * T));
+}
+
+void ora_thermo(const ora_problem *p, double *grt, double *lnkc)
+{
+    for (int k = 0; k < p->L; ++k) {
+        double T = p->T[k];
+        for (int y = 0; y < p->S; ++y)
+            grt[(size_t)k * p->S + y] = ora_gibbs_rt(p->nasa + 15 * y, T);
+        for (int r = 0; r < p->R; ++r)
+            lnkc[(size_t)k * p->R + r] = (p->rtype[r] == 2) ? 0.0
+                                       : ln_kc(p, r, T, grt + (size_t)k * p->S);
+    }
+}
+
+/* -------------------------------------------------------------- rates */
+
+static double arrhenius(double alpha, double beta, double gamma, double T, int form)
+{
+    double Tb = (form == 0) ? T / 300.0 : T;
+    return alpha * pow(Tb, beta) * exp(-gamma / T);
+}
+
+static double troe_factor(const double *tr, double T, double Pr)
+{
+    if (tr[0] == 0.0 || Pr <= 0.0)
+        return 1.0;
+    double Fc = (1.0 - tr[0]) * exp(-T / tr[1]) + tr[0] * exp(-T / tr[2]);
+    if (tr[3] != 0.0)
+        Fc += exp(-tr[3] / T);
+    double lFc = log10(Fc);
+    double c = -0.4 - 0.67 * lFc;
+    double N = 0.75 - 1.27 * lFc;
+    double x = log10(Pr) + c;
+    double q = x / (N - 0.14 * x);
+    return pow(10.0, lFc / (1.0 + q * q));
+}
+
+void ora_rate_coefficients(const ora_problem *p, double *kf, double *kr)
+{
+    int L = p->L, R = p->R, S = p->S;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    double *grt = malloc(sizeof(double) * S);
+    for (int k = 0; k < L; ++k) {
+        double T = p->T[k];
+        for (int y = 0; y < S; ++y)
+            grt[y] = ora_gibbs_rt(p->nasa + 15 * y, T);
+        for (int r = 0; r < R; ++r) {
+            const double *a = p->arr + 9 * r;
+            double f = 0.0, b = 0.0;
+            if (p->rtype[r] == 0) {
+                f = arrhenius(a[0], a[1], a[2], T, p->form[r]);
+            } else if (p->rtype[r] == 1) {
+                double k0 = arrhenius(a[3], a[4], a[5], T, p->form[r]);
+                double ki = arrhenius(a[6], a[7], a[8], T, p->form[r]);
+                double M = ngas[k];
+                double Pr = k0 * M / ki;
+                f = k0 * M / (1.0 + k0 * M / ki) * troe_factor(p->troe + 4 * r, T, Pr);
+            }
+            if (p->rtype[r] != 2)
+                b = f / exp(ln_kc(p, r, T, grt));
+            kf[(size_t)k * R + r] = f;
+            kr[(size_t)k * R + r] = b;
+        }
+    }
+    free(grt);
+    free(ngas);
+}
+
+void ora_photolysis(const ora_problem *p, const double *n, double *kph)
+{
+    int L = p->L, S = p->S, W = p->W, R = p->R, Rph = p->Rph;
+    if (Rph == 0)
+        return;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    double *alpha = malloc(sizeof(double) * L);
+    double *J = malloc(sizeof(double) * L * W);
+    for (int w = 0; w < W; ++w) {
+        /* absorption coefficient per layer: sum_i sigma_i n_i */
+        for (int k = 0; k < L; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < S; ++i)
+                s += p->sigma_abs[(size_t)i * W + w] * n[(size_t)k * S + i];
+            alpha[k] = s;
+        }
+        /* optical depth from the top down to the layer midpoint */
+        double above = 0.0;
+        for (int k = L - 1; k >= 0; --k) {
+            double tau = above + 0.5 * alpha[k] * dz[k];
+            J[(size_t)k * W + w] = p->J0[w] * exp(-tau / p->mu);
+            above += alpha[k] * dz[k];
+        }
+    }
+    for (int k = 0; k < L; ++k)
+        for (int q = 0; q < Rph; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < W; ++w)
+                s += J[(size_t)k * W + w] * p->sigma[(size_t)q * W + w] * p->dlam[w];
+            kph[(size_t)k * Rph + q] = p->tf * s;
+        }
+    (void)R;
+    free(J);
+    free(alpha);
+    free(ngas);
+}
+
+/* ---------------------------------------------------------- transport */
+
+void ora_transport(const ora_problem *p, double *u, double *v)
+{
+    int L = p->L, S = p->S;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    for (int k = 0; k + 1 < L; ++k) {
+        double Th = 0.5 * (p->T[k] + p->T[k + 1]);
+        double nh = 0.5 * (ngas[k] + ngas[k + 1]);
+        double Kh = 0.5 * (p->Kzz[k] + p->Kzz[k + 1]);
+        double h = dzi[k];
+        double dTdz = (p->T[k + 1] - p->T[k]) / h;
+        for (int y = 0; y < S; ++y) {
+            double D = p->dcoef[y] * pow(Th, 0.75) / nh;
+            double Hy = ORA_KB * Th / (p->mass[y] * ORA_AMU * p->g);
+            double a = 1.0 / Hy + (1.0 + p->alpha_T) * dTdz / Th;
+            /* eddy: -K n_gas d(n/n_gas)/dz; molecular: -D (dn/dz + n a) */
+            u[(size_t)k * S + y] = Kh * nh / (h * ngas[k]) + D * (1.0 / h - 0.5 * a);
+            v[(size_t)k * S + y] = Kh * nh / (h * ngas[k + 1]) + D * (1.0 / h + 0.5 * a);
+        }
+    }
+    free(ngas);
+}
+
+/* ----------------------------------------------------------- residual */
+
+static void layer_rates(const ora_problem *p, int k, const double *kf, const double *kr,
+                        const double *kph, double *kf_k, double *kr_k)
+{
+    for (int r = 0; r < p->R; ++r) {
+        if (p->rtype[r] == 2) {
+            kf_k[r] = kph[(size_t)k * p->Rph + p->prow[r]];
+            kr_k[r] = 0.0;
+        } else {
+            kf_k[r] = kf[(size_t)k * p->R + r];
+            kr_k[r] = kr[(size_t)k * p->R + r];
+        }
+    }
+}
+
+void ora_residual(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                  const double *n, double *F)
+{
+    int L = p->L, S = p->S, R = p->R;
+    double *kf_k = malloc(sizeof(double) * R * 2), *kr_k = kf_k + R;
+    double *u = malloc(sizeof(double) * (L > 1 ? (L - 1) : 1) * S * 2);
+    double *v = u + (size_t)(L > 1 ? (L - 1) : 1) * S;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    ora_transport(p, u, v);
+    for (int k = 0; k < L; ++k) {
+        const double *nk = n + (size_t)k * S;
+        double *Fk = F + (size_t)k * S;
+        for (int y = 0; y < S; ++y)
+            Fk[y] = 0.0;
+        layer_rates(p, k, kf, kr, kph, kf_k, kr_k);
+        /* chemistry: production minus loss, mass action */
+        for (int r = 0; r < R; ++r) {
+            double wf = kf_k[r], wb = kr_k[r];
+            for (int s = 0; s < 3; ++s) {
+                if (p->reac[3 * r + s] >= 0) wf *= nk[p->reac[3 * r + s]];
+                if (p->prod[3 * r + s] >= 0) wb *= nk[p->prod[3 * r + s]];
+            }
+            double w = wf - wb;
+            for (int s = 0; s < 3; ++s) {
+                if (p->reac[3 * r + s] >= 0) Fk[p->reac[3 * r + s]] -= w;
+                if (p->prod[3 * r + s] >= 0) Fk[p->prod[3 * r + s]] += w;
+            }
+        }
+        /* transport: -(phi_{k+1/2} - phi_{k-1/2}) / dz_k, zero flux at both ends */
+        for (int y = 0; y < S; ++y) {
+            double up = 0.0, dn = 0.0;
+            if (k + 1 < L)
+                up = u[(size_t)k * S + y] * nk[y] - v[(size_t)k * S + y] * n[(size_t)(k + 1) * S + y];
+            if (k > 0)
+                dn = u[(size_t)(k - 1) * S + y] * n[(size_t)(k - 1) * S + y] - v[(size_t)(k - 1) * S + y] * nk[y];
+            Fk[y] += -(up - dn) / dz[k];
+        }
+    }
+    free(ngas);
+    free(u);
+    free(kf_k);
+}
+
+/* ----------------------------------------------------------- jacobian */
+
+void ora_jacobian(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                  const double *n, double dt, double *A, double *lo, double *up)
+{
+    int L = p->L, S = p->S, R = p->R;
+    double *kf_k = malloc(sizeof(double) * R * 2), *kr_k = kf_k + R;
+    double *u = malloc(sizeof(double) * (L > 1 ? (L - 1) : 1) * S * 2);
+    double *v = u + (size_t)(L > 1 ? (L - 1) : 1) * S;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    ora_transport(p, u, v);
+    for (int k = 0; k < L; ++k) {
+        const double *nk = n + (size_t)k * S;
+        double *Ak = A + (size_t)k * S * S;
+        memset(Ak, 0, sizeof(double) * S * S);
+        layer_rates(p, k, kf, kr, kph, kf_k, kr_k);
+        /* dF_i/dn_j = sum_r nu_ir dw_r/dn_j; A = I/dt - dF/dn */
+        for (int r = 0; r < R; ++r) {
+            for (int side = 0; side < 2; ++side) {
+                const int *sp = (side == 0) ? p->reac + 3 * r : p->prod + 3 * r;
+                double kk = (side == 0) ? kf_k[r] : -kr_k[r];
+                for (int s = 0; s < 3; ++s) {
+                    int j = sp[s];
+                    if (j < 0)
+                        continue;
+                    double d = kk;                  /* derivative of k prod n w.r.t. the s-th factor */
+                    for (int t = 0; t < 3; ++t)
+                        if (t != s && sp[t] >= 0)
+                            d *= nk[sp[t]];
+                    for (int q = 0; q < 3; ++q) {
+                        if (p->reac[3 * r + q] >= 0) Ak[(size_t)p->reac[3 * r + q] * S + j] += d;  /* -(-d) */
+                        if (p->prod[3 * r + q] >= 0) Ak[(size_t)p->prod[3 * r + q] * S + j] -= d;  /* -(+d) */
+                    }
+                }
+            }
+        }
+        for (int y = 0; y < S; ++y) {
+            double diag = 1.0 / dt;
+            if (k + 1 < L) diag += u[(size_t)k * S + y] / dz[k];
+            if (k > 0) diag += v[(size_t)(k - 1) * S + y] / dz[k];
+            Ak[(size_t)y * S + y] += diag;
+            lo[(size_t)k * S + y] = (k > 0) ? -u[(size_t)(k - 1) * S + y] / dz[k] : 0.0;
+            up[(size_t)k * S + y] = (k + 1 < L) ? -v[(size_t)k * S + y] / dz[k] : 0.0;
+        }
+    }
+    free(ngas);
+    free(u);
+    free(kf_k);
+}
+
+/* ------------------------------------------------------ block solve */
+
+/* Gaussian elimination with partial pivoting: a (S x S) becomes L\U, piv the row order. */
+static int lu_factor(int S, double *a, int *piv)
+{
+    for (int i = 0; i < S; ++i)
+        piv[i] = i;
+    for (int c = 0; c < S; ++c) {
+        int best = c;
+        double bv = fabs(a[(size_t)c * S + c]);
+        for (int i = c + 1; i < S; ++i) {
+            double v = fabs(a[(size_t)i * S + c]);
+            if (v > bv) { bv = v; best = i; }
+        }
+        if (bv == 0.0)
+            return -1;
+        if (best != c) {
+            for (int j = 0; j < S; ++j) {
+                double t = a[(size_t)c * S + j];
+                a[(size_t)c * S + j] = a[(size_t)best * S + j];
+                a[(size_t)best * S + j] = t;
+            }
+            int t = piv[c]; piv[c] = piv[best]; piv[best] = t;
+        }
+        double inv = 1.0 / a[(size_t)c * S + c];
+        for (int i = c + 1; i < S; ++i) {
+            double l = a[(size_t)i * S + c] * inv;
+            a[(size_t)i * S + c] = l;
+            for (int j = c + 1; j < S; ++j)
+                a[(size_t)i * S + j] -= l * a[(size_t)c * S + j];
+        }
+    }
+    return 0;
+}
+
+/* Solve (L U) X = P B for m right-hand-side columns stored row-major in B (S x m). */
+static void lu_solve(int S, const double *a, const int *piv, const double *B, double *X, int m)
+{
+    for (int i = 0; i < S; ++i)
+        memcpy(X + (size_t)i * m, B + (size_t)piv[i] * m, sizeof(double) * m);
+    for (int i = 0; i < S; ++i)
+        for (int c = 0; c < i; ++c) {
+            double l = a[(size_t)i * S + c];
+            for (int j = 0; j < m; ++j)
+                X[(size_t)i * m + j] -= l * X[(size_t)c * m + j];
+        }
+    for (int i = S - 1; i >= 0; --i) {
+        for (int c = i + 1; c < S; ++c) {
+            double uu = a[(size_t)i * S + c];
+            for (int j = 0; j < m; ++j)
+                X[(size_t)i * m + j] -= uu * X[(size_t)c * m + j];
+        }
+        double inv = 1.0 / a[(size_t)i * S + i];
+        for (int j = 0; j < m; ++j)
+            X[(size_t)i * m + j] *= inv;
+    }
+}
+
+int ora_block_solve(int L, int S, double *A, const double *lo, const double *up,
+                    const double *f, double *x)
+{
+    int *piv = malloc(sizeof(int) * (size_t)L * S);
+    double *B = malloc(sizeof(double) * (size_t)S * S);
+    double *X = malloc(sizeof(double) * (size_t)S * S);
+    double *g = malloc(sizeof(double) * (size_t)L * S);
+    double *t = malloc(sizeof(double) * S);
+    int rc = 0;
+    /* forward elimination: D'_k = A_k - diag(lo_k) D'^-1_{k-1} diag(up_{k-1}) */
+    for (int k = 0; k < L && rc == 0; ++k) {
+        double *Ak = A + (size_t)k * S * S;
+        memcpy(g + (size_t)k * S, f + (size_t)k * S, sizeof(double) * S);
+        if (k > 0) {
+            double *Ap = A + (size_t)(k - 1) * S * S;
+            memset(B, 0, sizeof(double) * S * S);
+            for (int y = 0; y < S; ++y)
+                B[(size_t)y * S + y] = up[(size_t)(k - 1) * S + y];
+            lu_solve(S, Ap, piv + (size_t)(k - 1) * S, B, X, S);
+            for (int i = 0; i < S; ++i)
+                for (int j = 0; j < S; ++j)
+                    Ak[(size_t)i * S + j] -= lo[(size_t)k * S + i] * X[(size_t)i * S + j];
+            lu_solve(S, Ap, piv + (size_t)(k - 1) * S, g + (size_t)(k - 1) * S, t, 1);
+            for (int i = 0; i < S; ++i)
+                g[(size_t)k * S + i] -= lo[(size_t)k * S + i] * t[i];
+        }
+        if (lu_factor(S, Ak, piv + (size_t)k * S) != 0)
+            rc = -1;
+    }
+    /* back substitution: x_k = D'^-1_k (g_k - diag(up_k) x_{k+1}) */
+    for (int k = L - 1; k >= 0 && rc == 0; --k) {
+        for (int i = 0; i < S; ++i)
+            t[i] = g[(size_t)k * S + i] - ((k + 1 < L) ? up[(size_t)k * S + i] * x[(size_t)(k + 1) * S + i] : 0.0);
+        lu_solve(S, A + (size_t)k * S * S, piv + (size_t)k * S, t, x + (size_t)k * S, 1);
+    }
+    free(t); free(g); free(X); free(B); free(piv);
+    return rc;
+}
+
+/* ---------------------------------------------------------- stepping */
+
+int ora_step_delta(const ora_problem *p, const double *n, double dt, double *delta)
+{
+    int L = p->L, S = p->S, R = p->R;
+    size_t LS = (size_t)L * S;
+    double *kf = malloc(sizeof(double) * (size_t)L * R * 2), *kr = kf + (size_t)L * R;
+    double *kph = malloc(sizeof(double) * (size_t)L * (p->Rph > 0 ? p->Rph : 1));
+    double *F = malloc(sizeof(double) * LS * 3), *lo = F + LS, *up = lo + LS;
+    double *A = malloc(sizeof(double) * LS * S);
+    ora_rate_coefficients(p, kf, kr);
+    ora_photolysis(p, n, kph);
+    ora_residual(p, kf, kr, kph, n, F);
+    ora_jacobian(p, kf, kr, kph, n, dt, A, lo, up);
+    int rc = ora_block_solve(L, S, A, lo, up, F, delta);
+    free(A); free(F); free(kph); free(kf);
+    return rc;
+}
+
+int ora_step(const ora_problem *p, const ora_policy *pol, double *n, double dt, ora_step_info *info)
+{
+    int L = p->L, S = p->S;
+    size_t LS = (size_t)L * S;
+    double *delta = malloc(sizeof(double) * LS);
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    int rc = ora_step_delta(p, n, dt, delta);
+    int ok = (rc == 0);
+    double maxrel = 0.0;
+    int nneg = 0;
+    for (int k = 0; k < L && ok; ++k)
+        for (int y = 0; y < S; ++y) {
+            double d = delta[(size_t)k * S + y], nv = n[(size_t)k * S + y];
+            double nn = nv + d;
+            if (!isfinite(nn)) { ok = 0; break; }
+            if (nn < -pol->neg_tol * ngas[k]) ok = 0;
+            if (nv > pol->f_floor * ngas[k]) {
+                double rel = fabs(d) / nv;
+                if (rel > maxrel) maxrel = rel;
+            }
+        }
+    if (ok && maxrel > pol->rel_reject)
+        ok = 0;
+    info->dt_used = dt;
+    info->max_rel = maxrel;
+    info->n_neg = 0;
+    if (ok) {
+        for (size_t i = 0; i < LS; ++i) {
+            double nn = n[i] + delta[i];
+            if (nn < 0.0) { nn = 0.0; ++nneg; }
+            n[i] = nn;
+        }
+        double fac = (maxrel > 0.0) ? pol->rel_target / maxrel : pol->grow_max;
+        if (fac > pol->grow_max) fac = pol->grow_max;
+        if (fac < pol->shrink_min) fac = pol->shrink_min;
+        double dn = dt * fac;
+        info->dt_next = (dn > pol->dt_max) ? pol->dt_max : dn;
+        info->accepted = 1;
+        info->n_neg = nneg;
+    } else {
+        info->dt_next = 0.5 * dt;
+        info->accepted = 0;
+    }
+    free(ngas);
+    free(delta);
+    return 0;
+}
+
+int ora_run_to_steady(const ora_problem *p, const ora_policy *pol, double *n, double dt0,
+                      int max_steps, ora_run_info *info)
+{
+    double dt = dt0, t = 0.0;
+    int steps = 0, acc = 0, rej = 0, conv = 0;
+    ora_step_info si;
+    si.max_rel = 0.0;
+    while (steps < max_steps) {
+        ora_step(p, pol, n, dt, &si);
+        ++steps;
+        if (si.accepted) {
+            ++acc;
+            t += dt;
+            if (dt >= pol->ss_dt && si.max_rel < pol->ss_tol) { conv = 1; dt = si.dt_next; break; }
+        } else {
+            ++rej;
+        }
+        dt = si.dt_next;
+        if (dt < pol->dt_min)
+            break;
+    }
+    info->converged = conv;
+    info->steps = steps;
+    info->accepted = acc;
+    info->rejected = rej;
+    info->t = t;
+    info->dt = dt;
+    info->max_rel = si.max_rel;
+    return conv ? 0 : -1;
+}

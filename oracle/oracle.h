@@ -1,0 +1,98 @@
+/*
+ * Plain FP64 CPU oracle of the implicit photochemical-kinetics step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header,
+ * table or helper with the CUDA path; both start from the same raw inputs
+ * (element vectors, reaction lists, rate parameters, NASA-7 sets, cross
+ * sections, profiles) and compute everything else on their own.
+ *
+ * Every quantity is FP64.  Layout is row-major; layer 0 is the bottom of the
+ * atmosphere.  Units: cgs, pressure input in bar, wavelength in Angstrom.
+ */
+#ifndef XK_ORACLE_H
+#define XK_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int S, E, R, L, W, Rph;
+    const int *elem;        /* S x E */
+    const double *mass;     /* S (u) */
+    const int *rtype;       /* R: 0 two-body, 1 three-body, 2 photolysis */
+    const int *reac;        /* R x 3, -1 pad */
+    const int *prod;        /* R x 3, -1 pad */
+    const double *arr;      /* R x 9 */
+    const double *troe;     /* R x 4: a, T***, T*, T**; a == 0 -> Lindemann */
+    const int *form;        /* R: 0 Kooij, 1 modified Arrhenius */
+    const double *nasa;     /* S x 15: Tmid, low a1..a7, high a1..a7 */
+    const int *prow;        /* R: sigma row of a photolysis reaction, else -1 */
+    const double *lam, *dlam, *J0;   /* W */
+    const double *sigma;    /* Rph x W */
+    const double *sigma_abs;/* S x W */
+    double mu, tf;
+    const double *P_bar, *T, *Kzz;   /* L */
+    const double *dcoef;    /* S */
+    double g, mbar, alpha_T;
+} ora_problem;
+
+typedef struct {
+    double dt_max;      /* largest step (s) */
+    double rel_reject;  /* reject when max relative change exceeds this */
+    double rel_target;  /* step-size controller target relative change */
+    double grow_max, shrink_min;
+    double neg_tol;     /* reject when n < -neg_tol * n_gas */
+    double f_floor;     /* relative change measured over species with f > f_floor */
+    double dt_min;      /* give up below this step */
+    double ss_dt;       /* steady state needs dt >= ss_dt ... */
+    double ss_tol;      /* ... and max relative change < ss_tol */
+} ora_policy;
+
+typedef struct {
+    int accepted;       /* 1 accepted, 0 rejected */
+    double dt_used, dt_next, max_rel;
+    int n_neg;          /* entries clipped to zero on acceptance */
+} ora_step_info;
+
+typedef struct {
+    int converged, steps, accepted, rejected;
+    double t, dt, max_rel;
+} ora_run_info;
+
+/* Sec. 2.1: n_gas = P / (k_B T); hydrostatic altitudes; layer and interface widths. */
+void ora_grid(const ora_problem *p, double *ngas, double *z, double *dz, double *dzi);
+/* Appendix A: G/RT and Cp/R of one NASA-7 set at temperature T. */
+double ora_gibbs_rt(const double *nasa15, double T);
+double ora_cp_r(const double *nasa15, double T);
+/* Sec. 2.3.4: G/RT per layer and species, ln K_c per layer and reaction. */
+void ora_thermo(const ora_problem *p, double *grt, double *lnkc);
+/* Sec. 2.3.1-2.3.4: thermal k_f and k_r per layer and reaction (photolysis rows 0). */
+void ora_rate_coefficients(const ora_problem *p, double *kf, double *kr);
+/* Sec. 2.3.3: photolysis rate constants per layer and photolysis reaction. */
+void ora_photolysis(const ora_problem *p, const double *n, double *kph);
+/* Eq. 2: interface flux phi_{k+1/2} = u n_k - v n_{k+1}, per interface and species. */
+void ora_transport(const ora_problem *p, double *u, double *v);
+/* Eq. 1: F = P - L - d(phi)/dz at state n (kf/kr/kph supplied). */
+void ora_residual(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                  const double *n, double *F);
+/* Block-tridiagonal matrix I/dt - dF/dn: dense diagonal blocks A[L][S][S],
+ * diagonal couplings lo[L][S] (to layer k-1) and up[L][S] (to layer k+1). */
+void ora_jacobian(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                  const double *n, double dt, double *A, double *lo, double *up);
+/* Block Thomas with partial-pivot LU per block; A is overwritten.  Returns 0 or -1 (singular). */
+int ora_block_solve(int L, int S, double *A, const double *lo, const double *up,
+                    const double *f, double *x);
+/* One linearly implicit backward-Euler step of size dt: delta solves (I/dt - J) delta = F. */
+int ora_step_delta(const ora_problem *p, const double *n, double dt, double *delta);
+/* One controlled step: accept/reject, clip, next dt.  n is updated when accepted. */
+int ora_step(const ora_problem *p, const ora_policy *pol, double *n, double dt, ora_step_info *info);
+/* Steps from dt0 until steady state or max_steps. */
+int ora_run_to_steady(const ora_problem *p, const ora_policy *pol, double *n, double dt0,
+                      int max_steps, ora_run_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,425 @@
+"""Pins of the CPU oracle against values the paper prints, closed forms,
+invariants, special cases and library routines (no GPU needed).
+
+Each test targets one row of the method so that a dropped term, a wrong sign
+or index, or a transposed operand in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, default_policy, lib
+from paper_2512_06729_gb300 import synth
+from tests.helpers import custom_problem, full_matrix, nasa_const_cp, read_nasa_table
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+KB = 1.380649e-16
+AMU = 1.66053906660e-24
+R_GAS = 8.314462618          # J / mol / K
+
+
+def gibbs_rt(row, T):
+    a = np.ascontiguousarray(row, np.float64)
+    return lib().ora_gibbs_rt(a.ctypes.data_as(lib().ora_gibbs_rt.argtypes[0]), float(T))
+
+
+def cp_r(row, T):
+    a = np.ascontiguousarray(row, np.float64)
+    return lib().ora_cp_r(a.ctypes.data_as(lib().ora_cp_r.argtypes[0]), float(T))
+
+
+# ---------------------------------------------------------------- thermo (Appendix A)
+
+def test_gibbs_low_high_sets_meet_at_1000K():
+    """Appendix A table: the Burcat low and high sets of H2O and CO2 describe
+    the same G/RT and Cp/R at the 1000 K junction."""
+    tab = read_nasa_table(os.path.join(GOLD, "nasa7_table.txt"))
+    for name in ("H2O_burcat", "CO2_burcat"):
+        row = tab[name].copy()
+        high = gibbs_rt(row, 1000.0)            # T == T_mid takes the high set
+        row_low = row.copy(); row_low[0] = 1000.5
+        low = gibbs_rt(row_low, 1000.0)
+        assert abs(low - high) / abs(high) < 5e-6, (name, low, high)
+        assert abs(cp_r(row_low, 1000.0) - cp_r(row, 1000.0)) / cp_r(row, 1000.0) < 2e-3
+    # the values themselves (Appendix A formula; H2O -53.949, CO2 -75.699 at 1000 K)
+    assert gibbs_rt(tab["H2O_burcat"], 1000.0) == pytest.approx(-53.949, abs=2e-3)
+    assert gibbs_rt(tab["CO2_burcat"], 1000.0) == pytest.approx(-75.699, abs=2e-3)
+
+
+def test_gibbs_298K_matches_formation_data():
+    """At 298.15 K the Burcat low sets give G = dHf - T S (NIST-JANAF values)."""
+    tab = read_nasa_table(os.path.join(GOLD, "nasa7_table.txt"))
+    for line in open(os.path.join(GOLD, "standard_state_298K.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        name, dh, s, cp = line.split()
+        T = 298.15
+        g_ref = (float(dh) * 1e3 - T * float(s)) / (R_GAS * T)
+        assert gibbs_rt(tab[name], T) == pytest.approx(g_ref, rel=2e-4), name
+        assert cp_r(tab[name], T) == pytest.approx(float(cp) / R_GAS, rel=1e-2), name
+
+
+def test_gibbs_selects_range_by_temperature():
+    row = np.zeros(15); row[0] = 1000.0
+    row[1:8] = [3.0, 0, 0, 0, 0, 1000.0, 2.0]
+    row[8:15] = [4.0, 0, 0, 0, 0, -500.0, 1.0]
+    T = 800.0
+    assert gibbs_rt(row, T) == pytest.approx(3.0 * (1 - math.log(T)) + 1000.0 / T - 2.0, rel=1e-14)
+    T = 1200.0
+    assert gibbs_rt(row, T) == pytest.approx(4.0 * (1 - math.log(T)) - 500.0 / T - 1.0, rel=1e-14)
+
+
+# ---------------------------------------------------------------- rate laws (Sec. 2.3)
+
+def _one_layer(reactions, T, P_bar, S=4, nasa=None):
+    elem = np.eye(S, dtype=np.int32)
+    if nasa is None:
+        nasa = np.stack([nasa_const_cp(3.5, -1000.0 * i, 10.0) for i in range(S)])
+    return custom_problem(elem, np.full(S, 10.0), reactions, nasa, [P_bar], [T])
+
+
+def test_kooij_at_300K_and_form_switch():
+    al, be, ga = 3e-11, 1.7, 1234.0
+    rx = [dict(type=2 - 2, reac=[0, 1], prod=[2, 3], arr=[al, be, ga], form=0),
+          dict(type=0, reac=[0, 1], prod=[2, 3], arr=[al, be, ga], form=1)]
+    p = _one_layer(rx, 300.0, 1.0)
+    kf, _ = Oracle(p).rate_coefficients()
+    assert kf[0, 0] == pytest.approx(al * math.exp(-ga / 300.0), rel=1e-14)
+    assert kf[0, 1] / kf[0, 0] == pytest.approx(300.0 ** be, rel=1e-13)
+
+
+def test_arrhenius_slope():
+    """d ln k / d(1/T) = -gamma - beta T for k = alpha (T/300)^beta exp(-gamma/T)."""
+    al, be, ga = 1e-12, -1.3, 8000.0
+    T0, h = 1250.0, 1e-3
+    ks = []
+    for T in (T0 * (1 + h), T0 * (1 - h)):
+        p = _one_layer([dict(type=0, reac=[0, 1], prod=[2, 3], arr=[al, be, ga])], T, 1.0)
+        ks.append(Oracle(p).rate_coefficients()[0][0, 0])
+    slope = (math.log(ks[0]) - math.log(ks[1])) / (1 / (T0 * (1 + h)) - 1 / (T0 * (1 - h)))
+    assert slope == pytest.approx(-ga - be * T0, rel=1e-5)
+
+
+def _falloff(P_bar, troe, T=1000.0):
+    a = [0, 0, 0, 2e-30, -1.0, 100.0, 3e-11, 0.5, 50.0]
+    p = _one_layer([dict(type=1, reac=[0, 1], prod=[2], arr=a, troe=troe)], T, P_bar)
+    o = Oracle(p)
+    M = o.grid()[0][0]
+    k0 = 2e-30 * (T / 300) ** -1.0 * math.exp(-100.0 / T)
+    ki = 3e-11 * (T / 300) ** 0.5 * math.exp(-50.0 / T)
+    return o.rate_coefficients()[0][0, 0], k0, ki, M
+
+
+def test_lindemann_limits():
+    k, k0, ki, M = _falloff(1e-12, [0, 0, 0, 0])
+    assert k / M == pytest.approx(k0, rel=1e-6)          # low-pressure limit: k0 [M]
+    k, k0, ki, M = _falloff(1e12, [0, 0, 0, 0])
+    assert k == pytest.approx(ki, rel=1e-6)              # high-pressure limit: k_inf
+    k, k0, ki, M = _falloff(1.0, [0, 0, 0, 0])
+    assert 1 / k == pytest.approx(1 / (k0 * M) + 1 / ki, rel=1e-13)   # harmonic combination
+
+
+def test_troe_special_cases():
+    lind, _, _, _ = _falloff(0.3, [0, 0, 0, 0])
+    fc1, _, _, _ = _falloff(0.3, [1.0, 1e-30, 1e30, 0.0])
+    assert fc1 == pytest.approx(lind, rel=1e-14)         # F_cent = 1 gives Lindemann
+    # at the centre of the fall-off curve (log10 Pr = 0.4 + 0.67 log10 Fc) F = Fc
+    Fc, T = 0.45, 1000.0
+    k0 = 2e-30 * (T / 300) ** -1.0 * math.exp(-100.0 / T)
+    ki = 3e-11 * (T / 300) ** 0.5 * math.exp(-50.0 / T)
+    Pr = 10 ** (0.4 + 0.67 * math.log10(Fc))
+    M = Pr * ki / k0
+    P_bar = M * KB * T / 1e6
+    k, _, _, _ = _falloff(P_bar, [Fc, 1e-30, 1e30, 0.0])
+    lind, _, _, _ = _falloff(P_bar, [0, 0, 0, 0])
+    assert k / lind == pytest.approx(Fc, rel=1e-9)
+    # the T** term of F_cent: with T*** -> 0 and T* -> inf, F_cent = a + exp(-T**/T)
+    a, x = 0.3, 0.2
+    T2 = T * math.log(1 / x)
+    Fc = a + x
+    Pr = 10 ** (0.4 + 0.67 * math.log10(Fc))
+    P_bar = Pr * ki / k0 * KB * T / 1e6
+    k, _, _, _ = _falloff(P_bar, [a, 1e-30, 1e30, T2])
+    lind, _, _, _ = _falloff(P_bar, [0, 0, 0, 0])
+    assert k / lind == pytest.approx(Fc, rel=1e-9)
+    # far from the centre the broadening vanishes
+    k, _, _, _ = _falloff(1e-14, [Fc, 1e-30, 1e30, 0.0])
+    lind, _, _, _ = _falloff(1e-14, [0, 0, 0, 0])
+    assert abs(k / lind - 1) < 0.05
+
+
+# ------------------------------------------------- reverse rates / equilibrium (Sec. 2.3.4)
+
+def test_equilibrium_constant_in_pressure_units():
+    """A + B <-> C in one closed layer relaxes to p_C p0 / (p_A p_B) = exp(-dG/RT)."""
+    T = 1300.0
+    nasa = np.stack([nasa_const_cp(2.5, 3000.0, 5.0), nasa_const_cp(3.0, -2000.0, 8.0),
+                     nasa_const_cp(4.5, -45000.0, 2.0)])
+    elem = np.array([[1, 0], [0, 1], [1, 1]], np.int32)
+    rx = [dict(type=0, reac=[0, 1], prod=[2], arr=[1e-11, 0.0, 0.0])]
+    f0 = np.array([[0.3, 0.3, 0.4]])
+    p = custom_problem(elem, [10.0, 12.0, 22.0], rx, nasa, [0.5], [T], f0=f0)
+    o = Oracle(p)
+    n = o.initial_state()
+    n, info = o.run_to_steady(n, policy=default_policy(ss_tol=1e-12, dt_max=1e12, ss_dt=1e12), max_steps=2000)
+    assert info.converged
+    g = [gibbs_rt(nasa[i], T) for i in range(3)]
+    pr = n[0] * KB * T / 1e6                               # partial pressures in bar
+    Kp = pr[2] / (pr[0] * pr[1])
+    assert Kp == pytest.approx(math.exp(-(g[2] - g[0] - g[1])), rel=1e-8)
+
+
+def test_two_species_backward_euler_closed_form():
+    """A <-> B, one layer: n_A^m = n_eq + (n_A^0 - n_eq) / (1 + (kf + kr) dt)^m."""
+    T = 900.0
+    nasa = np.stack([nasa_const_cp(3.0, 0.0, 1.0), nasa_const_cp(3.0, -800.0, 0.5)])
+    elem = np.array([[1], [1]], np.int32)
+    rx = [dict(type=0, reac=[0], prod=[1], arr=[2.0e-3, 0.0, 0.0])]
+    p = custom_problem(elem, [10.0, 10.0], rx, nasa, [1.0], [T], f0=np.array([[0.9, 0.1]]))
+    o = Oracle(p)
+    kf, kr = o.rate_coefficients()
+    kf, kr = kf[0, 0], kr[0, 0]
+    assert kf / kr == pytest.approx(math.exp(-(gibbs_rt(nasa[1], T) - gibbs_rt(nasa[0], T))), rel=1e-12)
+    n = o.initial_state()
+    ntot = n.sum()
+    neq = ntot * kr / (kf + kr)
+    nA0 = n[0, 0]
+    dt = 37.0
+    for m in range(1, 9):
+        n = n + o.step_delta(n, dt)
+        expect = neq + (nA0 - neq) / (1 + (kf + kr) * dt) ** m
+        assert n[0, 0] == pytest.approx(expect, rel=1e-12)
+        assert n.sum() == pytest.approx(ntot, rel=1e-14)
+    # small steps follow the exact exponential relaxation
+    n = o.initial_state(); t = 0.0; dt = 1e-3 / (kf + kr)
+    for m in range(2000):
+        n = n + o.step_delta(n, dt); t += dt
+    exact = neq + (nA0 - neq) * math.exp(-(kf + kr) * t)
+    assert n[0, 0] == pytest.approx(exact, rel=2e-4)
+
+
+def test_closed_layer_reaches_gibbs_minimum():
+    """Photolysis and transport off: the steady state satisfies sum(nu ln n) =
+    ln K_c for every reaction and equals the minimum of the ideal-gas free
+    energy sum n_i (G_i/RT + ln(n_i k_B T / p0) - 1) at fixed element totals,
+    found independently by solving for the element potentials."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    T, P = 1400.0, 0.2
+    # species: A, B, AB, A2, AB2 over elements (a, b)
+    elem = np.array([[1, 0], [0, 1], [1, 1], [2, 0], [1, 2]], np.int32)
+    nasa = np.stack([nasa_const_cp(2.5, 2.0e4, 3.0), nasa_const_cp(2.5, 1.5e4, 2.0),
+                     nasa_const_cp(3.5, -1.0e4, 6.0), nasa_const_cp(3.5, -6.0e3, 5.0),
+                     nasa_const_cp(4.5, -2.2e4, 8.0)])
+    rx = [dict(type=0, reac=[0, 1], prod=[2], arr=[1e-11, 0.0, 0.0]),
+          dict(type=0, reac=[0, 0], prod=[3], arr=[2e-12, 0.5, 100.0]),
+          dict(type=0, reac=[2, 1], prod=[4], arr=[5e-12, 0.0, 0.0]),
+          dict(type=0, reac=[3, 1], prod=[2, 0], arr=[1e-12, -0.5, 500.0])]
+    f0 = np.array([[0.3, 0.4, 0.1, 0.1, 0.1]])
+    p = custom_problem(elem, [10.0, 12.0, 22.0, 20.0, 34.0], rx, nasa, [P], [T], f0=f0)
+    o = Oracle(p)
+    n0 = o.initial_state()
+    n, info = o.run_to_steady(n0, policy=default_policy(dt_max=1e6, ss_dt=1e6, ss_tol=1e-13), max_steps=4000)
+    assert info.converged
+    _, lnkc = o.thermo()
+    for r in range(p.R):
+        s = sum(math.log(n[0, i]) for i in p.prod[r] if i >= 0) - sum(math.log(n[0, i]) for i in p.reac[r] if i >= 0)
+        assert abs(s - lnkc[0, r]) < 1e-9, r
+    # element-potential form of the free-energy minimum: n_i = exp(sum_e lam_e E_ie - g_i) / c
+    g = np.array([gibbs_rt(nasa[i], T) for i in range(5)])
+    c = KB * T / 1e6
+    tot = elem.T.astype(float) @ n0[0]
+
+    def resid(lam):
+        m = np.exp(elem @ lam - g) / c
+        return elem.T @ m / tot - 1.0
+
+    lam = scipy_opt.fsolve(resid, np.log(tot * c), xtol=1e-13)
+    np.testing.assert_allclose(np.exp(elem @ lam - g) / c, n[0], rtol=1e-8)
+
+
+# ---------------------------------------------------------------- grid and transport (Sec. 2.1)
+
+def test_isothermal_hydrostatic_grid():
+    L, T = 30, 1100.0
+    P = np.geomspace(10.0, 1e-4, L)
+    p = custom_problem(np.eye(2, dtype=np.int32), [2.0, 4.0], [], np.stack([nasa_const_cp(2.5, 0, 0)] * 2),
+                       P, np.full(L, T), Kzz=np.full(L, 1e8))
+    ngas, z, dz, dzi = Oracle(p).grid()
+    H = KB * T / (p.mbar * AMU * p.g)
+    np.testing.assert_allclose(z, H * np.log(P[0] / P), rtol=1e-12, atol=1e-6)
+    np.testing.assert_allclose(ngas, P * 1e6 / (KB * T), rtol=1e-14)
+    assert dz.sum() == pytest.approx(z[-1] - z[0] + 0.5 * (dzi[0] + dzi[-1]), rel=1e-12)
+
+
+def _diffusion_column(L=40, T=1000.0, K=1e8, dc=0.0, masses=(2.0, 30.0), Ptop=1e-5):
+    P = np.geomspace(1.0, Ptop, L)
+    S = len(masses)
+    return custom_problem(np.eye(S, dtype=np.int32), list(masses), [],
+                          np.stack([nasa_const_cp(2.5, 0, 0)] * S), P, np.full(L, T),
+                          Kzz=np.full(L, K), dcoef=np.full(S, dc), f0=np.tile(np.linspace(0.2, 0.8, S), (L, 1)))
+
+
+def test_eddy_only_steady_state_is_well_mixed():
+    p = _diffusion_column()
+    o = Oracle(p)
+    ngas, _, dz, _ = o.grid()
+    rng = np.random.default_rng(0)
+    f = rng.uniform(0.1, 1.0, size=(p.L, p.S))
+    n0 = f * ngas[:, None]
+    # uniform mixing ratio is an exact zero of the eddy flux
+    F = o.residual(np.outer(ngas, [0.3, 0.7]))
+    scale = np.abs(o.residual(n0)).max()
+    assert np.abs(F).max() < 1e-12 * scale
+    # relaxation conserves the column and ends well mixed with f = sum(dz n) / sum(dz n_gas)
+    n, info = o.run_to_steady(n0, policy=default_policy(dt_max=1e12, ss_dt=1e12, ss_tol=1e-12), max_steps=3000)
+    assert info.converged
+    fbar = (dz[:, None] * n0).sum(0) / (dz * ngas).sum()
+    np.testing.assert_allclose(n / ngas[:, None], np.tile(fbar, (p.L, 1)), rtol=1e-8)
+
+
+def test_molecular_diffusion_equilibrium_profile():
+    """K = 0, isothermal: zero net flux gives n_{k+1}/n_k = (1 - a h/2)/(1 + a h/2),
+    a = 1/H_y; the continuum limit is the diffusive-equilibrium exp(-z/H_y) of Eq. 2."""
+    p = _diffusion_column(L=400, K=0.0, dc=1e17, Ptop=1e-3, masses=(2.0, 4.0))
+    o = Oracle(p)
+    ngas, z, dz, dzi = o.grid()
+    for y, m in enumerate(p.mass):
+        Hy = KB * p.T[0] / (m * AMU * p.g)
+        a = 1.0 / Hy
+        ratio = (1 - 0.5 * a * dzi) / (1 + 0.5 * a * dzi)
+        prof = np.concatenate([[1.0], np.cumprod(ratio)]) * 1e10
+        n = np.tile(prof[:, None], (1, p.S))
+        F = o.residual(n)[:, y]
+        u, v = o.transport()
+        flux_scale = np.abs(u[:, y] * n[:-1, y]).max() / dz.min()
+        assert np.abs(F).max() < 1e-10 * flux_scale
+        np.testing.assert_allclose(prof / prof[0], np.exp(-(z - z[0]) / Hy), rtol=2e-3)
+
+
+def test_element_conservation_zero_flux():
+    """Zero-flux boundaries: sum_k dz_k sum_y E_ey n_yk is invariant under an
+    unclipped step, for the tiny network and for a column with photolysis."""
+    for p in (synth.tiny_column(), synth.small_column(S=24, L=12, n_two=40, n_three=10, n_photo=6, W=60, elements="cho")):
+        o = Oracle(p)
+        _, _, dz, _ = o.grid()
+        n = o.initial_state()
+        tot0 = np.einsum("k,ky,ye->e", dz, n, p.elem.astype(float))
+        mol0 = np.einsum("k,ky->", dz, n)
+        for dt in (1e-6, 1e-3, 1.0):
+            d = o.step_delta(n, dt)
+            n = n + d
+            tot = np.einsum("k,ky,ye->e", dz, n, p.elem.astype(float))
+            np.testing.assert_allclose(tot, tot0, rtol=1e-11)
+        if p.name.startswith("tiny"):
+            # A + B -> C + D only: total molecule count is conserved too
+            assert np.einsum("k,ky->", dz, n) == pytest.approx(mol0, rel=1e-11)
+
+
+# ---------------------------------------------------------------- Jacobian, linear solve
+
+def test_jacobian_matches_central_differences():
+    p = synth.small_column(S=18, L=4, n_two=20, n_three=6, n_photo=3, W=40, elements="cho")
+    o = Oracle(p)
+    ngas = o.grid()[0]
+    # comparable abundances keep every entry above the differencing noise
+    n = ngas[:, None] * np.random.default_rng(1).uniform(0.5, 1.5, size=(p.L, p.S)) / p.S
+    kf, kr = o.rate_coefficients()
+    kph = o.photolysis(n)                    # photolysis is lagged: held fixed
+    dt = 1e300
+    A, lo, up = o.jacobian(n, dt, kf, kr, kph)
+    M = full_matrix(A, lo, up)               # = -dF/dn (1/dt vanishes)
+    LS = p.L * p.S
+    fd = np.zeros((LS, LS))
+    nf = n.ravel()
+    for j in range(LS):
+        h = 1e-5 * nf[j]
+        e = np.zeros(LS); e[j] = h
+        Fp = o.residual((nf + e).reshape(n.shape), kf, kr, kph).ravel()
+        Fm = o.residual((nf - e).reshape(n.shape), kf, kr, kph).ravel()
+        fd[:, j] = -(Fp - Fm) / (2 * h)
+    scale = np.abs(M).max(axis=1, keepdims=True) + 1e-300
+    assert np.abs((M - fd) / scale).max() < 1e-6
+
+
+def test_block_solve_matches_dense_library_solve():
+    rng = np.random.default_rng(3)
+    L, S = 7, 9
+    A = rng.normal(size=(L, S, S)) + 6 * np.eye(S)
+    lo = rng.normal(size=(L, S)); up = rng.normal(size=(L, S))
+    lo[0] = 0; up[-1] = 0
+    f = rng.normal(size=(L, S))
+    p = custom_problem(np.eye(S, dtype=np.int32), np.ones(S), [], np.stack([nasa_const_cp(2.5, 0, 0)] * S),
+                       np.geomspace(1, 1e-3, L), np.full(L, 1000.0))
+    x = Oracle(p).block_solve(A, lo, up, f)
+    ref = np.linalg.solve(full_matrix(A, lo, up), f.ravel())
+    np.testing.assert_allclose(x.ravel(), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_block_solve_needs_pivoting():
+    """A block with a zero leading entry is solved (partial pivoting)."""
+    L, S = 3, 4
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(L, S, S))
+    A[:, 0, 0] = 0.0
+    lo = 0.1 * rng.normal(size=(L, S)); up = 0.1 * rng.normal(size=(L, S))
+    lo[0] = 0; up[-1] = 0
+    f = rng.normal(size=(L, S))
+    p = custom_problem(np.eye(S, dtype=np.int32), np.ones(S), [], np.stack([nasa_const_cp(2.5, 0, 0)] * S),
+                       np.geomspace(1, 1e-3, L), np.full(L, 1000.0))
+    x = Oracle(p).block_solve(A, lo, up, f)
+    np.testing.assert_allclose(full_matrix(A, lo, up) @ x.ravel(), f.ravel(), atol=1e-10)
+
+
+# ---------------------------------------------------------------- photolysis (Sec. 2.3.3)
+
+def _photo_column(L, sigma_val, n_abs, W=1, Ptop=1e-4):
+    P = np.geomspace(1.0, Ptop, L)
+    T = np.full(L, 1000.0)
+    elem = np.array([[2, 0], [1, 0], [0, 1]], np.int32)
+    rx = [dict(type=2, reac=[0], prod=[1, 1])]
+    lam = np.linspace(1500.0, 1600.0, W); dlam = np.full(W, 2.0); J0 = np.full(W, 3e13)
+    sigma = np.full((1, W), sigma_val)
+    sigma_abs = np.zeros((3, W)); sigma_abs[0] = sigma_val
+    p = custom_problem(elem, [2.0, 1.0, 4.0], rx, np.stack([nasa_const_cp(2.5, 0, 0)] * 3), P, T,
+                       photo=(lam, dlam, J0, sigma, sigma_abs), mu=0.6, tf=0.5)
+    return p
+
+
+def test_photolysis_optically_thin_limit():
+    p = _photo_column(20, 1e-18, None, W=5)
+    o = Oracle(p)
+    n = np.zeros((p.L, p.S)); n[:, 2] = 1e12              # absorber density zero
+    kph = o.photolysis(n)
+    expect = p.tf * np.sum(p.J0 * p.sigma[0] * p.dlam)
+    np.testing.assert_allclose(kph[:, 0], expect, rtol=1e-14)
+
+
+def test_photolysis_absorbed_photon_budget():
+    """Beer-Lambert: the column absorbs J0 mu (1 - exp(-tau_tot / mu)) photons
+    per unit area and wavelength; the layer sum of k_ph n dz converges to it."""
+    p = _photo_column(600, 2e-23, None)
+    o = Oracle(p)
+    ngas, _, dz, _ = o.grid()
+    n = np.zeros((p.L, p.S)); n[:, 0] = 1e-3 * ngas
+    kph = o.photolysis(n)[:, 0]
+    absorbed = np.sum(kph * n[:, 0] * dz) / p.tf          # per unit wavelength bin x dlam
+    tau = np.sum(p.sigma[0, 0] * n[:, 0] * dz)
+    expect = p.J0[0] * p.dlam[0] * p.mu * (1 - math.exp(-tau / p.mu))
+    assert 0.5 < tau < 20
+    assert absorbed == pytest.approx(expect, rel=2e-3)
+
+
+# ---------------------------------------------------------------- step control
+
+def test_step_rejects_and_halves_on_large_change():
+    p = synth.tiny_column()
+    o = Oracle(p)
+    n = o.initial_state()
+    m, info = o.step(n, 1e6)
+    assert info.accepted == 0 and info.dt_next == 5e5
+    np.testing.assert_array_equal(m, n)
+    m, info = o.step(n, 1e-12)
+    assert info.accepted == 1 and info.dt_next == pytest.approx(3e-12)
