@@ -1,0 +1,222 @@
+/*
+ * libxk — implicit time step of the 1-D photochemical kinetics system
+ * (stiff chemistry plus vertical transport) on one NVIDIA GB300 (sm_103a).
+ *
+ * The problem is the one stated in the paper's model description (Ghosh et
+ * al., XODIAC): the continuity equation dn_y/dt = P_y - L_y - dphi_y/dz
+ * (Eq. 1) with the eddy + molecular-diffusion flux of Eq. 2, rate
+ * coefficients of Sec. 2.3 (Kooij / modified Arrhenius, Lindemann three-body,
+ * photolysis from the attenuated stellar flux, reverse rates from the Gibbs
+ * energy of reaction with NASA-7 polynomials of Appendix A), and zero-flux
+ * top and bottom boundaries (Sec. 2.5).  It is integrated by linearly
+ * implicit (backward) Euler steps: (I/dt - J) delta = F(n), solved with a
+ * block-tridiagonal LU (block Thomas) whose diagonal blocks are the dense
+ * species-by-species chemistry Jacobians of each layer and whose couplings
+ * are the diagonal transport terms.
+ *
+ * Conventions for every call:
+ *  - return value: XK_OK (0) or a negative XK_E* code; xk_last_error() gives
+ *    a message for the last failing call on that context.
+ *  - host arrays are owned by the caller and copied in; row-major (C order).
+ *  - layer 0 is the bottom of the atmosphere; state arrays are [L][S].
+ *  - units: cgs; pressure in bar; wavelength in Angstrom; densities cm^-3.
+ *  - device memory: the library allocates none for a column; the caller
+ *    provides one device workspace (xk_workspace_bytes / xk_set_workspace),
+ *    e.g. a PyTorch uint8 tensor.  The caller keeps it alive until
+ *    xk_destroy.  Work is issued on the stream given in xk_config.
+ *  - pointers documented as "device" must be device memory of the context's
+ *    GPU; "host" pointers host memory.  Calls taking both say which.
+ */
+#ifndef XK_H
+#define XK_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define XK_API __attribute__((visibility("default")))
+#else
+#define XK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XK_OK 0
+#define XK_EINVAL (-1)    /* bad argument: shape, index, NaN input, order of calls */
+#define XK_ENOMEM (-2)    /* workspace too small / footprint over budget */
+#define XK_ENOCONV (-3)   /* no steady state within max steps / solver did not converge */
+#define XK_ENEG (-4)      /* step size fell below dt_min (positivity could not be kept) */
+#define XK_ECUDA (-5)     /* CUDA runtime error */
+#define XK_ESINGULAR (-6) /* zero pivot in a diagonal block */
+#define XK_ETIMEOUT (-7)  /* a bounded device-side wait gave up */
+
+#define XK_PREC_FP64 0    /* FP64 block LU (plain path) */
+#define XK_PREC_MIXED 1   /* FP32 block LU as preconditioner + FP64 GMRES refinement */
+
+#define XK_RX_TWO_BODY 0
+#define XK_RX_THREE_BODY 1
+#define XK_RX_PHOTO 2
+
+typedef struct xk_ctx xk_ctx;
+
+typedef struct {
+    int precision;        /* XK_PREC_FP64 or XK_PREC_MIXED */
+    int device;           /* CUDA device ordinal */
+    void *stream;         /* cudaStream_t to issue work on (NULL: legacy default stream) */
+    /* step control (same policy as the CPU reference): */
+    double dt_max;        /* largest step (s) */
+    double rel_reject;    /* reject a step whose max relative change exceeds this */
+    double rel_target;    /* next dt = dt * clamp(rel_target / max_rel, shrink_min, grow_max) */
+    double grow_max, shrink_min;
+    double neg_tol;       /* reject when any n + delta < -neg_tol * n_gas */
+    double f_floor;       /* relative change is measured over species with n > f_floor n_gas */
+    double dt_min;        /* give up (XK_ENEG) below this step */
+    double ss_dt;         /* steady state: accepted step with dt >= ss_dt ... */
+    double ss_tol;        /* ... and max relative change < ss_tol */
+    /* mixed precision solver: */
+    int gmres_restart;    /* Krylov basis size m of FGMRES(m) */
+    int gmres_max_iter;   /* total iterations per linear solve */
+    double gmres_tol;     /* relative residual target in the scaled (relative) variables */
+    /* factorization tuning (0: chosen by the library / autotuner) */
+    int panel_width;      /* columns per panel of the blocked Gauss-Jordan block inversion */
+    int factor_ctas;      /* CTAs of the persistent factorization kernel per column */
+} xk_config;
+
+typedef struct {
+    int accepted;         /* 1 accepted, 0 rejected */
+    double dt_used, dt_next, max_rel;
+    int n_neg;            /* entries clipped to zero on acceptance */
+    int converged;        /* steady-state test passed on this step */
+    int solver_iters;     /* FGMRES iterations (mixed) or 0 */
+    double solver_resid;  /* final relative residual (mixed) or 0 */
+} xk_step_info;
+
+typedef struct {
+    int converged, steps, accepted, rejected;
+    double t, dt, max_rel;
+    long long solver_iters;   /* total FGMRES iterations */
+} xk_run_info;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+XK_API int xk_version(void);
+
+/* Fill cfg with the default policy: FP64, dt_max 1e8 s, rel_reject 1.0,
+ * rel_target 0.5, grow 3, shrink 0.5, neg_tol 1e-12, f_floor 1e-20,
+ * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 120 iterations, 1e-12. */
+XK_API int xk_config_init(xk_config *cfg);
+
+/* Create a context for one atmospheric column on cfg->device.  *out is set
+ * to NULL on failure.  The context owns host-side copies of all inputs. */
+XK_API int xk_create(xk_ctx **out, const xk_config *cfg);
+XK_API int xk_destroy(xk_ctx *ctx);
+XK_API const char *xk_last_error(const xk_ctx *ctx);
+
+/* Chemical network (Sec. 2.2-2.3; Appendix A).  All host arrays.
+ *  elem[S*E] element counts; mass[S] in u;
+ *  rtype[R] XK_RX_*; reac[R*3], prod[R*3] species indices, -1 padded
+ *    (a two-body or three-body reaction has >= 1 reactant and >= 1 product;
+ *     a photolysis reaction exactly one reactant);
+ *  arr[R*9] = alpha, beta, gamma (two-body) | alpha0, beta0, gamma0,
+ *    alpha_inf, beta_inf, gamma_inf (three-body); k = alpha T_b^beta exp(-gamma/T);
+ *  troe[R*4] = a, T***, T*, T** (a == 0: Lindemann without broadening);
+ *  form[R] 0: Kooij (T_b = T/300), 1: modified Arrhenius (T_b = T);
+ *  nasa[S*15] = T_mid, a1..a7 below T_mid, a1..a7 at and above T_mid.
+ * XK_EINVAL on out-of-range indices or sizes. */
+XK_API int xk_load_network(xk_ctx *ctx, int S, int E, int R, const int *elem, const double *mass,
+                    const int *rtype, const int *reac, const int *prod, const double *arr,
+                    const double *troe, const int *form, const double *nasa);
+
+/* Photolysis inputs (Sec. 2.3.3), host arrays.  prow[R]: row of sigma for
+ * each photolysis reaction (-1 otherwise); lambda[W], dlambda[W] (A);
+ * J0[W] top-of-atmosphere photon flux (cm^-2 s^-1 A^-1); sigma[Rph*W]
+ * dissociation cross sections; sigma_abs[S*W] absorption cross sections for
+ * the optical depth; mu = cos(zenith); tf = irradiated time fraction.
+ * Required (W may be 0) when the network has photolysis reactions. */
+XK_API int xk_load_photo(xk_ctx *ctx, int W, int Rph, const int *prow, const double *lambda,
+                  const double *dlambda, const double *J0, const double *sigma,
+                  const double *sigma_abs, double mu, double tf);
+
+/* Atmosphere (Sec. 2.1, Fig. 3), host arrays of length L: pressure (bar),
+ * temperature (K), Kzz (cm^2/s); dcoef[S]: molecular diffusion
+ * D_y = dcoef_y T^0.75 / n_gas; g (cm/s^2); mbar (u); alpha_T thermal
+ * diffusion factor.  Altitudes follow hydrostatic balance. */
+XK_API int xk_load_atmosphere(xk_ctx *ctx, int L, const double *P_bar, const double *T, const double *Kzz,
+                       const double *dcoef, double g, double mbar, double alpha_T);
+
+/* Device workspace needed for the loaded network and atmosphere (bytes). */
+XK_API int xk_workspace_bytes(xk_ctx *ctx, size_t *bytes);
+/* Attach a device workspace of at least xk_workspace_bytes (256-byte
+ * aligned) and upload the inputs.  Must follow the three loads. */
+XK_API int xk_set_workspace(xk_ctx *ctx, void *device_ptr, size_t bytes);
+
+/* State [L*S] number densities; on_device selects whether n is a device
+ * (1) or host (0) pointer.  xk_set_mixing_ratios sets n = f * n_gas. */
+XK_API int xk_set_state(xk_ctx *ctx, const double *n, int on_device);
+XK_API int xk_set_mixing_ratios(xk_ctx *ctx, const double *f, int on_device);
+XK_API int xk_get_state(xk_ctx *ctx, double *n, int on_device);
+
+/* One controlled implicit step of size dt (dt <= 0: use the context's
+ * current dt).  Evaluates rate coefficients, photolysis, residual, Jacobian,
+ * factorization and solve, then accepts (n updated, negatives clipped to 0)
+ * or rejects (n unchanged).  Synchronizes the stream and fills *info. */
+XK_API int xk_step(xk_ctx *ctx, double dt, xk_step_info *info);
+
+/* Steps from dt0 (dt0 <= 0: keep the current dt) until the steady-state test
+ * passes or max_steps attempts are made.  XK_ENOCONV if not converged. */
+XK_API int xk_run_to_steady(xk_ctx *ctx, double dt0, int max_steps, xk_run_info *info);
+
+/* ---- single rows of the step, on caller device buffers (for parity checks) ----
+ * Each runs on the context's stream and synchronizes it before returning. */
+/* grid: n_gas[L], z[L], dz[L], dzi[L-1] (device). */
+XK_API int xk_eval_grid(xk_ctx *ctx, double *ngas, double *z, double *dz, double *dzi);
+/* G/RT [L*S] and ln K_c [L*R] (device). */
+XK_API int xk_eval_thermo(xk_ctx *ctx, double *grt, double *lnkc);
+/* thermal k_f, k_r [L*R] (device; photolysis rows 0). */
+XK_API int xk_eval_rates(xk_ctx *ctx, double *kf, double *kr);
+/* photolysis rate constants kph [L*Rph] at state n (device). */
+XK_API int xk_eval_photolysis(xk_ctx *ctx, const double *n, double *kph);
+/* interface flux coefficients u, v [(L-1)*S] with phi = u n_k - v n_{k+1} (device). */
+XK_API int xk_eval_transport(xk_ctx *ctx, double *u, double *v);
+/* residual F(n) [L*S] (device). */
+XK_API int xk_eval_residual(xk_ctx *ctx, const double *n, double *F);
+/* I/dt - dF/dn: A [L*S*S], lo [L*S], up [L*S] (device). */
+XK_API int xk_eval_jacobian(xk_ctx *ctx, const double *n, double dt, double *A, double *lo, double *up);
+/* Solve the block-tridiagonal system given by A, lo, up (device, FP64) for
+ * right-hand side f, writing x (device).  A is not modified.  Uses the
+ * context's FP64 factorization kernels and workspace. */
+XK_API int xk_block_solve(xk_ctx *ctx, const double *A, const double *lo, const double *up,
+                   const double *f, double *x);
+/* delta solving (I/dt - J(n)) delta = F(n) with the context's precision
+ * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed). */
+XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
+
+/* ---- tracing: CUDA events around each phase of every step ----
+ * Phases: XK_PH_RATES (Gibbs energies + rate coefficients), XK_PH_PHOTO,
+ * XK_PH_REACTION (w and its derivatives), XK_PH_RESIDUAL, XK_PH_JACOBIAN,
+ * XK_PH_FACTOR (block inversions), XK_PH_SOLVE (block sweeps, or FGMRES with
+ * its sweeps in mixed mode), XK_PH_CONTROL (accept/reject/update).
+ * xk_profile(ctx, 1) starts recording (and clears totals); 0 stops.
+ * xk_profile_read fills ms[n] with the summed device time of each phase and
+ * calls[n] with the number of timed occurrences, synchronizing the stream.
+ * Event pairs beyond 65536 per phase are not recorded (calls stops growing). */
+#define XK_PH_RATES 0
+#define XK_PH_PHOTO 1
+#define XK_PH_REACTION 2
+#define XK_PH_RESIDUAL 3
+#define XK_PH_JACOBIAN 4
+#define XK_PH_FACTOR 5
+#define XK_PH_SOLVE 6
+#define XK_PH_CONTROL 7
+#define XK_PH_COUNT 8
+XK_API int xk_profile(xk_ctx *ctx, int enable);
+XK_API int xk_profile_read(xk_ctx *ctx, double *ms, long long *calls, int n);
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * contexts of the process; kernels that exit at once because their solve or
+ * step has finished are counted too). */
+XK_API long long xk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,837 @@
+// C-ABI entry points of libxk: context, input loading, workspace layout,
+// host-side index structures, and the enqueueing of the implicit step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "xk_gmres.cuh"
+#include "xk_internal.cuh"
+
+using namespace xk;
+
+struct xk_ctx {
+    xk_config cfg;
+    cudaStream_t st = nullptr;
+    std::string err;
+    // host copies of the inputs
+    int S = 0, E = 0, R = 0, L = 0, W = 0, Rph = 0;
+    std::vector<int> elem, rtype, reac, prod, form, prow;
+    std::vector<double> mass, arr, troe, nasa, lam, dlam, J0, sigma, sigma_abs, P, T, Kzz, dcoef;
+    double mu = 0.5, tf = 0.5, g = 0, mbar = 0, alpha_T = 0;
+    bool have_net = false, have_photo = false, have_atm = false;
+    // host index structures
+    std::vector<int> yp, yent, jp, jcol, jrs, abs_sp;
+    std::vector<double> sig_abs_c;
+    // device
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    Col col{};
+    Ctl *ctl = nullptr, *ctl_aux = nullptr;
+    Ctl *ctl_host = nullptr;   // pinned
+    double *A64 = nullptr, *lo64 = nullptr, *up64 = nullptr;
+    float *A32 = nullptr, *lo32 = nullptr, *up32 = nullptr;
+    int *ridx = nullptr, *sig = nullptr, *pinfo = nullptr;
+    unsigned *bar = nullptr;
+    double *gsol = nullptr;
+    // FGMRES buffers
+    double *V = nullptr, *Z = nullptr, *gw = nullptr, *h1 = nullptr, *h2 = nullptr, *red = nullptr, *partials = nullptr;
+    double *rowd = nullptr, *bhat = nullptr;   // row equilibration: diagonal of I/dt - J, scaled right-hand side
+    unsigned *counter = nullptr;
+    GmState *gm = nullptr;
+    FactorPlan plan{};
+    bool ready = false;
+    // tracing
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[XK_PH_COUNT];
+    size_t ev_used[XK_PH_COUNT] = {};
+};
+
+namespace {
+
+constexpr size_t kMaxEventPairs = 65536;
+
+// Marks one phase of a step with a pair of CUDA events when tracing is on.
+struct PhaseMark {
+    xk_ctx *c;
+    int ph;
+    cudaEvent_t end = nullptr;
+    PhaseMark(xk_ctx *ctx, int phase) : c(ctx), ph(phase)
+    {
+        if (!c->prof || c->ev_used[ph] >= kMaxEventPairs) return;
+        auto &v = c->ev[ph];
+        if (c->ev_used[ph] == v.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            v.push_back({a, b});
+        }
+        auto &pr = v[c->ev_used[ph]++];
+        cudaEventRecord(pr.first, c->st);
+        end = pr.second;
+    }
+    ~PhaseMark()
+    {
+        if (end) cudaEventRecord(end, c->st);
+    }
+};
+
+int fail(xk_ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(xk_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_check(xk_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+    return XK_OK;
+}
+
+Policy policy_of(const xk_config &c)
+{
+    Policy p;
+    p.dt_max = c.dt_max; p.rel_reject = c.rel_reject; p.rel_target = c.rel_target;
+    p.grow_max = c.grow_max; p.shrink_min = c.shrink_min; p.neg_tol = c.neg_tol;
+    p.f_floor = c.f_floor; p.dt_min = c.dt_min; p.ss_dt = c.ss_dt; p.ss_tol = c.ss_tol;
+    return p;
+}
+
+struct Bump {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// Index structures built once per network (symbolic, no arithmetic of the method).
+void build_indices(xk_ctx *c)
+{
+    const int S = c->S, R = c->R;
+    // species-major stoichiometry, in reaction order: for r, for slot s: reactant, then product
+    std::vector<std::vector<int>> ys(S);
+    for (int r = 0; r < R; ++r)
+        for (int s = 0; s < 3; ++s) {
+            int i = c->reac[3 * r + s];
+            if (i >= 0) ys[i].push_back(r * 16 + (-1 + 8));
+            int j = c->prod[3 * r + s];
+            if (j >= 0) ys[j].push_back(r * 16 + (1 + 8));
+        }
+    c->yp.assign(S + 1, 0);
+    c->yent.clear();
+    for (int y = 0; y < S; ++y) {
+        c->yent.insert(c->yent.end(), ys[y].begin(), ys[y].end());
+        c->yp[y + 1] = (int)c->yent.size();
+    }
+    // Jacobian rows: for r, side, slot s (column j), then each reactant (+) / product (-) row
+    std::vector<std::vector<std::pair<int, int>>> rows(S);
+    for (int r = 0; r < R; ++r)
+        for (int side = 0; side < 2; ++side)
+            for (int s = 0; s < 3; ++s) {
+                int j = side == 0 ? c->reac[3 * r + s] : c->prod[3 * r + s];
+                if (j < 0) continue;
+                int rs = r * 8 + side * 3 + s;
+                for (int q = 0; q < 3; ++q) {
+                    int i = c->reac[3 * r + q];
+                    if (i >= 0) rows[i].push_back({j | (1 << 16), rs});
+                    int k = c->prod[3 * r + q];
+                    if (k >= 0) rows[k].push_back({j, rs});
+                }
+            }
+    c->jp.assign(S + 1, 0);
+    c->jcol.clear();
+    c->jrs.clear();
+    for (int i = 0; i < S; ++i) {
+        for (auto &e : rows[i]) { c->jcol.push_back(e.first); c->jrs.push_back(e.second); }
+        c->jp[i + 1] = (int)c->jcol.size();
+    }
+    // absorbers with a non-zero cross section somewhere
+    c->abs_sp.clear();
+    c->sig_abs_c.clear();
+    if (c->have_photo && c->W > 0)
+        for (int y = 0; y < S; ++y) {
+            bool nz = false;
+            for (int w = 0; w < c->W; ++w) nz |= c->sigma_abs[(size_t)y * c->W + w] != 0.0;
+            if (!nz) continue;
+            c->abs_sp.push_back(y);
+            c->sig_abs_c.insert(c->sig_abs_c.end(), c->sigma_abs.begin() + (size_t)y * c->W,
+                                c->sigma_abs.begin() + (size_t)(y + 1) * c->W);
+        }
+}
+
+// Lay out the workspace; with base == nullptr only the size is computed.
+size_t layout(xk_ctx *c, char *base)
+{
+    Bump b{base};
+    const int S = c->S, R = c->R, L = c->L, W = c->W, Rph = c->Rph;
+    const int Sabs = (int)c->abs_sp.size();
+    const size_t LS = (size_t)L * S, LR = (size_t)L * R;
+    const int ld = round_up(S, 32);
+    Col &k = c->col;
+    Col t{};
+    t.S = S; t.E = c->E; t.R = R; t.L = L; t.W = W; t.Rph = Rph; t.Sabs = Sabs; t.ld = ld;
+    t.mass = b.take<double>(S); t.nasa = b.take<double>(15 * (size_t)S); t.dcoef = b.take<double>(S);
+    t.arr = b.take<double>(9 * (size_t)R); t.troe = b.take<double>(4 * (size_t)R);
+    t.rtype = b.take<int>(R); t.reac = b.take<int>(3 * (size_t)R); t.prod = b.take<int>(3 * (size_t)R);
+    t.form = b.take<int>(R); t.prow = b.take<int>(R);
+    t.yp = b.take<int>(S + 1); t.yent = b.take<int>(std::max<size_t>(1, c->yent.size()));
+    t.jp = b.take<int>(S + 1); t.jcol = b.take<int>(std::max<size_t>(1, c->jcol.size()));
+    t.jrs = b.take<int>(std::max<size_t>(1, c->jrs.size()));
+    t.J0 = b.take<double>(std::max(W, 1)); t.dlam = b.take<double>(std::max(W, 1));
+    t.sigma = b.take<double>(std::max<size_t>(1, (size_t)Rph * W));
+    t.sig_abs = b.take<double>(std::max<size_t>(1, (size_t)Sabs * W));
+    t.abs_sp = b.take<int>(std::max(Sabs, 1));
+    t.mu = c->mu; t.tf = c->tf;
+    t.P = b.take<double>(L); t.T = b.take<double>(L); t.Kzz = b.take<double>(L);
+    t.g = c->g; t.mbar = c->mbar; t.alpha_T = c->alpha_T;
+    t.ngas = b.take<double>(L); t.z = b.take<double>(L); t.dz = b.take<double>(L); t.dzi = b.take<double>(L);
+    t.u = b.take<double>(std::max<size_t>(1, (size_t)(L - 1) * S));
+    t.v = b.take<double>(std::max<size_t>(1, (size_t)(L - 1) * S));
+    t.grt = b.take<double>(LS); t.lnkc = b.take<double>(LR);
+    t.kf = b.take<double>(LR); t.kr = b.take<double>(LR);
+    t.kph = b.take<double>((size_t)L * std::max(Rph, 1));
+    t.alpha = b.take<double>((size_t)L * std::max(W, 1)); t.Jw = b.take<double>((size_t)L * std::max(W, 1));
+    t.w = b.take<double>(LR); t.d = b.take<double>(6 * LR);
+    t.n = b.take<double>(LS); t.F = b.take<double>(LS); t.s = b.take<double>(LS); t.b = b.take<double>(LS);
+    t.x = b.take<double>(LS); t.delta = b.take<double>(LS); t.tmp = b.take<double>(LS);
+    k = t;
+    c->gsol = b.take<double>(LS);
+    if (c->cfg.precision == XK_PREC_FP64) {
+        c->A64 = b.take<double>((size_t)L * S * ld);
+        c->lo64 = b.take<double>(LS);
+        c->up64 = b.take<double>(LS);
+        c->A32 = nullptr; c->lo32 = nullptr; c->up32 = nullptr;
+    } else {
+        c->A32 = b.take<float>((size_t)L * S * ld);
+        c->lo32 = b.take<float>(LS);
+        c->up32 = b.take<float>(LS);
+        c->A64 = nullptr; c->lo64 = nullptr; c->up64 = nullptr;
+        int m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
+        c->V = b.take<double>((size_t)(m + 1) * LS);
+        c->Z = b.take<double>((size_t)m * LS);
+        c->gw = b.take<double>(LS);
+        c->rowd = b.take<double>(LS);
+        c->bhat = b.take<double>(LS);
+        c->h1 = b.take<double>(kMaxBasis + 1);
+        c->h2 = b.take<double>(kMaxBasis + 1);
+        c->red = b.take<double>(8);
+        c->partials = b.take<double>((size_t)kGmPartialBlocks * (kMaxBasis + 1));
+        c->counter = b.take<unsigned>(8);
+        c->gm = b.take<GmState>(1);
+    }
+    c->ridx = b.take<int>(LS);
+    c->sig = b.take<int>(LS);
+    c->pinfo = b.take<int>(1 + 4 * 64);
+    c->bar = b.take<unsigned>(8);
+    c->ctl = b.take<Ctl>(1);
+    c->ctl_aux = b.take<Ctl>(1);
+    return b.off + 256;
+}
+
+template <typename T>
+void up(xk_ctx *c, const T *dst, const std::vector<T> &v)
+{
+    if (!v.empty()) cudaMemcpyAsync((void *)dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st);
+}
+
+BlockSys<double> sys64(xk_ctx *c)
+{
+    BlockSys<double> s;
+    s.D = c->A64; s.lo = c->lo64; s.up = c->up64; s.ridx = c->ridx; s.sig = c->sig;
+    s.pinfo = c->pinfo; s.bar = c->bar; s.L = c->L; s.S = c->S; s.ld = c->col.ld;
+    return s;
+}
+
+BlockSys<float> sys32(xk_ctx *c)
+{
+    BlockSys<float> s;
+    s.D = c->A32; s.lo = c->lo32; s.up = c->up32; s.ridx = c->ridx; s.sig = c->sig;
+    s.pinfo = c->pinfo; s.bar = c->bar; s.L = c->L; s.S = c->S; s.ld = c->col.ld;
+    return s;
+}
+
+int need_ready(xk_ctx *c)
+{
+    if (!c) return XK_EINVAL;
+    if (!c->ready) return fail(c, XK_EINVAL, "workspace not set (load network, photolysis and atmosphere, then xk_set_workspace)");
+    cudaSetDevice(c->cfg.device);
+    return XK_OK;
+}
+
+// Enqueue rows a1-a6 and the linear solve for state col.n (or n_override),
+// writing the unscaled delta into delta_out.  ctl gates every kernel.
+int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *delta_out, Ctl *ctl)
+{
+    Col col = c->col;
+    col.n = const_cast<double *>(n);
+    cudaStream_t st = c->st;
+    { PhaseMark m(c, XK_PH_RATES); launch_rates(col, st); }
+    { PhaseMark m(c, XK_PH_PHOTO); launch_photolysis(col, n, st); }
+    { PhaseMark m(c, XK_PH_REACTION); launch_reaction_terms(col, n, st); }
+    { PhaseMark m(c, XK_PH_RESIDUAL); launch_residual(col, n, col.F, ctl, c->cfg.f_floor, st); }
+    cudaError_t e;
+    if (c->cfg.precision == XK_PREC_FP64) {
+        { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, dt_override, 1, c->A64, c->lo64, c->up64, st); }
+        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan, ctl, st); }
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+        { PhaseMark m(c, XK_PH_SOLVE); e = launch_solve<double>(sys64(c), c->plan, col.b, col.x, c->gsol, ctl, st); }
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
+    } else {
+        if (dt_override > 0.0) return fail(c, XK_EINVAL, "mixed path reads dt from the control block");
+        {
+            PhaseMark m(c, XK_PH_JACOBIAN);
+            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, c->rowd, st);
+            // equations divided by their diagonal: residuals in units of relative change per species
+            launch_rowdiv((long long)c->L * c->S, col.b, c->rowd, c->bhat, st);
+        }
+        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<float>(sys32(c), c->plan, ctl, st); }
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+        GmArgs a;
+        a.N = (long long)c->L * c->S;
+        a.m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
+        a.max_iter = std::max(c->cfg.gmres_max_iter, 1);
+        a.tol = c->cfg.gmres_tol;
+        a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
+        a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
+        BlockSys<float> s32 = sys32(c);
+        FactorPlan plan = c->plan;
+        double *gsol = c->gsol;
+        const double *rowd = c->rowd;
+        a.matvec = [col, ctl, rowd](const double *x, double *y, const int *skip, cudaStream_t s) {
+            launch_jv(col, ctl, x, y, rowd, skip, s);
+        };
+        a.precond = [s32, plan, gsol, ctl, rowd](const double *v, double *z, const int *skip, cudaStream_t s) {
+            launch_solve<float>(s32, plan, v, z, gsol, ctl, s, rowd, skip);
+        };
+        { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
+    }
+    launch_unscale(col, col.x, delta_out, st);
+    return cuda_check(c, "step enqueue");
+}
+
+int enqueue_step(xk_ctx *c)
+{
+    Policy pol = policy_of(c->cfg);
+    launch_begin(c->ctl, c->st);
+    int rc = enqueue_linear_step(c, c->col.n, 0.0, c->col.delta, c->ctl);
+    if (rc) return rc;
+    {
+        PhaseMark m(c, XK_PH_CONTROL);
+        launch_check(c->col, c->ctl, pol, c->st);
+        launch_decide(c->col, c->ctl, pol, c->st);
+        launch_apply(c->col, c->ctl, c->st);
+    }
+    return cuda_check(c, "step enqueue");
+}
+
+int read_ctl(xk_ctx *c, Ctl *out)
+{
+    cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "sync: %s", cudaGetErrorString(e));
+    *out = *c->ctl_host;
+    return XK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int xk_version(void) { return 100; }
+
+int xk_config_init(xk_config *cfg)
+{
+    if (!cfg) return XK_EINVAL;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->precision = XK_PREC_FP64;
+    cfg->device = 0;
+    cfg->stream = nullptr;
+    cfg->dt_max = 1e8; cfg->rel_reject = 1.0; cfg->rel_target = 0.5; cfg->grow_max = 3.0; cfg->shrink_min = 0.5;
+    cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
+    cfg->gmres_restart = 30; cfg->gmres_max_iter = 120; cfg->gmres_tol = 1e-12;
+    cfg->panel_width = 0; cfg->factor_ctas = 0;
+    return XK_OK;
+}
+
+int xk_create(xk_ctx **out, const xk_config *cfg)
+{
+    if (!out) return XK_EINVAL;
+    *out = nullptr;
+    xk_config def;
+    xk_config_init(&def);
+    const xk_config &c = cfg ? *cfg : def;
+    if (c.precision != XK_PREC_FP64 && c.precision != XK_PREC_MIXED) return XK_EINVAL;
+    if (!(c.dt_max > 0) || !(c.dt_min > 0) || !(c.rel_reject > 0) || !(c.rel_target > 0)) return XK_EINVAL;
+    if (c.gmres_restart > kMaxBasis) return XK_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return XK_ECUDA;
+    }
+    xk_ctx *x = new xk_ctx();
+    x->cfg = c;
+    x->st = (cudaStream_t)c.stream;
+    cudaSetDevice(c.device);
+    if (cudaMallocHost((void **)&x->ctl_host, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return XK_ECUDA;
+    }
+    *out = x;
+    return XK_OK;
+}
+
+int xk_destroy(xk_ctx *ctx)
+{
+    if (!ctx) return XK_EINVAL;
+    for (auto &v : ctx->ev)
+        for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+    delete ctx;
+    return XK_OK;
+}
+
+const char *xk_last_error(const xk_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int xk_load_network(xk_ctx *c, int S, int E, int R, const int *elem, const double *mass, const int *rtype,
+                    const int *reac, const int *prod, const double *arr, const double *troe, const int *form,
+                    const double *nasa)
+{
+    if (!c) return XK_EINVAL;
+    if (S <= 0 || S > 65535 || E < 0 || R < 0 || R > (1 << 24)) return fail(c, XK_EINVAL, "bad sizes S=%d E=%d R=%d", S, E, R);
+    if (!mass || !nasa || (R > 0 && (!rtype || !reac || !prod || !arr || !troe || !form)) || (E > 0 && !elem))
+        return fail(c, XK_EINVAL, "null input array");
+    for (int r = 0; r < R; ++r) {
+        if (rtype[r] < 0 || rtype[r] > 2) return fail(c, XK_EINVAL, "reaction %d: bad type %d", r, rtype[r]);
+        int nr = 0, np = 0;
+        for (int s = 0; s < 3; ++s) {
+            if (reac[3 * r + s] >= S || reac[3 * r + s] < -1 || prod[3 * r + s] >= S || prod[3 * r + s] < -1)
+                return fail(c, XK_EINVAL, "reaction %d: species index out of range", r);
+            nr += reac[3 * r + s] >= 0;
+            np += prod[3 * r + s] >= 0;
+        }
+        if (nr == 0 || (rtype[r] != XK_RX_PHOTO && np == 0) || (rtype[r] == XK_RX_PHOTO && nr != 1))
+            return fail(c, XK_EINVAL, "reaction %d: bad reactant/product count", r);
+        for (int q = 0; q < 9; ++q)
+            if (!std::isfinite(arr[9 * r + q])) return fail(c, XK_EINVAL, "reaction %d: non-finite rate parameter", r);
+    }
+    for (int y = 0; y < S; ++y)
+        if (!(mass[y] > 0)) return fail(c, XK_EINVAL, "species %d: mass must be positive", y);
+    c->S = S; c->E = E; c->R = R;
+    c->elem.assign(elem, elem + (size_t)S * E);
+    c->mass.assign(mass, mass + S);
+    c->rtype.assign(rtype, rtype + R);
+    c->reac.assign(reac, reac + 3 * (size_t)R);
+    c->prod.assign(prod, prod + 3 * (size_t)R);
+    c->arr.assign(arr, arr + 9 * (size_t)R);
+    c->troe.assign(troe, troe + 4 * (size_t)R);
+    c->form.assign(form, form + R);
+    c->nasa.assign(nasa, nasa + 15 * (size_t)S);
+    c->have_net = true;
+    c->have_photo = false;
+    c->ready = false;
+    c->Rph = 0;
+    c->prow.assign(R, -1);
+    return XK_OK;
+}
+
+int xk_load_photo(xk_ctx *c, int W, int Rph, const int *prow, const double *lambda, const double *dlambda,
+                  const double *J0, const double *sigma, const double *sigma_abs, double mu, double tf)
+{
+    if (!c) return XK_EINVAL;
+    if (!c->have_net) return fail(c, XK_EINVAL, "load the network first");
+    if (W < 0 || Rph < 0) return fail(c, XK_EINVAL, "bad sizes");
+    if (!prow) return fail(c, XK_EINVAL, "null prow");
+    if (W > 0 && (!lambda || !dlambda || !J0 || !sigma_abs || (Rph > 0 && !sigma))) return fail(c, XK_EINVAL, "null input array");
+    if (!(mu > 0.0)) return fail(c, XK_EINVAL, "mu must be positive");
+    int nph = 0;
+    for (int r = 0; r < c->R; ++r) {
+        if (c->rtype[r] == XK_RX_PHOTO) {
+            if (prow[r] < 0 || prow[r] >= Rph) return fail(c, XK_EINVAL, "photolysis reaction %d: bad sigma row", r);
+            ++nph;
+        } else if (prow[r] != -1) {
+            return fail(c, XK_EINVAL, "reaction %d is not photolysis but has a sigma row", r);
+        }
+    }
+    c->W = W; c->Rph = Rph;
+    c->prow.assign(prow, prow + c->R);
+    c->lam.assign(lambda, lambda + W);
+    c->dlam.assign(dlambda, dlambda + W);
+    c->J0.assign(J0, J0 + W);
+    c->sigma.assign(sigma, sigma + (size_t)Rph * W);
+    c->sigma_abs.assign(sigma_abs, sigma_abs + (size_t)c->S * W);
+    c->mu = mu; c->tf = tf;
+    c->have_photo = true;
+    c->ready = false;
+    (void)nph;
+    return XK_OK;
+}
+
+int xk_load_atmosphere(xk_ctx *c, int L, const double *P_bar, const double *T, const double *Kzz,
+                       const double *dcoef, double g, double mbar, double alpha_T)
+{
+    if (!c) return XK_EINVAL;
+    if (!c->have_net) return fail(c, XK_EINVAL, "load the network first");
+    if (L <= 0) return fail(c, XK_EINVAL, "L must be positive");
+    if (!P_bar || !T || !Kzz || !dcoef) return fail(c, XK_EINVAL, "null input array");
+    for (int k = 0; k < L; ++k) {
+        if (!(P_bar[k] > 0) || !(T[k] > 0) || !(Kzz[k] >= 0)) return fail(c, XK_EINVAL, "layer %d: bad P/T/Kzz", k);
+        if (k > 0 && !(P_bar[k] < P_bar[k - 1])) return fail(c, XK_EINVAL, "pressure must fall with layer index");
+    }
+    if (!(g > 0) || !(mbar > 0)) return fail(c, XK_EINVAL, "g and mbar must be positive");
+    c->L = L;
+    c->P.assign(P_bar, P_bar + L);
+    c->T.assign(T, T + L);
+    c->Kzz.assign(Kzz, Kzz + L);
+    c->dcoef.assign(dcoef, dcoef + c->S);
+    c->g = g; c->mbar = mbar; c->alpha_T = alpha_T;
+    c->have_atm = true;
+    c->ready = false;
+    return XK_OK;
+}
+
+int xk_workspace_bytes(xk_ctx *c, size_t *bytes)
+{
+    if (!c || !bytes) return XK_EINVAL;
+    if (!c->have_net || !c->have_atm) return fail(c, XK_EINVAL, "load network and atmosphere first");
+    bool has_photo = false;
+    for (int r = 0; r < c->R; ++r) has_photo |= c->rtype[r] == XK_RX_PHOTO;
+    if (has_photo && !c->have_photo) return fail(c, XK_EINVAL, "network has photolysis reactions: load photolysis inputs");
+    build_indices(c);
+    *bytes = layout(c, nullptr);
+    return XK_OK;
+}
+
+int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
+{
+    size_t need = 0;
+    int rc = xk_workspace_bytes(c, &need);
+    if (rc) return rc;
+    if (!dptr || bytes < need) return fail(c, XK_ENOMEM, "workspace of %zu bytes, need %zu", bytes, need);
+    if (((uintptr_t)dptr) & 255) return fail(c, XK_EINVAL, "workspace must be 256-byte aligned");
+    cudaSetDevice(c->cfg.device);
+    c->ws = (char *)dptr;
+    c->ws_bytes = bytes;
+    layout(c, c->ws);
+    int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
+    if (factor_plan(c->S, sz, c->cfg.panel_width, c->cfg.factor_ctas, &c->plan) != 0)
+        return fail(c, XK_EINVAL, "no factorization plan for S=%d (panel %d)", c->S, c->cfg.panel_width);
+    Col &k = c->col;
+    up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
+    up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
+    up(c, k.prod, c->prod); up(c, k.form, c->form); up(c, k.prow, c->prow);
+    up(c, k.yp, c->yp); up(c, k.yent, c->yent); up(c, k.jp, c->jp); up(c, k.jcol, c->jcol); up(c, k.jrs, c->jrs);
+    up(c, k.J0, c->J0); up(c, k.dlam, c->dlam); up(c, k.sigma, c->sigma); up(c, k.sig_abs, c->sig_abs_c);
+    up(c, k.abs_sp, c->abs_sp);
+    up(c, k.P, c->P); up(c, k.T, c->T); up(c, k.Kzz, c->Kzz);
+    cudaMemsetAsync(c->bar, 0, 8 * sizeof(unsigned), c->st);
+    if (c->counter) cudaMemsetAsync(c->counter, 0, 8 * sizeof(unsigned), c->st);
+    cudaMemsetAsync(c->col.n, 0, sizeof(double) * (size_t)c->L * c->S, c->st);
+    Ctl init{};
+    init.dt = 1e-8;
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    launch_grid(c->col, c->st);
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "upload: %s", cudaGetErrorString(e));
+    c->ready = true;
+    return cuda_check(c, "set_workspace");
+}
+
+int xk_set_state(xk_ctx *c, const double *n, int on_device)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n) return fail(c, XK_EINVAL, "null state");
+    cudaMemcpyAsync(c->col.n, n, sizeof(double) * (size_t)c->L * c->S,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "set_state");
+    return cuda_check(c, "set_state");
+}
+
+int xk_set_mixing_ratios(xk_ctx *c, const double *f, int on_device)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!f) return fail(c, XK_EINVAL, "null mixing ratios");
+    cudaMemcpyAsync(c->col.tmp, f, sizeof(double) * (size_t)c->L * c->S,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st);
+    launch_set_mixing(c->col, c->col.tmp, c->col.n, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "set_mixing_ratios");
+    return cuda_check(c, "set_mixing_ratios");
+}
+
+int xk_get_state(xk_ctx *c, double *n, int on_device)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n) return fail(c, XK_EINVAL, "null output");
+    cudaMemcpyAsync(n, c->col.n, sizeof(double) * (size_t)c->L * c->S,
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "get_state");
+    return cuda_check(c, "get_state");
+}
+
+static void fill_step_info(const Ctl &h, xk_step_info *info)
+{
+    if (!info) return;
+    info->accepted = h.accepted;
+    info->dt_used = h.last_dt;
+    info->dt_next = h.dt;
+    info->max_rel = h.max_rel;
+    info->n_neg = h.n_neg;
+    info->converged = h.converged;
+    info->solver_iters = h.solver_iters;
+    info->solver_resid = h.solver_resid;
+}
+
+int xk_step(xk_ctx *c, double dt, xk_step_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    Ctl h;
+    if ((rc = read_ctl(c, &h))) return rc;
+    h.finished = 0;
+    h.converged = 0;
+    h.status = 0;
+    h.err_timeout = 0;
+    h.err_singular = 0;
+    if (dt > 0.0) h.dt = dt;
+    *c->ctl_host = h;
+    cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    if ((rc = enqueue_step(c))) return rc;
+    if ((rc = read_ctl(c, &h))) return rc;
+    fill_step_info(h, info);
+    if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (h.status) return fail(c, h.status, "step failed with status %d", h.status);
+    return XK_OK;
+}
+
+int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (max_steps <= 0) return fail(c, XK_EINVAL, "max_steps must be positive");
+    Ctl h;
+    if ((rc = read_ctl(c, &h))) return rc;
+    Ctl init{};
+    init.dt = dt0 > 0.0 ? dt0 : h.dt;
+    init.t = 0.0;
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    int enq = 0;
+    const int chunk = 16;
+    while (enq < max_steps) {
+        int nrun = std::min(chunk, max_steps - enq);
+        for (int i = 0; i < nrun; ++i)
+            if ((rc = enqueue_step(c))) return rc;
+        enq += nrun;
+        if ((rc = read_ctl(c, &h))) return rc;
+        if (h.finished) break;
+    }
+    if (info) {
+        info->converged = h.converged;
+        info->steps = h.steps;
+        info->accepted = h.n_acc;
+        info->rejected = h.n_rej;
+        info->t = h.t;
+        info->dt = h.dt;
+        info->max_rel = h.max_rel;
+        info->solver_iters = h.total_iters;
+    }
+    if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (h.status) return fail(c, h.status, "run stopped with status %d", h.status);
+    if (!h.converged) return fail(c, XK_ENOCONV, "no steady state after %d steps", h.steps);
+    return XK_OK;
+}
+
+// ---------------------------------------------------------------- rows
+
+static int finish_eval(xk_ctx *c, const char *what)
+{
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return cuda_check(c, what);
+}
+
+static void d2d(xk_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->st);
+}
+
+int xk_eval_grid(xk_ctx *c, double *ngas, double *z, double *dz, double *dzi)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    const size_t L = c->L;
+    if (ngas) d2d(c, ngas, c->col.ngas, L * 8);
+    if (z) d2d(c, z, c->col.z, L * 8);
+    if (dz) d2d(c, dz, c->col.dz, L * 8);
+    if (dzi && L > 1) d2d(c, dzi, c->col.dzi, (L - 1) * 8);
+    return finish_eval(c, "eval_grid");
+}
+
+int xk_eval_thermo(xk_ctx *c, double *grt, double *lnkc)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    launch_rates(c->col, c->st);
+    if (grt) d2d(c, grt, c->col.grt, (size_t)c->L * c->S * 8);
+    if (lnkc) d2d(c, lnkc, c->col.lnkc, (size_t)c->L * c->R * 8);
+    return finish_eval(c, "eval_thermo");
+}
+
+int xk_eval_rates(xk_ctx *c, double *kf, double *kr)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    launch_rates(c->col, c->st);
+    if (kf) d2d(c, kf, c->col.kf, (size_t)c->L * c->R * 8);
+    if (kr) d2d(c, kr, c->col.kr, (size_t)c->L * c->R * 8);
+    return finish_eval(c, "eval_rates");
+}
+
+int xk_eval_photolysis(xk_ctx *c, const double *n, double *kph)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n || !kph) return fail(c, XK_EINVAL, "null pointer");
+    launch_photolysis(c->col, n, c->st);
+    d2d(c, kph, c->col.kph, (size_t)c->L * c->Rph * 8);
+    return finish_eval(c, "eval_photolysis");
+}
+
+int xk_eval_transport(xk_ctx *c, double *u, double *v)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    size_t bytes = (size_t)(c->L - 1) * c->S * 8;
+    if (u) d2d(c, u, c->col.u, bytes);
+    if (v) d2d(c, v, c->col.v, bytes);
+    return finish_eval(c, "eval_transport");
+}
+
+int xk_eval_residual(xk_ctx *c, const double *n, double *F)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n || !F) return fail(c, XK_EINVAL, "null pointer");
+    launch_rates(c->col, c->st);
+    launch_photolysis(c->col, n, c->st);
+    launch_reaction_terms(c->col, n, c->st);
+    launch_residual(c->col, n, F, nullptr, c->cfg.f_floor, c->st);
+    return finish_eval(c, "eval_residual");
+}
+
+int xk_eval_jacobian(xk_ctx *c, const double *n, double dt, double *A, double *lo, double *up)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n || !A || !lo || !up || !(dt > 0)) return fail(c, XK_EINVAL, "bad argument");
+    Col col = c->col;
+    col.ld = c->S;
+    launch_rates(col, c->st);
+    launch_photolysis(col, n, c->st);
+    launch_reaction_terms(col, n, c->st);
+    launch_residual(col, n, col.F, nullptr, c->cfg.f_floor, c->st);
+    launch_jacobian64(col, n, nullptr, dt, 0, A, lo, up, c->st);
+    return finish_eval(c, "eval_jacobian");
+}
+
+int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *up, const double *f, double *x)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (c->cfg.precision != XK_PREC_FP64) return fail(c, XK_EINVAL, "xk_block_solve needs an FP64 context");
+    if (!A || !lo || !up || !f || !x) return fail(c, XK_EINVAL, "null pointer");
+    const size_t S = c->S, L = c->L;
+    cudaMemcpy2DAsync(c->A64, c->col.ld * 8, A, S * 8, S * 8, L * S, cudaMemcpyDeviceToDevice, c->st);
+    d2d(c, c->lo64, lo, L * S * 8);
+    d2d(c, c->up64, up, L * S * 8);
+    Ctl init{};
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    cudaError_t e = launch_factor<double>(sys64(c), c->plan, c->ctl_aux, c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+    e = launch_solve<double>(sys64(c), c->plan, f, x, c->gsol, c->ctl_aux, c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
+    cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    if ((rc = finish_eval(c, "block_solve"))) return rc;
+    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
+    return XK_OK;
+}
+
+int xk_step_delta(xk_ctx *c, const double *n, double dt, double *delta, int *iters, double *resid)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n || !delta || !(dt > 0)) return fail(c, XK_EINVAL, "bad argument");
+    Ctl init{};
+    init.dt = dt;
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    double dto = c->cfg.precision == XK_PREC_FP64 ? dt : 0.0;
+    if ((rc = enqueue_linear_step(c, n, dto, delta, c->ctl_aux))) return rc;
+    cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    if ((rc = finish_eval(c, "step_delta"))) return rc;
+    if (iters) *iters = c->ctl_host->solver_iters;
+    if (resid) *resid = c->ctl_host->solver_resid;
+    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
+    return XK_OK;
+}
+
+long long xk_launch_count(void) { return launches(); }
+
+int xk_profile(xk_ctx *c, int enable)
+{
+    if (!c) return XK_EINVAL;
+    c->prof = enable != 0;
+    for (auto &u : c->ev_used) u = 0;
+    return XK_OK;
+}
+
+int xk_profile_read(xk_ctx *c, double *ms, long long *calls, int n)
+{
+    if (!c || n < 0 || (n > 0 && (!ms || !calls))) return XK_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "profile sync: %s", cudaGetErrorString(e));
+    for (int p = 0; p < n && p < XK_PH_COUNT; ++p) {
+        double tot = 0.0;
+        for (size_t i = 0; i < c->ev_used[p]; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->ev[p][i].first, c->ev[p][i].second) == cudaSuccess) tot += t;
+            else cudaGetLastError();
+        }
+        ms[p] = tot;
+        calls[p] = (long long)c->ev_used[p];
+    }
+    return XK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,609 @@
+// Chemistry and transport rows of the implicit step: grid, thermochemistry,
+// rate coefficients, photolysis, reaction rates and their derivatives,
+// residual F(n) (Eq. 1 with the flux of Eq. 2), Jacobian blocks, the
+// matrix-free Jacobian-vector product, and device-side step control.
+#include <math.h>
+
+#include <atomic>
+
+#include "xk_internal.cuh"
+
+namespace xk {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int nblocks(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// grid (Sec. 2.1): n_gas = P / (k_B T); hydrostatic altitudes; layer widths
+// ---------------------------------------------------------------------------
+__global__ void k_grid(Col c)
+{
+    int L = c.L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x)
+        c.ngas[k] = c.P[k] * kBarToCgs / (kBoltz * c.T[k]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double z = 0.0;
+        c.z[0] = 0.0;
+        for (int k = 0; k + 1 < L; ++k) {
+            double Th = 0.5 * (c.T[k] + c.T[k + 1]);
+            double H = kBoltz * Th / (c.mbar * kAmu * c.g);
+            z = z + H * log(c.P[k] / c.P[k + 1]);
+            c.z[k + 1] = z;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        if (k + 1 < L) c.dzi[k] = c.z[k + 1] - c.z[k];
+        double w;
+        if (L == 1) w = 1.0;
+        else if (k == 0) w = c.z[1] - c.z[0];
+        else if (k == L - 1) w = c.z[L - 1] - c.z[L - 2];
+        else w = 0.5 * (c.z[k + 1] - c.z[k - 1]);
+        c.dz[k] = w;
+    }
+}
+
+// Eq. 2 at interface k+1/2: phi = u n_k - v n_{k+1}; eddy part in mixing-ratio
+// form -K n_gas d(n/n_gas)/dz, molecular part -D (dn/dz + n (1/H_y + (1+alpha_T) T'/T)).
+__global__ void k_transport(Col c)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int S = c.S;
+    if (idx >= (long long)(c.L - 1) * S) return;
+    int k = (int)(idx / S), y = (int)(idx % S);
+    double Th = 0.5 * (c.T[k] + c.T[k + 1]);
+    double nh = 0.5 * (c.ngas[k] + c.ngas[k + 1]);
+    double Kh = 0.5 * (c.Kzz[k] + c.Kzz[k + 1]);
+    double h = c.dzi[k];
+    double dTdz = (c.T[k + 1] - c.T[k]) / h;
+    double D = c.dcoef[y] * pow(Th, 0.75) / nh;
+    double Hy = kBoltz * Th / (c.mass[y] * kAmu * c.g);
+    double a = 1.0 / Hy + (1.0 + c.alpha_T) * dTdz / Th;
+    c.u[idx] = Kh * nh / (h * c.ngas[k]) + D * (1.0 / h - 0.5 * a);
+    c.v[idx] = Kh * nh / (h * c.ngas[k + 1]) + D * (1.0 / h + 0.5 * a);
+}
+
+// ---------------------------------------------------------------------------
+// thermochemistry (Appendix A) and rate coefficients (Sec. 2.3)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gibbs_rt(const double *nasa15, double T)
+{
+    const double *a = (T < nasa15[0]) ? nasa15 + 1 : nasa15 + 8;
+    return a[0] * (1.0 - log(T)) - a[1] * T / 2.0 - a[2] * T * T / 6.0
+         - a[3] * T * T * T / 12.0 - a[4] * T * T * T * T / 20.0 + a[5] / T - a[6];
+}
+
+__global__ void k_gibbs(Col c)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.S) return;
+    int k = (int)(idx / c.S), y = (int)(idx % c.S);
+    c.grt[idx] = gibbs_rt(c.nasa + 15 * y, c.T[k]);
+}
+
+__device__ __forceinline__ double arrh(double al, double be, double ga, double T, int form)
+{
+    double Tb = (form == 0) ? T / 300.0 : T;
+    return al * pow(Tb, be) * exp(-ga / T);
+}
+
+__device__ __forceinline__ double troe_f(const double *tr, double T, double Pr)
+{
+    if (tr[0] == 0.0 || Pr <= 0.0) return 1.0;
+    double Fc = (1.0 - tr[0]) * exp(-T / tr[1]) + tr[0] * exp(-T / tr[2]);
+    if (tr[3] != 0.0) Fc += exp(-tr[3] / T);
+    double lFc = log10(Fc);
+    double cc = -0.4 - 0.67 * lFc;
+    double N = 0.75 - 1.27 * lFc;
+    double x = log10(Pr) + cc;
+    double q = x / (N - 0.14 * x);
+    return pow(10.0, lFc / (1.0 + q * q));
+}
+
+// k_f, k_r and ln K_c per (layer, reaction); ln K_c = -sum nu G/RT + dnu ln(p0 / k_B T).
+__global__ void k_rates(Col c)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.R) return;
+    int k = (int)(idx / c.R), r = (int)(idx % c.R);
+    double T = c.T[k];
+    int t = c.rtype[r];
+    const double *grt = c.grt + (long long)k * c.S;
+    double dG = 0.0;
+    int dnu = 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        int i = c.reac[3 * r + s];
+        if (i >= 0) { dG -= grt[i]; dnu -= 1; }
+        int j = c.prod[3 * r + s];
+        if (j >= 0) { dG += grt[j]; dnu += 1; }
+    }
+    double lnk = (t == XK_RX_PHOTO) ? 0.0 : -dG + dnu * log(kP0 / (kBoltz * T));
+    const double *a = c.arr + 9 * r;
+    double f = 0.0, b = 0.0;
+    if (t == XK_RX_TWO_BODY) {
+        f = arrh(a[0], a[1], a[2], T, c.form[r]);
+    } else if (t == XK_RX_THREE_BODY) {
+        double k0 = arrh(a[3], a[4], a[5], T, c.form[r]);
+        double ki = arrh(a[6], a[7], a[8], T, c.form[r]);
+        double M = c.ngas[k];
+        double Pr = k0 * M / ki;
+        f = k0 * M / (1.0 + k0 * M / ki) * troe_f(c.troe + 4 * r, T, Pr);
+    }
+    if (t != XK_RX_PHOTO) b = f / exp(lnk);
+    c.kf[idx] = f;
+    c.kr[idx] = b;
+    if (c.lnkc) c.lnkc[idx] = lnk;
+}
+
+// ---------------------------------------------------------------------------
+// photolysis (Sec. 2.3.3): direct beam, optical depth to the layer midpoint
+// ---------------------------------------------------------------------------
+__global__ void k_photo_alpha(Col c, const double *n)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.W) return;
+    int k = (int)(idx / c.W), w = (int)(idx % c.W);
+    const double *nk = n + (long long)k * c.S;
+    double s = 0.0;
+    for (int i = 0; i < c.Sabs; ++i)
+        s += c.sig_abs[(long long)i * c.W + w] * nk[c.abs_sp[i]];
+    c.alpha[idx] = s;
+}
+
+__global__ void k_photo_J(Col c)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= c.W) return;
+    double above = 0.0;
+    double J0 = c.J0[w];
+    for (int k = c.L - 1; k >= 0; --k) {
+        double a = c.alpha[(long long)k * c.W + w];
+        double tau = above + 0.5 * a * c.dz[k];
+        c.Jw[(long long)k * c.W + w] = J0 * exp(-tau / c.mu);
+        above += a * c.dz[k];
+    }
+}
+
+// k_ph = t_f sum_w J(k, w) sigma(w) dlambda(w); one warp per (layer, reaction)
+__global__ void k_photo_k(Col c)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= c.L * c.Rph) return;
+    int k = warp / c.Rph, q = warp % c.Rph;
+    const double *J = c.Jw + (long long)k * c.W;
+    const double *sg = c.sigma + (long long)q * c.W;
+    // each lane sums a contiguous chunk in order; chunks are added in lane order
+    int per = (c.W + 31) / 32;
+    int w0 = lane * per, w1 = min(c.W, w0 + per);
+    double s = 0.0;
+    for (int w = w0; w < w1; ++w)
+        s += J[w] * sg[w] * c.dlam[w];
+    double tot = 0.0;
+    for (int l = 0; l < 32; ++l) {
+        double v = __shfl_sync(0xffffffffu, s, l);
+        tot += v;
+    }
+    if (lane == 0) c.kph[(long long)k * c.Rph + q] = c.tf * tot;
+}
+
+// ---------------------------------------------------------------------------
+// reaction rates w = k_f prod n_reac - k_r prod n_prod and partial derivatives
+// d[slot] = d(k_f prod n_reac)/d n_reac[slot] (slots 0-2) and
+//           -d(k_r prod n_prod)/d n_prod[slot] (slots 3-5)
+// ---------------------------------------------------------------------------
+__global__ void k_reaction_terms(Col c, const double *n)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.R) return;
+    int k = (int)(idx / c.R), r = (int)(idx % c.R);
+    const double *nk = n + (long long)k * c.S;
+    double kfv, krv;
+    if (c.rtype[r] == XK_RX_PHOTO) {
+        kfv = c.kph[(long long)k * c.Rph + c.prow[r]];
+        krv = 0.0;
+    } else {
+        kfv = c.kf[idx];
+        krv = c.kr[idx];
+    }
+    int ra[3], pa[3];
+    double na[3], pb[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        ra[s] = c.reac[3 * r + s];
+        pa[s] = c.prod[3 * r + s];
+        na[s] = ra[s] >= 0 ? nk[ra[s]] : 0.0;
+        pb[s] = pa[s] >= 0 ? nk[pa[s]] : 0.0;
+    }
+    double wf = kfv, wb = krv;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        if (ra[s] >= 0) wf *= na[s];
+        if (pa[s] >= 0) wb *= pb[s];
+    }
+    c.w[idx] = wf - wb;
+    double *d = c.d + idx * 6;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        double df = 0.0, db = 0.0;
+        if (ra[s] >= 0) {
+            df = kfv;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t != s && ra[t] >= 0) df *= na[t];
+        }
+        if (pa[s] >= 0) {
+            db = -krv;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t != s && pa[t] >= 0) db *= pb[t];
+        }
+        d[s] = df;
+        d[3 + s] = db;
+    }
+}
+
+// F = sum_r nu w_r - (phi_{k+1/2} - phi_{k-1/2}) / dz_k; also the solve scaling
+// s = max(n, f_floor n_gas) and the scaled right-hand side b = F / s.
+__global__ void k_residual(Col c, const double *n, double *F, const Ctl *ctl, double f_floor)
+{
+    if (ctl && ctl->finished) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int S = c.S, L = c.L;
+    if (idx >= (long long)L * S) return;
+    int k = (int)(idx / S), y = (int)(idx % S);
+    const double *wk = c.w + (long long)k * c.R;
+    double f = 0.0;
+    for (int e = c.yp[y]; e < c.yp[y + 1]; ++e) {
+        int code = c.yent[e];
+        int r = code >> 4;
+        int nu = (code & 15) - 8;
+        if (nu < 0) f -= wk[r];
+        else f += wk[r];
+    }
+    double nk = n[idx];
+    double upf = 0.0, dnf = 0.0;
+    if (k + 1 < L) upf = c.u[(long long)k * S + y] * nk - c.v[(long long)k * S + y] * n[idx + S];
+    if (k > 0) dnf = c.u[(long long)(k - 1) * S + y] * n[idx - S] - c.v[(long long)(k - 1) * S + y] * nk;
+    f += -(upf - dnf) / c.dz[k];
+    F[idx] = f;
+    if (c.s) {
+        double sc = fmax(nk, f_floor * c.ngas[k]);
+        c.s[idx] = sc;
+        c.b[idx] = f / sc;
+    }
+}
+
+// Dense diagonal blocks A_k = I/dt - dF_k/dn_k, couplings lo/up; one warp per row.
+// Contributions are summed in a fixed order (deterministic).  scaled != 0 writes
+// diag(1/s) A diag(s) and the matching couplings.
+template <typename T>
+__global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_override, int scaled,
+                           T *A, T *lo, T *up, double *dout)
+{
+    if (ctl && ctl->finished) return;
+    extern __shared__ double sh[];
+    int S = c.S, L = c.L;
+    int wpb = blockDim.x >> 5;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long row = (long long)blockIdx.x * wpb + warp;     // (k, i)
+    bool active = row < (long long)L * S;
+    double *rowbuf = sh + (long long)warp * (S + 64);
+    double *vals = rowbuf + S;
+    int *cols = (int *)(vals + 32);
+    int k = active ? (int)(row / S) : 0, i = active ? (int)(row % S) : 0;
+    if (!active) return;
+    for (int j = lane; j < S; j += 32) rowbuf[j] = 0.0;
+    __syncwarp();
+    const double *dk = c.d + (long long)k * c.R * 6;
+    int e0 = c.jp[i], e1 = c.jp[i + 1];
+    for (int base = e0; base < e1; base += 32) {
+        int e = base + lane;
+        if (e < e1) {
+            int jc = c.jcol[e];
+            int rs = c.jrs[e];
+            double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+            cols[lane] = jc & 0xffff;
+            vals[lane] = ((jc >> 16) > 0) ? dv : -dv;      // +d for a reactant row, -d for a product row
+        }
+        __syncwarp();
+        if (lane == 0) {
+            int cnt = min(32, e1 - base);
+            for (int q = 0; q < cnt; ++q) rowbuf[cols[q]] += vals[q];
+        }
+        __syncwarp();
+    }
+    double dt = dt_override > 0.0 ? dt_override : ctl->dt;
+    const double *sk = c.s + (long long)k * S;
+    if (lane == 0) {
+        double diag = 1.0 / dt;
+        if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
+        if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
+        rowbuf[i] += diag;
+        if (dout) dout[row] = fmax(fabs(rowbuf[i]), 1.0 / dt);
+        double lov = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
+        double upv = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+        if (scaled) {
+            if (k > 0) lov *= c.s[(long long)(k - 1) * S + i] / sk[i];
+            if (k + 1 < L) upv *= c.s[(long long)(k + 1) * S + i] / sk[i];
+        }
+        lo[row] = (T)lov;
+        up[row] = (T)upv;
+    }
+    __syncwarp();
+    T *Ar = A + ((long long)k * S + i) * c.ld;
+    if (scaled) {
+        double inv = 1.0 / sk[i];
+        for (int j = lane; j < S; j += 32) Ar[j] = (T)(rowbuf[j] * sk[j] * inv);
+    } else {
+        for (int j = lane; j < S; j += 32) Ar[j] = (T)rowbuf[j];
+    }
+    for (int j = S + lane; j < c.ld; j += 32) Ar[j] = (T)0;
+}
+
+// y = diag(1/s) (I/dt - J) diag(s) x, matrix-free from the reaction derivatives (FP64).
+__global__ void k_jv(Col c, const Ctl *ctl, const double *x, double *y, const double *rowdiv, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    int S = c.S, L = c.L;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= L * S) return;
+    int k = warp / S, i = warp % S;
+    const double *dk = c.d + (long long)k * c.R * 6;
+    const double *sk = c.s + (long long)k * S;
+    const double *xk = x + (long long)k * S;
+    double acc = 0.0;
+    for (int e = c.jp[i] + lane; e < c.jp[i + 1]; e += 32) {
+        int jc = c.jcol[e];
+        int rs = c.jrs[e];
+        double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+        int j = jc & 0xffff;
+        double t = dv * sk[j] * xk[j];
+        acc += ((jc >> 16) > 0) ? t : -t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        double si = sk[i];
+        double diag = 1.0 / ctl->dt;
+        if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
+        if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
+        double r = acc / si + diag * xk[i];
+        if (k > 0) r += (-c.u[(long long)(k - 1) * S + i] / c.dz[k]) * c.s[(long long)(k - 1) * S + i] / si * x[(long long)(k - 1) * S + i];
+        if (k + 1 < L) r += (-c.v[(long long)k * S + i] / c.dz[k]) * c.s[(long long)(k + 1) * S + i] / si * x[(long long)(k + 1) * S + i];
+        if (rowdiv) r /= rowdiv[(long long)k * S + i];
+        y[(long long)k * S + i] = r;
+    }
+}
+
+// y = x / d (row equilibration of a right-hand side)
+__global__ void k_rowdiv(long long N, const double *x, const double *d, double *y)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < N) y[idx] = x[idx] / d[idx];
+}
+
+__global__ void k_unscale(Col c, const double *xs, double *delta)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.S) return;
+    delta[idx] = xs[idx] * c.s[idx];
+}
+
+// ---------------------------------------------------------------------------
+// step control on the device
+// ---------------------------------------------------------------------------
+__global__ void k_check(Col c, Ctl *ctl, Policy pol)
+{
+    if (ctl->finished) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int S = c.S;
+    double rel = 0.0;
+    int bad = 0, neg = 0;
+    if (idx < (long long)c.L * S) {
+        int k = (int)(idx / S);
+        double nv = c.n[idx], dv = c.delta[idx];
+        double nn = nv + dv;
+        double ng = c.ngas[k];
+        if (!isfinite(nn)) bad = 1;
+        else {
+            if (nn < -pol.neg_tol * ng) bad = 1;
+            if (nn < 0.0) neg = 1;
+            if (nv > pol.f_floor * ng) rel = fabs(dv) / nv;
+        }
+    }
+    // warp-level combine, one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rel = fmax(rel, __shfl_xor_sync(0xffffffffu, rel, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        neg += __shfl_xor_sync(0xffffffffu, neg, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (rel > 0.0) atomicMax(&ctl->max_rel_bits, (unsigned long long)__double_as_longlong(rel));
+        if (bad) atomicOr(&ctl->bad, 1);
+        if (neg) atomicAdd(&ctl->n_neg, neg);
+    }
+}
+
+__global__ void k_begin(Ctl *ctl)
+{
+    if (ctl->finished) {
+        ctl->accepted = 0;
+        return;
+    }
+    ctl->max_rel_bits = 0ull;
+    ctl->bad = 0;
+    ctl->n_neg = 0;
+    ctl->accepted = 0;
+    ctl->converged = 0;
+}
+
+__global__ void k_decide(Ctl *ctl, Policy pol)
+{
+    if (ctl->finished) return;
+    double dt = ctl->dt;
+    double maxrel = __longlong_as_double((long long)ctl->max_rel_bits);
+    int ok = !ctl->bad && !ctl->err_singular && !ctl->err_timeout;
+    if (ok && maxrel > pol.rel_reject) ok = 0;
+    ctl->max_rel = maxrel;
+    ctl->last_dt = dt;
+    ctl->steps += 1;
+    if (ok) {
+        double fac = (maxrel > 0.0) ? pol.rel_target / maxrel : pol.grow_max;
+        if (fac > pol.grow_max) fac = pol.grow_max;
+        if (fac < pol.shrink_min) fac = pol.shrink_min;
+        double dn = dt * fac;
+        ctl->dt_next = (dn > pol.dt_max) ? pol.dt_max : dn;
+        ctl->accepted = 1;
+        ctl->n_acc += 1;
+        ctl->t += dt;
+        if (dt >= pol.ss_dt && maxrel < pol.ss_tol) {
+            ctl->converged = 1;
+            ctl->finished = 1;
+        }
+    } else {
+        ctl->dt_next = 0.5 * dt;
+        ctl->accepted = 0;
+        ctl->n_neg = 0;
+        ctl->n_rej += 1;
+        if (ctl->err_timeout) { ctl->status = XK_ETIMEOUT; ctl->finished = 1; }
+        else if (ctl->dt_next < pol.dt_min) { ctl->status = XK_ENEG; ctl->finished = 1; }
+    }
+    ctl->dt = ctl->dt_next;
+}
+
+// n <- max(n + delta, 0) on an accepted step (reads the decision of this step).
+__global__ void k_apply(Col c, Ctl *ctl)
+{
+    if (!ctl->accepted) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.S) return;
+    double nn = c.n[idx] + c.delta[idx];
+    c.n[idx] = nn < 0.0 ? 0.0 : nn;
+}
+
+__global__ void k_set_mixing(Col c, const double *f, double *n)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.S) return;
+    n[idx] = f[idx] * c.ngas[idx / c.S];
+}
+
+}  // namespace
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+void launch_set_mixing(const Col &c, const double *f, double *n, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_set_mixing<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, f, n); }
+}
+
+// ---------------------------------------------------------------------------
+void launch_grid(const Col &c, cudaStream_t st)
+{
+    count_launches(1); k_grid<<<1, 256, 0, st>>>(c);
+    if (c.L > 1) { count_launches(1); k_transport<<<nblocks((long long)(c.L - 1) * c.S), kThreads, 0, st>>>(c); }
+}
+
+void launch_thermo(const Col &c, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_gibbs<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c); }
+}
+
+void launch_rates(const Col &c, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_gibbs<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c); }
+    if (((long long)c.L * c.R) > 0) { count_launches(1); k_rates<<<nblocks((long long)c.L * c.R), kThreads, 0, st>>>(c); }
+}
+
+void launch_photolysis(const Col &c, const double *n, cudaStream_t st)
+{
+    if (c.Rph == 0) return;
+    if (c.W > 0) {
+        if (((long long)c.L * c.W) > 0) { count_launches(1); k_photo_alpha<<<nblocks((long long)c.L * c.W), kThreads, 0, st>>>(c, n); }
+        if ((c.W) > 0) { count_launches(1); k_photo_J<<<nblocks(c.W, 128), 128, 0, st>>>(c); }
+    }
+    if (((long long)c.L * c.Rph * 32) > 0) { count_launches(1); k_photo_k<<<nblocks((long long)c.L * c.Rph * 32), kThreads, 0, st>>>(c); }
+}
+
+void launch_reaction_terms(const Col &c, const double *n, cudaStream_t st)
+{
+    if (((long long)c.L * c.R) > 0) { count_launches(1); k_reaction_terms<<<nblocks((long long)c.L * c.R), kThreads, 0, st>>>(c, n); }
+}
+
+void launch_residual(const Col &c, const double *n, double *F, const Ctl *ctl, double f_floor, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_residual<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, n, F, ctl, f_floor); }
+}
+
+static size_t jac_smem(const Col &c, int wpb)
+{
+    return (size_t)wpb * ((size_t)(c.S + 64) * sizeof(double));
+}
+
+void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_override, int scaled,
+                       double *A, double *lo, double *up, cudaStream_t st)
+{
+    const int wpb = 4;
+    size_t sm = jac_smem(c, wpb);
+    cudaFuncSetAttribute(k_jacobian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr); }
+}
+
+void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
+                       cudaStream_t st)
+{
+    const int wpb = 4;
+    size_t sm = jac_smem(c, wpb);
+    cudaFuncSetAttribute(k_jacobian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag); }
+}
+
+void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
+               cudaStream_t st)
+{
+    if (((long long)c.L * c.S * 32) > 0) { count_launches(1); k_jv<<<nblocks((long long)c.L * c.S * 32), kThreads, 0, st>>>(c, ctl, xs, ys, rowdiv, skip); }
+}
+
+void launch_rowdiv(long long N, const double *x, const double *d, double *y, cudaStream_t st)
+{
+    if (N > 0) { count_launches(1); k_rowdiv<<<nblocks(N), kThreads, 0, st>>>(N, x, d, y); }
+}
+
+void launch_unscale(const Col &c, const double *xs, double *delta, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_unscale<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, xs, delta); }
+}
+
+void launch_check(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_check<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, ctl, pol); }
+}
+
+void launch_decide(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st)
+{
+    (void)c;
+    count_launches(1); k_decide<<<1, 1, 0, st>>>(ctl, pol);
+}
+
+void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st)
+{
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_apply<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, ctl); }
+}
+
+void launch_begin(Ctl *ctl, cudaStream_t st)
+{
+    count_launches(1);
+    k_begin<<<1, 1, 0, st>>>(ctl);
+}
+
+}  // namespace xk

@@ -1,0 +1,113 @@
+// Internal structures shared by the libxk translation units (CUDA path only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/xk.h"
+
+namespace xk {
+
+// number of kernels this library has launched (all contexts), for reporting
+void count_launches(long long n);
+long long launches();
+
+constexpr double kBoltz = 1.380649e-16;       // erg / K
+constexpr double kAmu = 1.66053906660e-24;    // g
+constexpr double kP0 = 1.0e6;                 // 1 bar in dyn / cm^2
+constexpr double kBarToCgs = 1.0e6;
+
+// Device-side view of one column: network, photolysis and atmosphere inputs,
+// derived grid/transport arrays, per-step buffers.  All pointers are device
+// pointers inside the caller-provided workspace.
+struct Col {
+    int S, E, R, L, W, Rph, Sabs;
+    int ld;               // leading dimension of a dense S x S block (elements)
+    // network
+    const double *mass, *nasa, *dcoef, *arr, *troe;
+    const int *rtype, *reac, *prod, *form, *prow;
+    // species-major stoichiometry (residual gather): entries r * 16 + (nu + 8)
+    const int *yp, *yent;
+    // row-major Jacobian pattern: per row i, entries (j, coeff) and (r, slot)
+    const int *jp, *jcol, *jrs;
+    // photolysis
+    const double *J0, *dlam, *sigma, *sig_abs;   // sig_abs: Sabs x W
+    const int *abs_sp;
+    double mu, tf;
+    // atmosphere
+    const double *P, *T, *Kzz;
+    double g, mbar, alpha_T;
+    // derived on the device
+    double *ngas, *z, *dz, *dzi, *u, *v;
+    // per step
+    double *grt, *lnkc, *kf, *kr, *kph, *alpha, *Jw, *w, *d;
+    double *n, *F, *s, *b, *x, *delta, *tmp;
+};
+
+// Device control block: step-size state, decisions and counters.
+struct Ctl {
+    double dt, t, max_rel, dt_next, last_dt;
+    unsigned long long max_rel_bits;
+    int bad;              // non-finite or too negative
+    int n_neg;
+    int accepted, converged, status, finished;
+    int steps, n_acc, n_rej;
+    int solver_iters;
+    double solver_resid;
+    long long total_iters;
+    int err_timeout;      // a bounded wait gave up
+    int err_singular;     // zero pivot met
+};
+
+struct Policy {
+    double dt_max, rel_reject, rel_target, grow_max, shrink_min, neg_tol, f_floor, dt_min, ss_dt, ss_tol;
+};
+
+// Launch helpers implemented in xk_chem.cu
+void launch_grid(const Col &c, cudaStream_t st);
+void launch_thermo(const Col &c, cudaStream_t st);
+void launch_rates(const Col &c, cudaStream_t st);
+void launch_photolysis(const Col &c, const double *n, cudaStream_t st);
+void launch_reaction_terms(const Col &c, const double *n, cudaStream_t st);
+void launch_residual(const Col &c, const double *n, double *F, const Ctl *ctl, double f_floor, cudaStream_t st);
+void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_override, int scaled,
+                       double *A, double *lo, double *up, cudaStream_t st);
+void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
+                       cudaStream_t st);
+void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
+               cudaStream_t st);
+void launch_rowdiv(long long N, const double *x, const double *d, double *y, cudaStream_t st);
+void launch_check(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st);
+void launch_decide(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st);
+void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st);
+void launch_unscale(const Col &c, const double *xs, double *delta, cudaStream_t st);
+void launch_begin(Ctl *ctl, cudaStream_t st);
+void launch_set_mixing(const Col &c, const double *f, double *n, cudaStream_t st);
+
+// Block-Thomas factorization and solve (xk_factor.cu)
+struct FactorPlan {
+    int nb;          // panel width
+    int ctas;        // persistent CTAs
+    int threads;
+    size_t smem;
+};
+template <typename T>
+struct BlockSys {
+    T *D;            // [L][S][ld] diagonal blocks, overwritten by their inverses (row-pivoted form)
+    const T *lo, *up;
+    int *ridx;       // [L][S] row origin after pivoting
+    int *sig;        // [L][S] inverse of ridx
+    int *pinfo;      // panel scratch: [1 + 4 * nb]
+    unsigned *bar;   // grid barrier: [2]
+    int L, S, ld;
+};
+int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPlan *out);
+template <typename T>
+cudaError_t launch_factor(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
+                         double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,
+                         const int *skip = nullptr);
+size_t barrier_words();
+
+}  // namespace xk

@@ -1,0 +1,293 @@
+"""Thin Python binding of libxk (ctypes).  Argument marshalling only: every
+row of the implicit step runs in the library's CUDA kernels.  PyTorch supplies
+device memory (the workspace and the caller's buffers) and the stream.
+
+The functions keep the C names without the ``xk_`` prefix where they are
+methods of :class:`Column`; the raw C functions are reachable through
+:func:`lib`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+XK_OK = 0
+ERRORS = {-1: "XK_EINVAL", -2: "XK_ENOMEM", -3: "XK_ENOCONV", -4: "XK_ENEG", -5: "XK_ECUDA",
+          -6: "XK_ESINGULAR", -7: "XK_ETIMEOUT"}
+PREC = {"fp64": 0, "mixed": 1}
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+        ("dt_max", C.c_double), ("rel_reject", C.c_double), ("rel_target", C.c_double),
+        ("grow_max", C.c_double), ("shrink_min", C.c_double), ("neg_tol", C.c_double),
+        ("f_floor", C.c_double), ("dt_min", C.c_double), ("ss_dt", C.c_double), ("ss_tol", C.c_double),
+        ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int), ("gmres_tol", C.c_double),
+        ("panel_width", C.c_int), ("factor_ctas", C.c_int),
+    ]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("accepted", C.c_int), ("dt_used", C.c_double), ("dt_next", C.c_double),
+                ("max_rel", C.c_double), ("n_neg", C.c_int), ("converged", C.c_int),
+                ("solver_iters", C.c_int), ("solver_resid", C.c_double)]
+
+
+class RunInfo(C.Structure):
+    _fields_ = [("converged", C.c_int), ("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int),
+                ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double), ("solver_iters", C.c_longlong)]
+
+
+class XkError(RuntimeError):
+    def __init__(self, where, code, msg):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+# name -> (restype, argtypes); mirrors include/xk.h
+SIGNATURES = {
+    "xk_version": (C.c_int, []),
+    "xk_config_init": (C.c_int, [C.POINTER(Config)]),
+    "xk_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Config)]),
+    "xk_destroy": (C.c_int, [_vp]),
+    "xk_last_error": (C.c_char_p, [_vp]),
+    "xk_load_network": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _ip, _dp, _ip, _ip, _ip, _dp, _dp, _ip, _dp]),
+    "xk_load_photo": (C.c_int, [_vp, C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double]),
+    "xk_load_atmosphere": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double]),
+    "xk_workspace_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
+    "xk_set_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "xk_set_state": (C.c_int, [_vp, _vp, C.c_int]),
+    "xk_set_mixing_ratios": (C.c_int, [_vp, _vp, C.c_int]),
+    "xk_get_state": (C.c_int, [_vp, _vp, C.c_int]),
+    "xk_step": (C.c_int, [_vp, C.c_double, C.POINTER(StepInfo)]),
+    "xk_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(RunInfo)]),
+    "xk_eval_grid": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "xk_eval_thermo": (C.c_int, [_vp, _vp, _vp]),
+    "xk_eval_rates": (C.c_int, [_vp, _vp, _vp]),
+    "xk_eval_photolysis": (C.c_int, [_vp, _vp, _vp]),
+    "xk_eval_transport": (C.c_int, [_vp, _vp, _vp]),
+    "xk_eval_residual": (C.c_int, [_vp, _vp, _vp]),
+    "xk_eval_jacobian": (C.c_int, [_vp, _vp, C.c_double, _vp, _vp, _vp]),
+    "xk_block_solve": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "xk_step_delta": (C.c_int, [_vp, _vp, C.c_double, _vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "xk_profile": (C.c_int, [_vp, C.c_int]),
+    "xk_launch_count": (C.c_longlong, []),
+    "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
+}
+
+PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control"]
+
+
+def lib(build_if_missing=False):
+    """Load libxk.so; raises if it is not built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libxk is not built ({path}); run paper_2512_06729_gb300.build.build()")
+        l = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+    return _lib
+
+
+def default_config(**kw):
+    cfg = Config()
+    lib().xk_config_init(C.byref(cfg))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PREC[v]
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Column:
+    """One atmospheric column on one GPU: owns an xk context and its workspace."""
+
+    def __init__(self, prob, precision="fp64", device=0, stream=None, **cfg_kw):
+        import torch
+        self._torch = torch
+        self.prob = prob
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self.cfg = default_config(precision=precision, device=device, stream=stream.cuda_stream, **cfg_kw)
+        self.precision = precision
+        l = lib()
+        h = _vp()
+        rc = l.xk_create(C.byref(h), C.byref(self.cfg))
+        if rc != XK_OK:
+            raise XkError("xk_create", rc, "could not create context")
+        self.h = h
+        self.S, self.L, self.R = prob.S, prob.L, prob.R
+        self._keep = []
+        p = prob
+        d = lambda a: self._keep_arr(_np(a, np.float64)).ctypes.data_as(_dp)
+        i = lambda a: self._keep_arr(_np(a, np.int32)).ctypes.data_as(_ip)
+        self._call("xk_load_network", p.S, p.E, p.R, i(p.elem), d(p.mass), i(p.rtype), i(p.reac), i(p.prod),
+                   d(p.arr), d(p.troe), i(p.form), d(p.nasa))
+        W, Rph = p.W, p.Rph
+        if Rph > 0 or W > 0:
+            one = np.zeros(1)
+            self._call("xk_load_photo", W, Rph, i(p.prow), d(p.lam if W else one), d(p.dlam if W else one),
+                       d(p.J0 if W else one), d(p.sigma if p.sigma.size else one),
+                       d(p.sigma_abs if p.sigma_abs.size else one), float(p.mu), float(p.tf))
+        self._call("xk_load_atmosphere", p.L, d(p.P_bar), d(p.T), d(p.Kzz), d(p.dcoef), float(p.g),
+                   float(p.mbar), float(p.alpha_T))
+        nbytes = C.c_size_t()
+        self._call("xk_workspace_bytes", C.byref(nbytes))
+        self.workspace_bytes = int(nbytes.value)
+        self.ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        aligned = (base + 255) & ~255
+        self._call("xk_set_workspace", _vp(aligned), C.c_size_t(self.workspace_bytes))
+        self._keep = []
+
+    def _keep_arr(self, a):
+        self._keep.append(a)
+        return a
+
+    def _call(self, name, *args):
+        rc = getattr(lib(), name)(self.h, *args)
+        if rc != XK_OK:
+            msg = lib().xk_last_error(self.h)
+            raise XkError(name, rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().xk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -----------------------------------------------------------
+    def _dev(self, *shape):
+        return self._torch.empty(*shape, dtype=self._torch.float64, device=self.device)
+
+    def _ptr(self, t):
+        assert t.is_cuda and t.is_contiguous() and t.dtype == self._torch.float64
+        return _vp(t.data_ptr())
+
+    # -- state ---------------------------------------------------------------
+    def set_mixing_ratios(self, f):
+        t = self._torch.as_tensor(_np(f, np.float64), device=self.device).contiguous()
+        self._call("xk_set_mixing_ratios", self._ptr(t), 1)
+
+    def set_state(self, n):
+        if isinstance(n, np.ndarray):
+            a = _np(n, np.float64)
+            self._call("xk_set_state", _vp(a.ctypes.data), 0)
+        else:
+            self._call("xk_set_state", self._ptr(n.contiguous()), 1)
+
+    def get_state(self, device=False):
+        if device:
+            out = self._dev(self.L, self.S)
+            self._call("xk_get_state", self._ptr(out), 1)
+            return out
+        out = np.zeros((self.L, self.S))
+        self._call("xk_get_state", _vp(out.ctypes.data), 0)
+        return out
+
+    def step(self, dt=0.0):
+        info = StepInfo()
+        self._call("xk_step", float(dt), C.byref(info))
+        return info
+
+    def run_to_steady(self, dt0=1e-8, max_steps=5000, raise_on_noconv=False):
+        info = RunInfo()
+        rc = lib().xk_run_to_steady(self.h, float(dt0), int(max_steps), C.byref(info))
+        if rc != XK_OK and (raise_on_noconv or rc != -3):
+            msg = lib().xk_last_error(self.h)
+            raise XkError("xk_run_to_steady", rc, msg.decode() if msg else "")
+        return info
+
+    # -- rows ----------------------------------------------------------------
+    def eval_grid(self):
+        L = self.L
+        ng, z, dz, dzi = self._dev(L), self._dev(L), self._dev(L), self._dev(max(L - 1, 1))
+        self._call("xk_eval_grid", self._ptr(ng), self._ptr(z), self._ptr(dz), self._ptr(dzi))
+        return ng, z, dz, dzi[: L - 1]
+
+    def eval_thermo(self):
+        grt, lnkc = self._dev(self.L, self.S), self._dev(self.L, self.R)
+        self._call("xk_eval_thermo", self._ptr(grt), self._ptr(lnkc))
+        return grt, lnkc
+
+    def eval_rates(self):
+        kf, kr = self._dev(self.L, self.R), self._dev(self.L, self.R)
+        self._call("xk_eval_rates", self._ptr(kf), self._ptr(kr))
+        return kf, kr
+
+    def eval_photolysis(self, n):
+        kph = self._dev(self.L, max(self.prob.Rph, 1))
+        self._call("xk_eval_photolysis", self._ptr(n.contiguous()), self._ptr(kph))
+        return kph[:, : self.prob.Rph]
+
+    def eval_transport(self):
+        m = max(self.L - 1, 1)
+        u, v = self._dev(m, self.S), self._dev(m, self.S)
+        self._call("xk_eval_transport", self._ptr(u), self._ptr(v))
+        return u[: self.L - 1], v[: self.L - 1]
+
+    def eval_residual(self, n):
+        F = self._dev(self.L, self.S)
+        self._call("xk_eval_residual", self._ptr(n.contiguous()), self._ptr(F))
+        return F
+
+    def eval_jacobian(self, n, dt):
+        A = self._dev(self.L, self.S, self.S)
+        lo, up = self._dev(self.L, self.S), self._dev(self.L, self.S)
+        self._call("xk_eval_jacobian", self._ptr(n.contiguous()), float(dt), self._ptr(A), self._ptr(lo), self._ptr(up))
+        return A, lo, up
+
+    def block_solve(self, A, lo, up, f):
+        x = self._dev(self.L, self.S)
+        self._call("xk_block_solve", self._ptr(A.contiguous()), self._ptr(lo.contiguous()),
+                   self._ptr(up.contiguous()), self._ptr(f.contiguous()), self._ptr(x))
+        return x
+
+    @staticmethod
+    def lib_launches():
+        return int(lib().xk_launch_count())
+
+    def profile(self, enable=True):
+        self._call("xk_profile", 1 if enable else 0)
+
+    def profile_read(self):
+        ms = (C.c_double * len(PHASES))()
+        calls = (C.c_longlong * len(PHASES))()
+        self._call("xk_profile_read", ms, calls, len(PHASES))
+        return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+
+    def step_delta(self, n, dt):
+        d = self._dev(self.L, self.S)
+        it = C.c_int()
+        res = C.c_double()
+        self._call("xk_step_delta", self._ptr(n.contiguous()), float(dt), self._ptr(d), C.byref(it), C.byref(res))
+        return d, int(it.value), float(res.value)

@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Every row of the implicit step is compared element by element on seeded
+inputs: grid, Gibbs energies and ln K_c, rate coefficients, photolysis rates,
+transport coefficients, residual, Jacobian blocks, the block-tridiagonal
+solve, single linear steps in both precision modes, controlled step
+sequences and runs to steady state.
+
+Tolerances (FP64 everywhere except the mixed-precision factorization):
+  - quantities computed by the same formula in the same order: 1e-12 relative
+    (CUDA exp/log/pow are within 1-2 ulp of the host libm);
+  - rate coefficients: 1e-11 relative (exp(-ln K_c) amplifies the ulp error of
+    ln K_c, |ln K_c| < 100);
+  - residual: 1e-10 of the gross production + loss of each species (F is a
+    sum with cancellation);
+  - linear steps: 1e-6 of max(n, 1e-20 n_gas) (condition numbers of 1e10 to
+    1e16 turn 1e-16 roundoff into this; the two sides pivot differently);
+  - end states of runs: 1e-6 relative on species above 1e-20 mixing ratio.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import Oracle, default_policy
+from paper_2512_06729_gb300 import synth
+from tests.helpers import full_matrix
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2512_06729_gb300 import build as xkbuild  # noqa: E402
+from paper_2512_06729_gb300 import xk  # noqa: E402
+
+xkbuild.build()
+
+
+def cpu(t):
+    return t.detach().cpu().numpy()
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float64), device="cuda")
+
+
+PROBLEMS = {
+    "tiny": lambda: synth.tiny_column(),
+    "small": lambda: synth.small_column(),
+    "chons": lambda: synth.chons_column(),
+}
+
+
+@pytest.fixture(scope="module", params=list(PROBLEMS))
+def pair(request):
+    p = PROBLEMS[request.param]()
+    return p, Oracle(p), xk.Column(p, "fp64")
+
+
+def relerr(a, b, floor=0.0):
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), floor)) if a.size else 0.0
+
+
+def test_grid(pair):
+    p, o, c = pair
+    ng, z, dz, dzi = (cpu(t) for t in c.eval_grid())
+    ong, oz, odz, odzi = o.grid()
+    assert relerr(ng, ong) < 1e-14
+    np.testing.assert_allclose(z, oz, rtol=1e-12, atol=1e-9 * oz.max())
+    np.testing.assert_allclose(dz, odz, rtol=1e-11)
+    np.testing.assert_allclose(dzi, odzi, rtol=1e-11)
+
+
+def test_thermo_and_rates(pair):
+    p, o, c = pair
+    grt, lnkc = (cpu(t) for t in c.eval_thermo())
+    ogrt, olnkc = o.thermo()
+    assert np.max(np.abs(grt - ogrt) / np.maximum(np.abs(ogrt), 1.0)) < 1e-12
+    assert np.max(np.abs(lnkc - olnkc) / np.maximum(np.abs(olnkc), 1.0)) < 1e-12
+    kf, kr = (cpu(t) for t in c.eval_rates())
+    okf, okr = o.rate_coefficients()
+    assert relerr(kf, okf, 1e-300) < 1e-11
+    assert relerr(kr, okr, 1e-300) < 1e-11
+
+
+def test_photolysis(pair):
+    p, o, c = pair
+    if p.Rph == 0:
+        pytest.skip("no photolysis in this network")
+    n = o.initial_state()
+    kph = cpu(c.eval_photolysis(dev(n)))
+    assert relerr(kph, o.photolysis(n), 1e-300) < 1e-12
+
+
+def test_transport(pair):
+    p, o, c = pair
+    u, v = (cpu(t) for t in c.eval_transport())
+    ou, ov = o.transport()
+    assert relerr(u, ou, 1e-300) < 1e-11
+    assert relerr(v, ov, 1e-300) < 1e-11
+
+
+def _gross(p, o, n):
+    """Sum over reactions of |nu| (w_f + w_b) per species: the scale of F's cancellation."""
+    kf, kr = o.rate_coefficients()
+    kph = o.photolysis(n)
+    L, S = n.shape
+    g = np.zeros((L, S))
+    for r in range(p.R):
+        if p.rtype[r] == 2:
+            f = kph[:, p.prow[r]].copy(); b = np.zeros(L)
+        else:
+            f = kf[:, r].copy(); b = kr[:, r].copy()
+        for s in range(3):
+            if p.reac[r, s] >= 0: f = f * n[:, p.reac[r, s]]
+            if p.prod[r, s] >= 0: b = b * n[:, p.prod[r, s]]
+        for s in range(3):
+            for sp in (p.reac[r, s], p.prod[r, s]):
+                if sp >= 0: g[:, sp] += np.abs(f) + np.abs(b)
+    # transport: the four flux terms of each layer
+    if L > 1:
+        u, v = o.transport()
+        dz = o.grid()[2]
+        t = np.zeros((L, S))
+        t[:-1] += np.abs(u * n[:-1]) + np.abs(v * n[1:])
+        t[1:] += np.abs(u * n[:-1]) + np.abs(v * n[1:])
+        g += t / dz[:, None]
+    return g
+
+
+def test_residual(pair):
+    p, o, c = pair
+    n = o.initial_state()
+    F = cpu(c.eval_residual(dev(n)))
+    oF = o.residual(n)
+    gross = _gross(p, o, n) + np.abs(oF) + 1e-300
+    assert np.max(np.abs(F - oF) / gross) < 1e-10
+
+
+def test_jacobian(pair):
+    p, o, c = pair
+    n = o.initial_state()
+    for dt in (1e-3, 1e6):
+        A, lo, up = (cpu(t) for t in c.eval_jacobian(dev(n), dt))
+        oA, olo, oup = o.jacobian(n, dt)
+        scale = np.abs(oA).max(axis=2, keepdims=True) + 1e-300
+        assert np.max(np.abs(A - oA) / scale) < 1e-12
+        np.testing.assert_allclose(lo, olo, rtol=1e-11, atol=0)
+        np.testing.assert_allclose(up, oup, rtol=1e-11, atol=0)
+
+
+def test_block_solve_matches_oracle(pair):
+    p, o, c = pair
+    n = o.initial_state()
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=n.shape) * n
+    for dt in (1e-6, 1e-2):
+        oA, olo, oup = o.jacobian(n, dt)
+        x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(f)))
+        ox = o.block_solve(oA, olo, oup, f)
+        scale = np.abs(ox).max() + 1e-300
+        assert np.max(np.abs(x - ox)) / scale < 1e-10
+
+
+def test_block_solve_late_state_large_dt(pair):
+    """Near steady state at dt = dt_max = 1e8 s the block system has condition
+    numbers near 1e16, so two FP64 solvers that pivot differently (scaled
+    explicit inverses here, unscaled LU in the oracle) can differ by up to
+    kappa * eps ~ 1e-4 of the solution in the ill-determined directions; the
+    bound below is that.  Trajectory parity over many such steps is checked
+    separately (the backward-Euler map contracts those differences)."""
+    p, o, c = pair
+    if p.L * p.S > 4000:
+        pytest.skip("late state is prepared only for the small columns")
+    ng = o.grid()[0]
+    n, _ = o.run_to_steady(o.initial_state(), max_steps=400)
+    oA, olo, oup = o.jacobian(n, 1e8)
+    f = o.residual(n)
+    x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(f)))
+    ox = o.block_solve(oA, olo, oup, f)
+    s = np.maximum(n, 1e-20 * ng[:, None])
+    assert np.max(np.abs(x - ox) / s) < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_delta(precision):
+    p = synth.small_column()
+    o = Oracle(p)
+    c = xk.Column(p, precision)
+    ng = o.grid()[0]
+    n = o.initial_state()
+    for dt in (1e-6, 1e-2, 1e2):
+        d, iters, res = c.step_delta(dev(n), dt)
+        d = cpu(d)
+        od = o.step_delta(n, dt)
+        s = np.maximum(n, 1e-20 * ng[:, None])
+        err = np.max(np.abs(d - od) / s)
+        assert err < 1e-6, (precision, dt, err, iters, res)
+
+
+def test_controlled_steps_follow_the_oracle():
+    p = synth.tiny_column()
+    o = Oracle(p)
+    c = xk.Column(p, "fp64")
+    ng = o.grid()[0]
+    n = o.initial_state()
+    c.set_mixing_ratios(p.f0)
+    np.testing.assert_allclose(c.get_state(), n, rtol=1e-15)
+    dt = 1e-8
+    pol = default_policy()
+    for it in range(60):
+        info = c.step(dt)
+        n, oinfo = o.step(n, dt, pol)
+        assert info.accepted == oinfo.accepted
+        assert info.dt_next == pytest.approx(oinfo.dt_next, rel=1e-6)
+        m = c.get_state()
+        s = np.maximum(n, 1e-20 * ng[:, None])
+        assert np.max(np.abs(m - n) / s) < 1e-8
+        dt = oinfo.dt_next
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fixed_schedule_trajectory(precision):
+    """A prescribed dt schedule from 1e-8 s to 1e8 s with every step accepted:
+    both sides apply the same map n <- max(n + delta(n, dt), 0), so the states
+    stay together step after step."""
+    p = synth.tiny_column()
+    o = Oracle(p)
+    ng = o.grid()[0]
+    loose = dict(rel_reject=1e300, neg_tol=1e300, dt_max=1e8)
+    pol = default_policy(**loose)
+    c = xk.Column(p, precision, **loose)
+    c.set_mixing_ratios(p.f0)
+    n = o.initial_state()
+    dts = list(np.geomspace(1e-8, 1e8, 120)) + [1e8] * 80
+    worst = 0.0
+    for dt in dts:
+        info = c.step(dt)
+        n, oinfo = o.step(n, dt, pol)
+        assert info.accepted == 1 and oinfo.accepted == 1
+        m = c.get_state()
+        mask = n > 1e-20 * ng[:, None]
+        worst = max(worst, float(np.max(np.abs(m[mask] - n[mask]) / n[mask])))
+    assert worst <= 1e-6, worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_run_to_steady_matches_oracle(precision):
+    """Adaptive run to the steady-state test on the 40-species column; both
+    sides reach the same state within 1e-6 on species above 1e-20."""
+    p = synth.small_column()
+    o = Oracle(p)
+    ng = o.grid()[0]
+    on, oinfo = o.run_to_steady(o.initial_state(), dt0=1e-8, max_steps=6000)
+    assert oinfo.converged
+    c = xk.Column(p, precision)
+    c.set_mixing_ratios(p.f0)
+    info = c.run_to_steady(1e-8, 6000)
+    assert info.converged
+    n = c.get_state()
+    mask = on > 1e-20 * ng[:, None]
+    err = np.max(np.abs(n[mask] - on[mask]) / on[mask])
+    assert err <= 1e-6, (err, info.steps, oinfo.steps)
+
+
+def test_single_layer_and_no_photolysis_edge_cases():
+    p = synth.tiny_column()
+    p1 = p.replace(P_bar=p.P_bar[:1], T=p.T[:1], Kzz=p.Kzz[:1], f0=p.f0[:1])
+    o = Oracle(p1)
+    c = xk.Column(p1, "fp64")
+    n = o.initial_state()
+    d, _, _ = c.step_delta(dev(n), 1e-4)
+    np.testing.assert_allclose(cpu(d), o.step_delta(n, 1e-4), rtol=1e-9, atol=1e-12 * n.max())
+    F = cpu(c.eval_residual(dev(n)))
+    oF = o.residual(n)
+    assert np.max(np.abs(F - oF) / (_gross(p1, o, n) + 1e-300)) < 1e-10
+
+
+def test_invalid_inputs_raise():
+    p = synth.tiny_column()
+    bad = p.replace(reac=p.reac.copy())
+    bad.reac[3, 0] = p.S + 5
+    with pytest.raises(xk.XkError):
+        xk.Column(bad, "fp64")
+    bad = p.replace(P_bar=p.P_bar[::-1].copy())
+    with pytest.raises(xk.XkError):
+        xk.Column(bad, "fp64")
