@@ -52,7 +52,9 @@ extern "C" {
 #define XK_ETIMEOUT (-7)  /* a bounded device-side wait gave up */
 
 #define XK_PREC_FP64 0    /* FP64 block LU (plain path) */
-#define XK_PREC_MIXED 1   /* FP32 block LU as preconditioner + FP64 GMRES refinement */
+#define XK_PREC_MIXED 1   /* FP32 block LU as preconditioner + FP64 GMRES refinement; a step whose
+                             GMRES does not reach gmres_tol within gmres_max_iter is re-solved with
+                             the FP64 block LU, and so is every later step at that dt or above */
 
 #define XK_RX_TWO_BODY 0
 #define XK_RX_THREE_BODY 1
@@ -90,12 +92,14 @@ typedef struct {
     int converged;        /* steady-state test passed on this step */
     int solver_iters;     /* FGMRES iterations (mixed) or 0 */
     double solver_resid;  /* final relative residual (mixed) or 0 */
+    int used_fp64;        /* mixed mode: this step was solved by the FP64 factorization */
 } xk_step_info;
 
 typedef struct {
     int converged, steps, accepted, rejected;
     double t, dt, max_rel;
     long long solver_iters;   /* total FGMRES iterations */
+    long long fp64_steps;     /* mixed mode: steps solved by the FP64 factorization */
 } xk_run_info;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -103,7 +107,7 @@ XK_API int xk_version(void);
 
 /* Fill cfg with the default policy: FP64, dt_max 1e8 s, rel_reject 1.0,
  * rel_target 0.5, grow 3, shrink 0.5, neg_tol 1e-12, f_floor 1e-20,
- * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 120 iterations, 1e-12. */
+ * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 40 iterations, 1e-14. */
 XK_API int xk_config_init(xk_config *cfg);
 
 /* Create a context for one atmospheric column on cfg->device.  *out is set
@@ -183,12 +187,13 @@ XK_API int xk_eval_residual(xk_ctx *ctx, const double *n, double *F);
 /* I/dt - dF/dn: A [L*S*S], lo [L*S], up [L*S] (device). */
 XK_API int xk_eval_jacobian(xk_ctx *ctx, const double *n, double dt, double *A, double *lo, double *up);
 /* Solve the block-tridiagonal system given by A, lo, up (device, FP64) for
- * right-hand side f, writing x (device).  A is not modified.  Uses the
- * context's FP64 factorization kernels and workspace. */
+ * right-hand side f, writing x (device).  A is not modified.  Uses the FP64
+ * factorization kernels and the context's workspace (either mode). */
 XK_API int xk_block_solve(xk_ctx *ctx, const double *A, const double *lo, const double *up,
                    const double *f, double *x);
 /* delta solving (I/dt - J(n)) delta = F(n) with the context's precision
- * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed). */
+ * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed;
+ * *iters = -1 when the FP64 fallback solved the step). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
 
 /* ---- tracing: CUDA events around each phase of every step ----

@@ -45,7 +45,8 @@ struct xk_ctx {
     double *rowd = nullptr, *bhat = nullptr;   // row equilibration: diagonal of I/dt - J, scaled right-hand side
     unsigned *counter = nullptr;
     GmState *gm = nullptr;
-    FactorPlan plan{};
+    FactorPlan plan{};     // plan of the context's precision
+    FactorPlan plan64{};   // FP64 plan (fallback of the mixed path)
     bool ready = false;
     // tracing
     bool prof = false;
@@ -219,16 +220,17 @@ size_t layout(xk_ctx *c, char *base)
     t.x = b.take<double>(LS); t.delta = b.take<double>(LS); t.tmp = b.take<double>(LS);
     k = t;
     c->gsol = b.take<double>(LS);
+    // FP64 blocks in both modes: the mixed path falls back to them when the
+    // FP32-preconditioned solve does not converge
+    c->A64 = b.take<double>((size_t)L * S * ld);
+    c->lo64 = b.take<double>(LS);
+    c->up64 = b.take<double>(LS);
     if (c->cfg.precision == XK_PREC_FP64) {
-        c->A64 = b.take<double>((size_t)L * S * ld);
-        c->lo64 = b.take<double>(LS);
-        c->up64 = b.take<double>(LS);
         c->A32 = nullptr; c->lo32 = nullptr; c->up32 = nullptr;
     } else {
         c->A32 = b.take<float>((size_t)L * S * ld);
         c->lo32 = b.take<float>(LS);
         c->up32 = b.take<float>(LS);
-        c->A64 = nullptr; c->lo64 = nullptr; c->up64 = nullptr;
         int m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
         c->V = b.take<double>((size_t)(m + 1) * LS);
         c->Z = b.take<double>((size_t)m * LS);
@@ -301,13 +303,15 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     } else {
         if (dt_override > 0.0) return fail(c, XK_EINVAL, "mixed path reads dt from the control block");
+        launch_route(ctl, st);
+        const int *skip32 = &ctl->skip32;
         {
             PhaseMark m(c, XK_PH_JACOBIAN);
-            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, c->rowd, st);
+            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, c->rowd, st, skip32);
             // equations divided by their diagonal: residuals in units of relative change per species
             launch_rowdiv((long long)c->L * c->S, col.b, c->rowd, c->bhat, st);
         }
-        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<float>(sys32(c), c->plan, ctl, st); }
+        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<float>(sys32(c), c->plan, ctl, st, skip32); }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
         GmArgs a;
         a.N = (long long)c->L * c->S;
@@ -327,6 +331,16 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
             launch_solve<float>(s32, plan, v, z, gsol, ctl, s, rowd, skip);
         };
         { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
+        // FP64 fallback, gated on the device by ctl->skip64
+        const int *skip64 = &ctl->skip64;
+        { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, 0.0, 1, c->A64, c->lo64, c->up64, st, skip64); }
+        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan64, ctl, st, skip64); }
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+        {
+            PhaseMark m(c, XK_PH_SOLVE);
+            e = launch_solve<double>(sys64(c), c->plan64, col.b, col.x, c->gsol, ctl, st, nullptr, skip64);
+        }
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     }
     launch_unscale(col, col.x, delta_out, st);
     return cuda_check(c, "step enqueue");
@@ -371,7 +385,7 @@ int xk_config_init(xk_config *cfg)
     cfg->stream = nullptr;
     cfg->dt_max = 1e8; cfg->rel_reject = 1.0; cfg->rel_target = 0.5; cfg->grow_max = 3.0; cfg->shrink_min = 0.5;
     cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
-    cfg->gmres_restart = 30; cfg->gmres_max_iter = 120; cfg->gmres_tol = 1e-12;
+    cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-14;
     cfg->panel_width = 0; cfg->factor_ctas = 0;
     return XK_OK;
 }
@@ -539,6 +553,8 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
     if (factor_plan(c->S, sz, c->cfg.panel_width, c->cfg.factor_ctas, &c->plan) != 0)
         return fail(c, XK_EINVAL, "no factorization plan for S=%d (panel %d)", c->S, c->cfg.panel_width);
+    if (factor_plan(c->S, 8, 0, 0, &c->plan64) != 0)
+        return fail(c, XK_EINVAL, "no FP64 factorization plan for S=%d", c->S);
     Col &k = c->col;
     up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
     up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
@@ -552,6 +568,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     cudaMemsetAsync(c->col.n, 0, sizeof(double) * (size_t)c->L * c->S, c->st);
     Ctl init{};
     init.dt = 1e-8;
+    init.dt_fp64 = 1e300;
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
@@ -607,6 +624,7 @@ static void fill_step_info(const Ctl &h, xk_step_info *info)
     info->converged = h.converged;
     info->solver_iters = h.solver_iters;
     info->solver_resid = h.solver_resid;
+    info->used_fp64 = h.used_fp64;
 }
 
 int xk_step(xk_ctx *c, double dt, xk_step_info *info)
@@ -641,6 +659,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
     Ctl init{};
     init.dt = dt0 > 0.0 ? dt0 : h.dt;
     init.t = 0.0;
+    init.dt_fp64 = h.dt_fp64;
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     int enq = 0;
@@ -662,6 +681,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
         info->dt = h.dt;
         info->max_rel = h.max_rel;
         info->solver_iters = h.total_iters;
+        info->fp64_steps = h.fp64_steps;
     }
     if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
     if (h.status) return fail(c, h.status, "run stopped with status %d", h.status);
@@ -766,7 +786,6 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
 {
     int rc = need_ready(c);
     if (rc) return rc;
-    if (c->cfg.precision != XK_PREC_FP64) return fail(c, XK_EINVAL, "xk_block_solve needs an FP64 context");
     if (!A || !lo || !up || !f || !x) return fail(c, XK_EINVAL, "null pointer");
     const size_t S = c->S, L = c->L;
     cudaMemcpy2DAsync(c->A64, c->col.ld * 8, A, S * 8, S * 8, L * S, cudaMemcpyDeviceToDevice, c->st);
@@ -775,9 +794,9 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
     Ctl init{};
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
-    cudaError_t e = launch_factor<double>(sys64(c), c->plan, c->ctl_aux, c->st);
+    cudaError_t e = launch_factor<double>(sys64(c), c->plan64, c->ctl_aux, c->st);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-    e = launch_solve<double>(sys64(c), c->plan, f, x, c->gsol, c->ctl_aux, c->st);
+    e = launch_solve<double>(sys64(c), c->plan64, f, x, c->gsol, c->ctl_aux, c->st);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve"))) return rc;
@@ -793,13 +812,14 @@ int xk_step_delta(xk_ctx *c, const double *n, double dt, double *delta, int *ite
     if (!n || !delta || !(dt > 0)) return fail(c, XK_EINVAL, "bad argument");
     Ctl init{};
     init.dt = dt;
+    init.dt_fp64 = 1e300;
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     double dto = c->cfg.precision == XK_PREC_FP64 ? dt : 0.0;
     if ((rc = enqueue_linear_step(c, n, dto, delta, c->ctl_aux))) return rc;
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "step_delta"))) return rc;
-    if (iters) *iters = c->ctl_host->solver_iters;
+    if (iters) *iters = c->ctl_host->used_fp64 ? -1 : c->ctl_host->solver_iters;
     if (resid) *resid = c->ctl_host->solver_resid;
     if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
     if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");

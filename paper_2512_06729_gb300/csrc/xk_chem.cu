@@ -284,9 +284,9 @@ __global__ void k_residual(Col c, const double *n, double *F, const Ctl *ctl, do
 // diag(1/s) A diag(s) and the matching couplings.
 template <typename T>
 __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_override, int scaled,
-                           T *A, T *lo, T *up, double *dout)
+                           T *A, T *lo, T *up, double *dout, const int *skip)
 {
-    if (ctl && ctl->finished) return;
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
     extern __shared__ double sh[];
     int S = c.S, L = c.L;
     int wpb = blockDim.x >> 5;
@@ -432,6 +432,15 @@ __global__ void k_check(Col c, Ctl *ctl, Policy pol)
     }
 }
 
+// Mixed precision routing at the start of a step: steps at dt at or above the
+// smallest dt where the FP32-preconditioned solve failed go straight to FP64.
+__global__ void k_route(Ctl *ctl)
+{
+    ctl->skip32 = ctl->dt >= ctl->dt_fp64 ? 1 : 0;
+    ctl->skip64 = ctl->skip32 ? 0 : 1;
+    ctl->used_fp64 = ctl->skip32;
+}
+
 __global__ void k_begin(Ctl *ctl)
 {
     if (ctl->finished) {
@@ -439,6 +448,8 @@ __global__ void k_begin(Ctl *ctl)
         return;
     }
     ctl->max_rel_bits = 0ull;
+    ctl->solver_iters = 0;
+    ctl->solver_resid = 0.0;
     ctl->bad = 0;
     ctl->n_neg = 0;
     ctl->accepted = 0;
@@ -455,6 +466,7 @@ __global__ void k_decide(Ctl *ctl, Policy pol)
     ctl->max_rel = maxrel;
     ctl->last_dt = dt;
     ctl->steps += 1;
+    if (ctl->used_fp64) ctl->fp64_steps += 1;
     if (ok) {
         double fac = (maxrel > 0.0) ? pol.rel_target / maxrel : pol.grow_max;
         if (fac > pol.grow_max) fac = pol.grow_max;
@@ -551,21 +563,21 @@ static size_t jac_smem(const Col &c, int wpb)
 }
 
 void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_override, int scaled,
-                       double *A, double *lo, double *up, cudaStream_t st)
+                       double *A, double *lo, double *up, cudaStream_t st, const int *skip)
 {
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr, skip); }
 }
 
 void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
-                       cudaStream_t st)
+                       cudaStream_t st, const int *skip)
 {
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag, skip); }
 }
 
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
@@ -598,6 +610,12 @@ void launch_decide(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st)
 void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st)
 {
     if (((long long)c.L * c.S) > 0) { count_launches(1); k_apply<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, ctl); }
+}
+
+void launch_route(Ctl *ctl, cudaStream_t st)
+{
+    count_launches(1);
+    k_route<<<1, 1, 0, st>>>(ctl);
 }
 
 void launch_begin(Ctl *ctl, cudaStream_t st)

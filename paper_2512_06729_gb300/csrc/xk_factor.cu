@@ -223,9 +223,9 @@ __device__ void trailing_update(T *D, const int *pinfo, int S, int ld, int c0, i
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl *ctl)
+__global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl *ctl, const int *skip)
 {
-    if (ctl->finished) return;
+    if (ctl->finished || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = a.S, ld = a.ld, L = a.L;
     const long long gstride = (long long)gridDim.x * blockDim.x;
@@ -373,30 +373,33 @@ int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPl
 }
 
 template <typename T, int NB>
-static cudaError_t launch_factor_nb(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st)
+static cudaError_t launch_factor_nb(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
+                                    const int *skip)
 {
     auto fn = k_factor<T, NB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return e;
     BlockSys<T> a = sys;
-    void *args[] = {(void *)&a, (void *)&ctl};
+    void *args[] = {(void *)&a, (void *)&ctl, (void *)&skip};
     count_launches(1);
     return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.ctas), dim3(plan.threads), args, plan.smem, st);
 }
 
 template <>
-cudaError_t launch_factor<double>(const BlockSys<double> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st)
+cudaError_t launch_factor<double>(const BlockSys<double> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
+                                  const int *skip)
 {
-    if (plan.nb == 8) return launch_factor_nb<double, 8>(sys, plan, ctl, st);
-    if (plan.nb == 16) return launch_factor_nb<double, 16>(sys, plan, ctl, st);
+    if (plan.nb == 8) return launch_factor_nb<double, 8>(sys, plan, ctl, st, skip);
+    if (plan.nb == 16) return launch_factor_nb<double, 16>(sys, plan, ctl, st, skip);
     return cudaErrorInvalidValue;
 }
 
 template <>
-cudaError_t launch_factor<float>(const BlockSys<float> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st)
+cudaError_t launch_factor<float>(const BlockSys<float> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
+                                 const int *skip)
 {
-    if (plan.nb == 16) return launch_factor_nb<float, 16>(sys, plan, ctl, st);
-    if (plan.nb == 32) return launch_factor_nb<float, 32>(sys, plan, ctl, st);
+    if (plan.nb == 16) return launch_factor_nb<float, 16>(sys, plan, ctl, st, skip);
+    if (plan.nb == 32) return launch_factor_nb<float, 32>(sys, plan, ctl, st, skip);
     return cudaErrorInvalidValue;
 }
 

@@ -219,16 +219,22 @@ __global__ void k_zero(double *x, long long N)
 
 __global__ void k_gm_skip_if_finished(GmState *gm, const Ctl *ctl)
 {
-    if (ctl->finished) { gm->done = 1; gm->applied = 1; gm->idle = 1; }
+    if (ctl->finished || ctl->skip32) { gm->done = 1; gm->applied = 1; gm->idle = 1; }
 }
 
+// Record the solve; a solve that did not reach the tolerance hands the step to
+// the FP64 factorization, and so does every later step at this dt or above.
 __global__ void k_gm_report(const GmState *gm, Ctl *ctl)
 {
-    if (ctl->finished) return;
+    if (ctl->finished || ctl->skip32) return;
     ctl->solver_iters = gm->iters;
     ctl->solver_resid = gm->resid;
     ctl->total_iters += gm->iters;
-    if (gm->failed) ctl->bad = 1;
+    if (gm->failed || !(gm->resid <= gm->tol)) {
+        ctl->skip64 = 0;
+        ctl->used_fp64 = 1;
+        if (ctl->dt < ctl->dt_fp64) ctl->dt_fp64 = ctl->dt;
+    }
 }
 
 }  // namespace

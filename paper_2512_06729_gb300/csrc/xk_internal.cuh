@@ -57,6 +57,11 @@ struct Ctl {
     long long total_iters;
     int err_timeout;      // a bounded wait gave up
     int err_singular;     // zero pivot met
+    // mixed precision routing: skip32 = this step goes straight to FP64; skip64 = FP64 solve not needed
+    int skip32, skip64;
+    int used_fp64;        // this step was solved by the FP64 factorization
+    long long fp64_steps;
+    double dt_fp64;       // smallest dt at which the FP32-preconditioned solve did not converge
 };
 
 struct Policy {
@@ -71,9 +76,10 @@ void launch_photolysis(const Col &c, const double *n, cudaStream_t st);
 void launch_reaction_terms(const Col &c, const double *n, cudaStream_t st);
 void launch_residual(const Col &c, const double *n, double *F, const Ctl *ctl, double f_floor, cudaStream_t st);
 void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_override, int scaled,
-                       double *A, double *lo, double *up, cudaStream_t st);
+                       double *A, double *lo, double *up, cudaStream_t st, const int *skip = nullptr);
 void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
-                       cudaStream_t st);
+                       cudaStream_t st, const int *skip = nullptr);
+void launch_route(Ctl *ctl, cudaStream_t st);
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
                cudaStream_t st);
 void launch_rowdiv(long long N, const double *x, const double *d, double *y, cudaStream_t st);
@@ -103,7 +109,8 @@ struct BlockSys {
 };
 int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPlan *out);
 template <typename T>
-cudaError_t launch_factor(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st);
+cudaError_t launch_factor(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
+                          const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
                          double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,

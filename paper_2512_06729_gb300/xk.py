@@ -40,12 +40,13 @@ class Config(C.Structure):
 class StepInfo(C.Structure):
     _fields_ = [("accepted", C.c_int), ("dt_used", C.c_double), ("dt_next", C.c_double),
                 ("max_rel", C.c_double), ("n_neg", C.c_int), ("converged", C.c_int),
-                ("solver_iters", C.c_int), ("solver_resid", C.c_double)]
+                ("solver_iters", C.c_int), ("solver_resid", C.c_double), ("used_fp64", C.c_int)]
 
 
 class RunInfo(C.Structure):
     _fields_ = [("converged", C.c_int), ("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int),
-                ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double), ("solver_iters", C.c_longlong)]
+                ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double), ("solver_iters", C.c_longlong),
+                ("fp64_steps", C.c_longlong)]
 
 
 class XkError(RuntimeError):

@@ -42,7 +42,7 @@ def test_binding_covers_the_header():
 def test_config_defaults(libxk):
     cfg = xk.Config()
     assert libxk.xk_config_init(C.byref(cfg)) == 0
-    assert cfg.precision == 0 and cfg.dt_max == 1e8 and cfg.ss_tol == 1e-3 and cfg.gmres_restart == 30
+    assert cfg.precision == 0 and cfg.dt_max == 1e8 and cfg.ss_tol == 1e-3 and cfg.gmres_restart == 30 and cfg.gmres_max_iter == 40
     assert libxk.xk_version() >= 100
 
 
