@@ -196,6 +196,31 @@ XK_API int xk_block_solve(xk_ctx *ctx, const double *A, const double *lo, const 
  * *iters = -1 when the FP64 fallback solved the step). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
 
+/* ---- block solve without any device allocation ----
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc (code inside another framework's memory pool or allocator
+ * hooks, hosts that forbid device allocations in plugins, work being set up
+ * while other streams are captured).  It solves the same block-tridiagonal
+ * system as xk_block_solve with the same FP64 kernels, without a context or
+ * a workspace.  A [L*S*S], lo [L*S], up [L*S], f [L*S] and x [L*S] are
+ * caller-owned device pointers of the current device; A is not modified;
+ * stream is a cudaStream_t (NULL: legacy default stream).  The call
+ * synchronizes the stream.
+ * Scratch lives in one file-scope device array of XK_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that every GPU loading the library holds until the process exits;
+ * the call needs about L*S*(8*round_up(S, 32) + 16) bytes of it and returns
+ * XK_ENOMEM when that exceeds the array (e.g. S = 96 fits up to L = 445,
+ * S = 594 up to L = 11).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture on that device.  All calls share the array and it keeps the last
+ * call's contents (the control flags and barrier words are cleared at the
+ * start of each call), so calls that overlap on the GPU, from any thread or
+ * stream, race and must be serialized by the caller.
+ * Returns XK_OK, XK_EINVAL, XK_ENOMEM, XK_ESINGULAR, XK_ETIMEOUT or XK_ECUDA. */
+#define XK_NOALLOC_SCRATCH_BYTES (32u << 20)
+XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *lo, const double *up,
+                                  const double *f, double *x, void *stream);
+
 /* ---- tracing: CUDA events around each phase of every step ----
  * Phases: XK_PH_RATES (Gibbs energies + rate coefficients), XK_PH_PHOTO,
  * XK_PH_REACTION (w and its derivatives), XK_PH_RESIDUAL, XK_PH_JACOBIAN,

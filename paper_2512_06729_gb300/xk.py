@@ -81,6 +81,7 @@ SIGNATURES = {
     "xk_eval_jacobian": (C.c_int, [_vp, _vp, C.c_double, _vp, _vp, _vp]),
     "xk_block_solve": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "xk_step_delta": (C.c_int, [_vp, _vp, C.c_double, _vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "xk_block_solve_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
