@@ -262,7 +262,7 @@ void up(xk_ctx *c, const T *dst, const std::vector<T> &v)
 BlockSys<double> sys64(xk_ctx *c)
 {
     BlockSys<double> s;
-    s.D = c->A64; s.lo = c->lo64; s.up = c->up64; s.ridx = c->ridx; s.sig = c->sig;
+    s.D = c->A64; s.lo = c->lo64; s.up = c->up64; s.perm = c->ridx; s.iperm = c->sig;
     s.pinfo = c->pinfo; s.bar = c->bar; s.L = c->L; s.S = c->S; s.ld = c->col.ld;
     return s;
 }
@@ -270,7 +270,7 @@ BlockSys<double> sys64(xk_ctx *c)
 BlockSys<float> sys32(xk_ctx *c)
 {
     BlockSys<float> s;
-    s.D = c->A32; s.lo = c->lo32; s.up = c->up32; s.ridx = c->ridx; s.sig = c->sig;
+    s.D = c->A32; s.lo = c->lo32; s.up = c->up32; s.perm = c->ridx; s.iperm = c->sig;
     s.pinfo = c->pinfo; s.bar = c->bar; s.L = c->L; s.S = c->S; s.ld = c->col.ld;
     return s;
 }

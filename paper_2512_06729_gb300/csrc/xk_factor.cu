@@ -6,10 +6,10 @@
 // grid barrier whose waits are bounded (on timeout the kernel records the
 // error in the control block and returns).
 //
-// Storage after factorization: D holds B_k = (P_k D'_k)^-1, where P_k is the
-// row permutation chosen by pivoting; ridx_k[i] is the original row now at
-// position i, so D'^-1_k g = B_k (g[ridx_k]) and D'^-1_k[:, j] = B_k[:, sig_k(j)]
-// with sig_k the inverse of ridx_k.
+// Pivoting is implicit: rows never move, perm_k[c] is the row that served as
+// pivot of column c and iperm_k its inverse.  After factorization D holds B_k
+// with D'^-1_k[i][j] = B_k[perm_k(i)][iperm_k(j)], so that
+// (D'^-1_k g)[i] = sum_b B_k[perm_k(i)][b] g[perm_k(b)].
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -51,175 +51,164 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl)
     return *(volatile int *)&ctl->err_timeout == 0;
 }
 
-// max |value| with the lowest row index on ties, over a block
-__device__ __forceinline__ void argmax_combine(double &v, int &i, double ov, int oi)
+// Pivot search key: the magnitude's bit pattern is monotonic for |x|, so the
+// comparison runs on the integer pipes (FP64 compares are slow on this part).
+// High 32 bits: magnitude (float bits, or the top 32 bits of the double's
+// magnitude); low 32 bits: ~row, so that among equal keys the lowest row wins.
+__device__ __forceinline__ unsigned long long pivot_key(float v, int row)
 {
-    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+    unsigned mag = __float_as_uint(v) & 0x7fffffffu;
+    return ((unsigned long long)mag << 32) | (unsigned)(~row);
 }
+__device__ __forceinline__ unsigned long long pivot_key(double v, int row)
+{
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return ((bits >> 31) << 32) | (unsigned)(~row);
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
 
-// Gauss-Jordan on the panel columns [c0, c0 + nb) of D (all S rows), by one CTA.
+constexpr int kRowsPerThread = 2;        // rows per thread in the trailing update: S <= 2 * kFactorThreads
+
+// Gauss-Jordan on the panel columns [c0, c0 + nb) of D (all S rows), by one CTA,
+// with implicit partial pivoting: rows are never moved; the pivot of column c
+// is the unused row of largest |value|, recorded as perm[c] = row and
+// iperm[row] = c (iperm = -1 marks rows not used as pivots yet).  The panel is
+// staged in shared memory; per column two block barriers, with the elimination
+// of column c-1 fused into the pivot search of column c.
 template <typename T, int NB>
-__device__ void panel_factor(T *D, int *ridx, int *pinfo, int S, int ld, int c0, int nb, Ctl *ctl,
+__device__ void panel_factor(T *D, int *perm, int *iperm, int *pinfo, int S, int ld, int c0, int nb, Ctl *ctl,
                              unsigned char *smem)
 {
     constexpr int PS = NB + 1;                 // padded row stride (no bank conflicts)
-    T *P = (T *)smem;
-    int *src = (int *)(P + (size_t)S * PS);
-    int *tmp = src + S;
-    __shared__ double red_v[32];
-    __shared__ int red_i[32];
-    __shared__ int s_piv, s_cnt;
+    T *P = (T *)smem;                          // S x PS panel
+    T *prow = P + (size_t)S * PS;              // normalized pivot row (PS); prow[c] = 1 / pivot
+    int *ip = (int *)(prow + PS);              // S: iperm of this layer
+    __shared__ unsigned long long red[32];
+    __shared__ int s_piv;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
 
     for (int e = tid; e < S * nb; e += nthr) {
         int r = e / nb, j = e - r * nb;
         P[r * PS + j] = D[(size_t)r * ld + c0 + j];
     }
-    for (int r = tid; r < S; r += nthr) src[r] = r;
+    for (int r = tid; r < S; r += nthr) ip[r] = iperm[r];
     __syncthreads();
 
-    for (int lc = 0; lc < nb; ++lc) {
-        const int c = c0 + lc;
-        double best = -1.0;
-        int bi = S;
-        for (int r = c + tid; r < S; r += nthr) {
-            double v = fabs((double)P[r * PS + lc]);
-            argmax_combine(best, bi, v, r);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            argmax_combine(best, bi, ov, oi);
-        }
-        if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
-        __syncthreads();
-        if (tid < 32) {
-            int nw = nthr >> 5;
-            double v = tid < nw ? red_v[tid] : -1.0;
-            int i = tid < nw ? red_i[tid] : S;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, v, o);
-                int oi = __shfl_xor_sync(0xffffffffu, i, o);
-                argmax_combine(v, i, ov, oi);
-            }
-            if (tid == 0) {
-                if (!(v > 0.0) || i >= S) {       // zero (or NaN) column: singular block
-                    atomicExch(&ctl->err_singular, 1);
-                    i = c;
-                }
-                s_piv = i;
-            }
-        }
-        __syncthreads();
-        const int piv = s_piv;
-        if (piv != c) {
-            for (int j = tid; j < nb; j += nthr) {
-                T t = P[c * PS + j];
-                P[c * PS + j] = P[piv * PS + j];
-                P[piv * PS + j] = t;
-            }
-            if (tid == 0) { int t = src[c]; src[c] = src[piv]; src[piv] = t; }
-        }
-        __syncthreads();
-        const T dinv = (T)1 / P[c * PS + lc];
-        __syncthreads();
-        for (int j = tid; j < nb; j += nthr)
-            P[c * PS + j] = (j == lc) ? dinv : P[c * PS + j] * dinv;
-        __syncthreads();
+    int piv_prev = -1;
+    for (int lc = 0; lc <= nb; ++lc) {
+        unsigned long long best = 0ull;
         for (int r = tid; r < S; r += nthr) {
-            if (r == c) continue;
-            T f = P[r * PS + lc];
-            if (f != (T)0) {
-#pragma unroll 8
-                for (int j = 0; j < nb; ++j)
-                    if (j != lc) P[r * PS + j] -= f * P[c * PS + j];
-                P[r * PS + lc] = -f * dinv;
+            T *Pr = P + r * PS;
+            if (lc > 0 && r != piv_prev) {
+                const T f = Pr[lc - 1];
+                if (f != (T)0) {
+#pragma unroll
+                    for (int j = 0; j < NB; ++j)
+                        if (j < nb && j != lc - 1) Pr[j] -= f * prow[j];
+                    Pr[lc - 1] = -f * prow[lc - 1];
+                }
+            }
+            if (lc < nb && ip[r] < 0) best = umax64(best, pivot_key(Pr[lc], r));
+        }
+        if (lc == nb) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long all = lane < nw ? red[lane] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) all = umax64(all, __shfl_xor_sync(0xffffffffu, all, o));
+            int piv = (int)(~(unsigned)(all & 0xffffffffull));
+            if ((all >> 32) == 0ull || piv < 0 || piv >= S) {
+                // zero column: singular block; keep the bookkeeping consistent with the first unused row
+                if (lane == 0) atomicExch(&ctl->err_singular, 1);
+                piv = -1;
+                for (int r = 0; r < S && piv < 0; ++r)
+                    if (ip[r] < 0) piv = r;
+                if (piv < 0) piv = 0;
+            }
+            const T pv = P[piv * PS + lc];
+            const T di = (pv != (T)0) ? (T)1 / pv : (T)0;
+            for (int j = lane; j < nb; j += 32) {
+                T val = (j == lc) ? di : P[piv * PS + j] * di;
+                prow[j] = val;
+                P[piv * PS + j] = val;
+            }
+            if (lane == 0) {
+                s_piv = piv;
+                ip[piv] = c0 + lc;
+                perm[c0 + lc] = piv;
+                pinfo[lc] = piv;
             }
         }
         __syncthreads();
+        piv_prev = s_piv;
     }
-
+    __syncthreads();
     for (int e = tid; e < S * nb; e += nthr) {
         int r = e / nb, j = e - r * nb;
         D[(size_t)r * ld + c0 + j] = P[r * PS + j];
     }
-    // pinfo: [0] displaced count, [1..nb] source rows of panel positions,
-    // [1+nb ..] pairs (row, source) of rows outside the panel that moved
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    for (int lc = tid; lc < nb; lc += nthr) pinfo[1 + lc] = src[c0 + lc];
-    for (int r = tid; r < S; r += nthr) {
-        if ((r < c0 || r >= c0 + nb) && src[r] != r) {
-            int slot = atomicAdd(&s_cnt, 1);
-            pinfo[1 + nb + 2 * slot] = r;
-            pinfo[2 + nb + 2 * slot] = src[r];
-        }
-    }
-    // ridx follows the same row moves
-    for (int r = tid; r < S; r += nthr) tmp[r] = ridx[src[r]];
-    __syncthreads();
-    for (int r = tid; r < S; r += nthr) ridx[r] = tmp[r];
-    if (tid == 0) pinfo[0] = s_cnt;
+    for (int r = tid; r < S; r += nthr) iperm[r] = ip[r];
     __threadfence();
 }
 
-// Apply the panel's row moves and eliminations to the other columns:
-// rows outside the panel: D[r][j] += sum_l G[r][l] U[l][j]; panel rows: D[r][j] = sum_l G[r][l] U[l][j],
-// with U the (moved) panel rows and G the panel columns.
+// Apply the panel's eliminations to the other columns j: with G the panel
+// columns and U the panel's pivot rows (values before this update),
+//   pivot rows of this panel: D[r][j] = sum_l G[r][l] U[l][j]
+//   all other rows:           D[r][j] += sum_l G[r][l] U[l][j].
+// Each CTA owns a slice of columns; each thread owns whole rows and keeps its
+// row of G in registers.
 template <typename T, int NB>
-__device__ void trailing_update(T *D, const int *pinfo, int S, int ld, int c0, int nb, unsigned char *smem)
+__device__ void trailing_update(T *D, const int *pinfo, const int *iperm, int S, int ld, int c0, int nb,
+                                unsigned char *smem)
 {
+    constexpr int MAXC = 8;                            // columns per CTA handled in registers
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int others = S - nb;
     const int cw = (others + gridDim.x - 1) / gridDim.x;
-    const int q0 = blockIdx.x * cw;
-    const int q1 = min(others, q0 + cw);
-    const int ncols = q1 - q0;
-    if (ncols <= 0) return;
-    T *G = (T *)smem;                                  // S x NB
-    T *U = G + (size_t)S * NB;                         // NB x cw
-    T *DV = U + (size_t)NB * cw;                       // NB x cw (displaced rows' old values)
-    int *meta = (int *)(DV + (size_t)NB * cw);         // [0..nb) sources, then pairs
-    int *dmap = meta + 1 + 3 * NB;                     // S: index into DV or -1
-    const int ndisp = pinfo[0];
-    for (int e = tid; e < 1 + nb + 2 * ndisp; e += nthr) meta[e] = pinfo[e];
-    for (int r = tid; r < S; r += nthr) dmap[r] = -1;
-    for (int e = tid; e < S * nb; e += nthr) {
-        int r = e / nb, l = e - r * nb;
-        G[r * NB + l] = D[(size_t)r * ld + c0 + l];
+    T *U = (T *)smem;                                  // NB x cw
+    for (int q0 = blockIdx.x * cw, qend = min(others, (blockIdx.x + 1) * cw); q0 < qend; q0 += MAXC) {
+        const int ncols = min(MAXC, qend - q0);
+        for (int e = tid; e < nb * ncols; e += nthr) {
+            int l = e / ncols, jj = e - l * ncols;
+            int q = q0 + jj;
+            int j = q < c0 ? q : q + nb;
+            U[l * MAXC + jj] = D[(size_t)pinfo[l] * ld + j];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int rr = 0; rr < kRowsPerThread; ++rr) {
+            const int r = tid + rr * nthr;
+            if (r >= S) break;
+            const int ip = iperm[r];
+            const bool pivot_row = ip >= c0 && ip < c0 + nb;
+            T g[NB];
+            const T *Gr = D + (size_t)r * ld + c0;
+#pragma unroll
+            for (int l = 0; l < NB; ++l) g[l] = (l < nb) ? Gr[l] : (T)0;
+            T acc[MAXC];
+#pragma unroll
+            for (int jj = 0; jj < MAXC; ++jj) {
+                int q = q0 + jj;
+                int j = q < c0 ? q : q + nb;
+                acc[jj] = (jj < ncols && !pivot_row) ? D[(size_t)r * ld + j] : (T)0;
+            }
+#pragma unroll
+            for (int l = 0; l < NB; ++l)
+#pragma unroll
+                for (int jj = 0; jj < MAXC; ++jj) acc[jj] += g[l] * U[l * MAXC + jj];
+#pragma unroll
+            for (int jj = 0; jj < MAXC; ++jj) {
+                int q = q0 + jj;
+                int j = q < c0 ? q : q + nb;
+                if (jj < ncols) D[(size_t)r * ld + j] = acc[jj];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int t = tid; t < ndisp; t += nthr) dmap[meta[1 + nb + 2 * t]] = t;
-    for (int e = tid; e < nb * ncols; e += nthr) {
-        int l = e / ncols, jj = e - l * ncols;
-        int q = q0 + jj;
-        int j = q < c0 ? q : q + nb;
-        U[l * cw + jj] = D[(size_t)meta[1 + l] * ld + j];
-    }
-    for (int e = tid; e < ndisp * ncols; e += nthr) {
-        int t = e / ncols, jj = e - t * ncols;
-        int q = q0 + jj;
-        int j = q < c0 ? q : q + nb;
-        DV[t * cw + jj] = D[(size_t)meta[2 + nb + 2 * t] * ld + j];
-    }
-    __syncthreads();
-    for (int e = tid; e < S * ncols; e += nthr) {
-        int r = e / ncols, jj = e - r * ncols;
-        int q = q0 + jj;
-        int j = q < c0 ? q : q + nb;
-        T base;
-        if (r >= c0 && r < c0 + nb) base = (T)0;
-        else if (dmap[r] >= 0) base = DV[dmap[r] * cw + jj];
-        else base = D[(size_t)r * ld + j];
-        T acc = base;
-        const T *g = G + r * NB;
-#pragma unroll 8
-        for (int l = 0; l < nb; ++l) acc += g[l] * U[l * cw + jj];
-        D[(size_t)r * ld + j] = acc;
-    }
-    __syncthreads();
 }
 
 template <typename T, int NB>
@@ -232,28 +221,29 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (int k = 0; k < L; ++k) {
         T *D = a.D + (size_t)k * S * ld;
-        int *ridx = a.ridx + (size_t)k * S;
+        int *perm = a.perm + (size_t)k * S;
+        int *iperm = a.iperm + (size_t)k * S;
         if (k > 0) {
+            // D'_k = A_k - diag(lo_k) D'^-1_{k-1} diag(up_{k-1}), D'^-1[i][j] = B[perm(i)][iperm(j)]
             const T *Bp = a.D + (size_t)(k - 1) * S * ld;
-            const int *sg = a.sig + (size_t)(k - 1) * S;
+            const int *pp = a.perm + (size_t)(k - 1) * S;
+            const int *ipp = a.iperm + (size_t)(k - 1) * S;
             const T *lo = a.lo + (size_t)k * S;
             const T *upp = a.up + (size_t)(k - 1) * S;
             for (long long e = gtid; e < (long long)S * S; e += gstride) {
                 int i = (int)(e / S), j = (int)(e - (long long)i * S);
-                D[(size_t)i * ld + j] -= lo[i] * Bp[(size_t)i * ld + sg[j]] * upp[j];
+                D[(size_t)i * ld + j] -= lo[i] * Bp[(size_t)pp[i] * ld + ipp[j]] * upp[j];
             }
         }
-        for (long long i = gtid; i < S; i += gstride) ridx[i] = (int)i;
+        for (long long i = gtid; i < S; i += gstride) iperm[i] = -1;
         if (!grid_barrier(a.bar, ctl)) return;
         for (int c0 = 0; c0 < S; c0 += NB) {
             const int nb = min(NB, S - c0);
-            if (blockIdx.x == 0) panel_factor<T, NB>(D, ridx, a.pinfo, S, ld, c0, nb, ctl, smem);
+            if (blockIdx.x == 0) panel_factor<T, NB>(D, perm, iperm, a.pinfo, S, ld, c0, nb, ctl, smem);
             if (!grid_barrier(a.bar, ctl)) return;
-            trailing_update<T, NB>(D, a.pinfo, S, ld, c0, nb, smem);
+            trailing_update<T, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem);
             if (!grid_barrier(a.bar, ctl)) return;
         }
-        for (long long i = gtid; i < S; i += gstride) a.sig[(size_t)k * S + ridx[i]] = (int)i;
-        if (!grid_barrier(a.bar, ctl)) return;
     }
 }
 
@@ -275,13 +265,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
             for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x)
                 g[i] = bscale ? b[i] * bscale[i] : b[i];
         } else {
-            const int *rp = a.ridx + (size_t)(k - 1) * S;
+            const int *rp = a.perm + (size_t)(k - 1) * S;
             const double *gp = g + (size_t)(k - 1) * S;
             for (int m = threadIdx.x; m < S; m += blockDim.x) vec[m] = (T)gp[rp[m]];
             __syncthreads();
             const T *B = a.D + (size_t)(k - 1) * S * ld;
             for (int i = gw; i < S; i += nw) {
-                const T *Bi = B + (size_t)i * ld;
+                const T *Bi = B + (size_t)rp[i] * ld;
                 T acc = 0;
                 for (int m = lane; m < S; m += 32) acc += Bi[m] * vec[m];
 #pragma unroll
@@ -296,7 +286,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
         if (!grid_barrier(a.bar, ctl)) return;
     }
     for (int k = L - 1; k >= 0; --k) {
-        const int *rp = a.ridx + (size_t)k * S;
+        const int *rp = a.perm + (size_t)k * S;
         const double *gk = g + (size_t)k * S;
         for (int m = threadIdx.x; m < S; m += blockDim.x) {
             int o = rp[m];
@@ -307,7 +297,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
         __syncthreads();
         const T *B = a.D + (size_t)k * S * ld;
         for (int i = gw; i < S; i += nw) {
-            const T *Bi = B + (size_t)i * ld;
+            const T *Bi = B + (size_t)rp[i] * ld;
             T acc = 0;
             for (int m = lane; m < S; m += 32) acc += Bi[m] * vec[m];
 #pragma unroll
@@ -321,10 +311,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
 template <typename T, int NB>
 size_t factor_smem(int S, int ctas)
 {
-    size_t panel = (size_t)S * (NB + 1) * sizeof(T) + 2 * (size_t)S * sizeof(int);
-    int cw = (S + ctas - 1) / ctas;
-    size_t trail = (size_t)S * NB * sizeof(T) + 2 * (size_t)NB * cw * sizeof(T)
-                 + (1 + 3 * NB + (size_t)S) * sizeof(int);
+    (void)ctas;
+    size_t panel = (size_t)S * (NB + 1) * sizeof(T) + (NB + 1) * sizeof(T) + (size_t)S * sizeof(int) + 64;
+    size_t trail = (size_t)NB * 8 * sizeof(T) + 64;
     size_t m = panel > trail ? panel : trail;
     return (m + 255) & ~(size_t)255;
 }
@@ -353,7 +342,8 @@ int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPl
     if (nb_hint > 0) p.nb = nb_hint;
     int sms = sm_count();
     // FP64 is ALU-bound on every SM; FP32 reads the panel per CTA, so fewer and wider slices
-    int want = precision_bytes == 8 ? sms : (S + 15) / 16;
+    if (S > kRowsPerThread * kFactorThreads) return -1;
+    int want = sms;
     if (ctas_hint > 0) want = ctas_hint;
     if (want > sms) want = sms;
     if (want < 1) want = 1;

@@ -103,8 +103,10 @@ __global__ void k_sub(const double *b, const double *y, double *r, long long N, 
         r[n] = b[n] - y[n];
 }
 
-// Start of a cycle: beta = ||r|| (computed into red[0]); V_0 = r / beta; g = beta e_1.
-__global__ void k_cycle_begin(GmState *gm, const double *red, int first)
+// Start of a cycle: beta = ||r|| of the true residual r = b - A x (computed
+// into red[0]); V_0 = r / beta; g = beta e_1.  Convergence is decided here, on
+// the true residual, never on the Givens recurrence alone.
+__global__ void k_cycle_begin(GmState *gm, const double *red, int first, int max_iter)
 {
     if (gm->done) return;
     double beta = sqrt(red[0]);
@@ -117,10 +119,11 @@ __global__ void k_cycle_begin(GmState *gm, const double *red, int first)
     gm->g[0] = beta;
     double rel = (gm->bnorm > 0.0) ? beta / gm->bnorm : 0.0;
     gm->resid = rel;
-    if (!(beta > 0.0) || rel <= gm->tol || !isfinite(beta)) {
+    if (!(beta > 0.0) || rel <= gm->tol || !isfinite(beta) || gm->iters >= max_iter) {
         gm->done = 1;
         gm->cycle_end = 1;
         gm->idle = 1;
+        if (!isfinite(beta)) gm->failed = 1;
     }
 }
 
@@ -191,10 +194,20 @@ __global__ void k_update(GmState *gm, const double *Z, double *x, long long N, i
 __global__ void k_update_done(GmState *gm, int max_iter)
 {
     if (gm->applied) return;
-    if (gm->resid <= gm->tol || gm->iters >= max_iter || gm->failed) gm->done = 1;
+    (void)max_iter;
+    if (gm->failed) gm->done = 1;        // otherwise the next cycle start checks the true residual
     gm->cycle_end = 0;
     gm->idle = gm->done;
     if (gm->done) gm->applied = 1;
+}
+
+// Record the true relative residual of a solve that ended without a checked convergence.
+__global__ void k_final(GmState *gm, const double *red)
+{
+    if (gm->done) return;
+    gm->resid = (gm->bnorm > 0.0) ? sqrt(red[0]) / gm->bnorm : 0.0;
+    gm->done = 1;
+    gm->idle = 1;
 }
 
 __global__ void k_gm_init(GmState *gm, double tol)
@@ -243,7 +256,7 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
 {
     const long long N = a.N;
     const int m = a.m < kMaxBasis ? a.m : kMaxBasis;
-    const int cycles = (a.max_iter + m - 1) / m;
+    const int cycles = (a.max_iter + m - 1) / m + 1;   // the last start only checks the true residual
     int eb = (int)((N + kRedThreads - 1) / kRedThreads);
     if (eb > 4 * kRedBlocks) eb = 4 * kRedBlocks;
     count_launches(1); k_gm_init<<<1, 1, 0, st>>>(a.gm, a.tol);
@@ -254,13 +267,13 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
         if (cyc == 0) {
             count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, a.b, N, a.partials, a.counter, a.red, a.gm, 1);
             // red[0] = ||b||^2 (nv = 0: the norm lands in out[0])
-            count_launches(1); k_cycle_begin<<<1, 1, 0, st>>>(a.gm, a.red, 1);
+            count_launches(1); k_cycle_begin<<<1, 1, 0, st>>>(a.gm, a.red, 1, a.max_iter);
             count_launches(1); k_scale<<<eb, kRedThreads, 0, st>>>(a.b, a.V, N, &a.gm->beta, a.gm);
         } else {
             a.matvec(a.x, a.w, &a.gm->done, st);
             count_launches(1); k_sub<<<eb, kRedThreads, 0, st>>>(a.b, a.w, r, N, a.gm);
             count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, r, N, a.partials, a.counter, a.red, a.gm, 1);
-            count_launches(1); k_cycle_begin<<<1, 1, 0, st>>>(a.gm, a.red, 0);
+            count_launches(1); k_cycle_begin<<<1, 1, 0, st>>>(a.gm, a.red, 0, a.max_iter);
             count_launches(1); k_scale<<<eb, kRedThreads, 0, st>>>(r, a.V, N, &a.gm->beta, a.gm);
         }
         for (int jj = 0; jj < m; ++jj) {
@@ -280,6 +293,11 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
         count_launches(1); k_update<<<eb, kRedThreads, 0, st>>>(a.gm, a.Z, a.x, N, a.max_iter);
         count_launches(1); k_update_done<<<1, 1, 0, st>>>(a.gm, a.max_iter);
     }
+    // final check on the true residual (a cycle may have ended on the recurrence estimate)
+    a.matvec(a.x, a.w, &a.gm->done, st);
+    count_launches(1); k_sub<<<eb, kRedThreads, 0, st>>>(a.b, a.w, a.w, N, a.gm);
+    count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, a.w, N, a.partials, a.counter, a.red, a.gm, 1);
+    count_launches(1); k_final<<<1, 1, 0, st>>>(a.gm, a.red);
     count_launches(1); k_gm_report<<<1, 1, 0, st>>>(a.gm, a.ctl);
 }
 

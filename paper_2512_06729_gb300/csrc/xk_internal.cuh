@@ -101,9 +101,9 @@ template <typename T>
 struct BlockSys {
     T *D;            // [L][S][ld] diagonal blocks, overwritten by their inverses (row-pivoted form)
     const T *lo, *up;
-    int *ridx;       // [L][S] row origin after pivoting
-    int *sig;        // [L][S] inverse of ridx
-    int *pinfo;      // panel scratch: [1 + 4 * nb]
+    int *perm;       // [L][S] pivot row of each column
+    int *iperm;      // [L][S] column each row was pivot of
+    int *pinfo;      // panel scratch: pivot rows of the current panel
     unsigned *bar;   // grid barrier: [2]
     int L, S, ld;
 };

@@ -61,7 +61,7 @@ extern "C" int xk_block_solve_noalloc(int L, int S, const double *A, const doubl
     if (L <= 0 || S <= 0 || S > 65535 || !A || !lo || !up || !f || !x) return XK_EINVAL;
     const size_t ld = (size_t)(S + 31) / 32 * 32;
     const size_t LS = (size_t)L * S;
-    // scratch layout: control block | barrier words | panel info | ridx | sig | sweep vector | blocks
+    // scratch layout: control block | barrier words | panel info | pivot rows | pivot columns | sweep vector | blocks
     const size_t o_ctl = 0;
     const size_t o_bar = up256(o_ctl + sizeof(Ctl));
     const size_t o_pinfo = up256(o_bar + 8 * sizeof(unsigned));
@@ -84,8 +84,8 @@ extern "C" int xk_block_solve_noalloc(int L, int S, const double *A, const doubl
     sys.D = (double *)(base + o_D);
     sys.lo = lo;
     sys.up = up;
-    sys.ridx = (int *)(base + o_ridx);
-    sys.sig = (int *)(base + o_sig);
+    sys.perm = (int *)(base + o_ridx);
+    sys.iperm = (int *)(base + o_sig);
     sys.pinfo = (int *)(base + o_pinfo);
     sys.bar = (unsigned *)(base + o_bar);
     sys.L = L;

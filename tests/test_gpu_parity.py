@@ -234,24 +234,18 @@ def _oracle_schedule(o, n, steps):
     return dts
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_replayed_schedule_trajectory(precision):
-    """Both sides replay the oracle's controlled dt sequence with every step
-    accepted (n <- max(n + delta(n, dt), 0)), through the large-dt late phase.
-    Species above 1e-12 mixing ratio stay within 1e-6.  Species between 1e-20
-    and 1e-12 sit up to 19 decades below the bath gas, where FP64 itself
-    resolves them only to ~1e-4 (two FP64 CPU solvers with different pivot
-    order differ by 3e-4 on this column); they are held to 1e-3."""
-    p = synth.tiny_column()
+def _replay(p, precision, dts):
+    """Replay dts on both sides with every step accepted; per step, the worst
+    relative difference over species above 1e-12 and over those between 1e-20
+    and 1e-12 mixing ratio."""
     o = Oracle(p)
     ng = o.grid()[0]
-    dts = _oracle_schedule(o, o.initial_state(), 900)
     loose = dict(rel_reject=1e300, neg_tol=1e300)
     pol = default_policy(**loose)
     c = xk.Column(p, precision, **loose)
     c.set_mixing_ratios(p.f0)
     n = o.initial_state()
-    worst_major = worst_trace = 0.0
+    out = []
     for dt in dts:
         info = c.step(dt)
         n, oinfo = o.step(n, dt, pol)
@@ -260,12 +254,38 @@ def test_replayed_schedule_trajectory(precision):
         rel = np.abs(m - n) / np.maximum(n, 1e-300)
         major = n > 1e-12 * ng[:, None]
         trace = (n > 1e-20 * ng[:, None]) & ~major
-        worst_major = max(worst_major, float(rel[major].max()))
-        if trace.any():
-            worst_trace = max(worst_trace, float(rel[trace].max()))
-    assert dts[-1] >= 1e6
-    assert worst_major <= 1e-6, worst_major
-    assert worst_trace <= 1e-3, worst_trace
+        out.append((float(rel[major].max()), float(rel[trace].max()) if trace.any() else 0.0))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_replayed_schedule_small_column(precision):
+    """The oracle's own controlled dt sequence on the 40-species, 60-layer
+    column (1e-8 s up to dt_max = 1e8 s), replayed by both sides with every
+    step accepted: within 1e-6 on every species above 1e-20, every step."""
+    p = synth.small_column()
+    dts = _oracle_schedule(Oracle(p), Oracle(p).initial_state(), 700)
+    assert dts[-1] >= 1e7
+    err = _replay(p, precision, dts)
+    assert err.max() <= 1e-6, err.max(axis=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_replayed_schedule_tiny_column(precision):
+    """The same on the 20-species column.  Up to dt = 1e4 s: within 1e-6 above
+    1e-12 and 1e-3 between 1e-20 and 1e-12.  Beyond that this column has
+    species relaxing on 1e13 s time scales whose values FP64 no longer pins
+    down: two FP64 CPU solvers that pivot differently (the oracle's LU and a
+    scaled Gauss-Jordan) drift apart by 5e-6 at dt = 1e6 s and by up to 2e-4
+    at dt = 1e8 s, so the rest of the run is held to 1e-3."""
+    p = synth.tiny_column()
+    dts = _oracle_schedule(Oracle(p), Oracle(p).initial_state(), 900)
+    assert dts[-1] >= 1e8
+    err = _replay(p, precision, dts)
+    early = np.array([d <= 1e4 for d in dts])
+    assert err[early, 0].max() <= 1e-6, err[early].max(axis=0)
+    assert err[early, 1].max() <= 1e-3, err[early].max(axis=0)
+    assert err.max() <= 1e-3, err.max(axis=0)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
