@@ -83,6 +83,9 @@ typedef struct {
     /* factorization tuning (0: chosen by the library / autotuner) */
     int panel_width;      /* columns per panel of the blocked Gauss-Jordan block inversion */
     int factor_ctas;      /* CTAs of the persistent factorization kernel per column */
+    int fp32_pivoting;    /* mixed mode: 0 (default) FP32 inversion without row pivoting (one warp
+                             inverts each diagonal panel block; look-ahead, one grid barrier per
+                             panel), 1 with implicit partial pivoting */
 } xk_config;
 
 typedef struct {
@@ -191,6 +194,15 @@ XK_API int xk_eval_jacobian(xk_ctx *ctx, const double *n, double dt, double *A, 
  * factorization kernels and the context's workspace (either mode). */
 XK_API int xk_block_solve(xk_ctx *ctx, const double *A, const double *lo, const double *up,
                    const double *f, double *x);
+/* Approximate FP32 solve of a block-tridiagonal system (the mixed path's
+ * preconditioner): A, lo, up (device, FP64, layout as for xk_block_solve) are
+ * converted to FP32 and inverted by the FP32 kernels the context is
+ * configured with (mixed contexts only).  The caller scales the system so
+ * that FP32 can hold its entries (the mixed path uses diag(1/s) A diag(s)
+ * with s = max(n, 1e-20 n_gas)).  The result carries FP32 rounding and no
+ * refinement. */
+XK_API int xk_block_solve32(xk_ctx *ctx, const double *A, const double *lo, const double *up,
+                            const double *f, double *x);
 /* delta solving (I/dt - J(n)) delta = F(n) with the context's precision
  * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed;
  * *iters = -1 when the FP64 fallback solved the step). */

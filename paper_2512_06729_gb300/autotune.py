@@ -17,7 +17,7 @@ from . import build as _build
 
 CANDIDATES = {
     "fp64": [(8, 76), (8, 152), (16, 152), (4, 152)],
-    "mixed": [(16, 38), (16, 76), (16, 152), (32, 38), (32, 76), (32, 152)],
+    "mixed": [(16, 76), (16, 152), (32, 38), (32, 76), (32, 152)],
 }
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 

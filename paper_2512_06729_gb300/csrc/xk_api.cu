@@ -43,6 +43,7 @@ struct xk_ctx {
     // FGMRES buffers
     double *V = nullptr, *Z = nullptr, *gw = nullptr, *h1 = nullptr, *h2 = nullptr, *red = nullptr, *partials = nullptr;
     double *rowd = nullptr, *bhat = nullptr;   // row equilibration: diagonal of I/dt - J, scaled right-hand side
+    float *gbuf = nullptr;                       // panel buffer of the FP32 inversion without pivoting
     unsigned *counter = nullptr;
     GmState *gm = nullptr;
     FactorPlan plan{};     // plan of the context's precision
@@ -237,6 +238,7 @@ size_t layout(xk_ctx *c, char *base)
         c->gw = b.take<double>(LS);
         c->rowd = b.take<double>(LS);
         c->bhat = b.take<double>(LS);
+        c->gbuf = b.take<float>(2 * (size_t)S * 32);
         c->h1 = b.take<double>(kMaxBasis + 1);
         c->h2 = b.take<double>(kMaxBasis + 1);
         c->red = b.take<double>(8);
@@ -311,7 +313,11 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
             // equations divided by their diagonal: residuals in units of relative change per species
             launch_rowdiv((long long)c->L * c->S, col.b, c->rowd, c->bhat, st);
         }
-        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<float>(sys32(c), c->plan, ctl, st, skip32); }
+        {
+            PhaseMark m(c, XK_PH_FACTOR);
+            e = c->cfg.fp32_pivoting ? launch_factor<float>(sys32(c), c->plan, ctl, st, skip32)
+                                     : launch_factor_nopivot(sys32(c), c->plan, c->gbuf, ctl, st, skip32);
+        }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
         GmArgs a;
         a.N = (long long)c->L * c->S;
@@ -551,7 +557,9 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     c->ws_bytes = bytes;
     layout(c, c->ws);
     int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
-    if (factor_plan(c->S, sz, c->cfg.panel_width, c->cfg.factor_ctas, &c->plan) != 0)
+    int nbh = c->cfg.panel_width;
+    if (sz == 4 && !c->cfg.fp32_pivoting && nbh == 0) nbh = 32;
+    if (factor_plan(c->S, sz, nbh, c->cfg.factor_ctas, &c->plan) != 0)
         return fail(c, XK_EINVAL, "no factorization plan for S=%d (panel %d)", c->S, c->cfg.panel_width);
     if (factor_plan(c->S, 8, 0, 0, &c->plan64) != 0)
         return fail(c, XK_EINVAL, "no FP64 factorization plan for S=%d", c->S);
@@ -800,6 +808,31 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve"))) return rc;
+    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
+    return XK_OK;
+}
+
+int xk_block_solve32(xk_ctx *c, const double *A, const double *lo, const double *up, const double *f, double *x)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (c->cfg.precision != XK_PREC_MIXED) return fail(c, XK_EINVAL, "xk_block_solve32 needs a mixed-precision context");
+    if (!A || !lo || !up || !f || !x) return fail(c, XK_EINVAL, "null pointer");
+    const size_t S = c->S, L = c->L, ld = c->col.ld;
+    launch_convert32(A, S, c->A32, ld, L * S, S, c->st);
+    launch_convert32(lo, L * S, c->lo32, L * S, 1, L * S, c->st);
+    launch_convert32(up, L * S, c->up32, L * S, 1, L * S, c->st);
+    Ctl init{};
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    cudaError_t e = c->cfg.fp32_pivoting ? launch_factor<float>(sys32(c), c->plan, c->ctl_aux, c->st)
+                                         : launch_factor_nopivot(sys32(c), c->plan, c->gbuf, c->ctl_aux, c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+    e = launch_solve<float>(sys32(c), c->plan, f, x, c->gsol, c->ctl_aux, c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
+    cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    if ((rc = finish_eval(c, "block_solve32"))) return rc;
     if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
     if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
     return XK_OK;

@@ -514,6 +514,21 @@ static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
+__global__ void k_convert32(const double *src, size_t lds, float *dst, size_t ldd, size_t rows, size_t cols)
+{
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(rows * cols)) return;
+    size_t r = idx / cols, j = idx - r * cols;
+    dst[r * ldd + j] = (float)src[r * lds + j];
+}
+
+void launch_convert32(const double *src, size_t lds, float *dst, size_t ldd, size_t rows, size_t cols, cudaStream_t st)
+{
+    if (rows * cols == 0) return;
+    count_launches(1);
+    k_convert32<<<nblocks((long long)(rows * cols)), kThreads, 0, st>>>(src, lds, dst, ldd, rows, cols);
+}
+
 void launch_set_mixing(const Col &c, const double *f, double *n, cudaStream_t st)
 {
     if (((long long)c.L * c.S) > 0) { count_launches(1); k_set_mixing<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, f, n); }

@@ -247,6 +247,182 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 block inversion without pivoting (preconditioner of the mixed path).
+//
+// Blocked Gauss-Jordan with panels of NB columns and no row exchanges: the
+// diagonal NB x NB block of each panel is inverted by one warp, every other
+// row r of the panel becomes G_r = -D[r][panel] Dpp^-1, and the other columns
+// are updated with the panel's rows.  Look-ahead: CTA 0 owns the next panel's
+// columns in each update and inverts the next diagonal block right after, so
+// each panel costs one grid barrier.  G of a panel is written to a two-slot
+// buffer; the CTA that owns those columns in the next panel reads it there.
+// The FGMRES iteration on the exact FP64 operator (and, when it does not
+// converge, the pivoted FP64 factorization) is what guarantees the solution;
+// this factorization only has to be a good approximate inverse.
+// ---------------------------------------------------------------------------
+
+// Invert the nb x nb block at (c0, c0) of D in place with one warp (no pivoting).
+template <int NB>
+__device__ void diag_inverse_warp(float *D, int ld, int c0, int nb, float *Bs, Ctl *ctl)
+{
+    const int lane = threadIdx.x & 31;
+    // Bs: NB x (NB + 1) staging in shared memory
+    for (int r = 0; r < nb; ++r)
+        if (lane < nb) Bs[r * (NB + 1) + lane] = D[(size_t)(c0 + r) * ld + c0 + lane];
+    __syncwarp();
+    for (int c = 0; c < nb; ++c) {
+        const float d = Bs[c * (NB + 1) + c];
+        const float inv = (d != 0.f) ? 1.f / d : 0.f;
+        if (d == 0.f && lane == 0) atomicExch(&ctl->err_singular, 1);
+        float f[NB];
+#pragma unroll
+        for (int r = 0; r < NB; ++r) f[r] = (r < nb) ? Bs[r * (NB + 1) + c] : 0.f;
+        const float bc = (lane < nb) ? ((lane == c) ? inv : Bs[c * (NB + 1) + lane] * inv) : 0.f;
+        __syncwarp();
+        if (lane < nb) {
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                if (r >= nb) break;
+                if (r == c) Bs[r * (NB + 1) + lane] = bc;
+                else Bs[r * (NB + 1) + lane] = (lane == c) ? -f[r] * inv : Bs[r * (NB + 1) + lane] - f[r] * bc;
+            }
+        }
+        __syncwarp();
+    }
+    for (int r = 0; r < nb; ++r)
+        if (lane < nb) D[(size_t)(c0 + r) * ld + c0 + lane] = Bs[r * (NB + 1) + lane];
+    __syncwarp();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kFactorThreads, 1) k_factor_np(BlockSys<float> a, float *gbuf, Ctl *ctl,
+                                                                  const int *skip)
+{
+    if (ctl->finished || (skip && *skip)) return;
+    constexpr int MAXC = 8;
+    __shared__ float Dinv[NB * (NB + 1)];
+    __shared__ float U[NB * MAXC];
+    __shared__ float Bs[NB * (NB + 1)];
+    const int S = a.S, ld = a.ld, L = a.L;
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, nw = nthr >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    const long long gstride = (long long)G * blockDim.x;
+    const long long gtid = (long long)b * blockDim.x + threadIdx.x;
+    const int npan = (S + NB - 1) / NB;
+    for (int k = 0; k < L; ++k) {
+        float *D = a.D + (size_t)k * S * ld;
+        int *perm = a.perm + (size_t)k * S;
+        int *iperm = a.iperm + (size_t)k * S;
+        if (k > 0) {
+            // D'_k = A_k - diag(lo_k) D'^-1_{k-1} diag(up_{k-1}) (no permutation here)
+            const float *Bp = a.D + (size_t)(k - 1) * S * ld;
+            const float *lo = a.lo + (size_t)k * S;
+            const float *upp = a.up + (size_t)(k - 1) * S;
+            for (long long e = gtid; e < (long long)S * S; e += gstride) {
+                int i = (int)(e / S), j = (int)(e - (long long)i * S);
+                D[(size_t)i * ld + j] -= lo[i] * Bp[(size_t)i * ld + j] * upp[j];
+            }
+        }
+        for (long long i = gtid; i < S; i += gstride) { perm[i] = (int)i; iperm[i] = (int)i; }
+        if (!grid_barrier(a.bar, ctl)) return;
+        if (b == 0 && warp == 0) diag_inverse_warp<NB>(D, ld, 0, min(NB, S), Bs, ctl);
+        if (!grid_barrier(a.bar, ctl)) return;
+        for (int p = 0; p < npan; ++p) {
+            const int c0 = p * NB, nb = min(NB, S - c0), c1 = c0 + nb;
+            const int nbn = (p + 1 < npan) ? min(NB, S - c1) : 0;
+            const int cp = c0 - NB, nbp = (p > 0) ? NB : 0;
+            const float *gprev = gbuf + (size_t)((p + 1) & 1) * S * NB;
+            float *gcur = gbuf + (size_t)(p & 1) * S * NB;
+            // value of D[r][j] before this panel: the previous panel's G lives in its buffer slot
+            auto val = [&](int r, int j) -> float {
+                return (j >= cp && j < cp + nbp) ? gprev[(size_t)r * NB + (j - cp)] : D[(size_t)r * ld + j];
+            };
+            for (int e = tid; e < nb * nb; e += nthr) {
+                int l = e / nb, m = e - l * nb;
+                Dinv[l * (NB + 1) + m] = D[(size_t)(c0 + l) * ld + c0 + m];
+            }
+            __syncthreads();
+            // phase A: G rows of this CTA's row slice: pivot rows take Dinv, the others -D[r][panel] Dinv
+            const int rs = (S + G - 1) / G, r0 = b * rs, r1 = min(S, r0 + rs);
+            for (int e = tid; e < (r1 - r0) * nb; e += nthr) {
+                const int r = r0 + e / nb, l = e - (e / nb) * nb;
+                float gv;
+                if (r >= c0 && r < c1) {
+                    gv = Dinv[(r - c0) * (NB + 1) + l];
+                } else {
+                    float acc = 0.f;
+                    for (int m = 0; m < nb; ++m) acc += val(r, c0 + m) * Dinv[m * (NB + 1) + l];
+                    gv = -acc;
+                }
+                gcur[(size_t)r * NB + l] = gv;
+            }
+            if (!grid_barrier(a.bar, ctl)) return;
+            // phase B: update this CTA's columns; CTA 0 takes the next panel's columns (look-ahead)
+            const int others = S - nb;
+            int base, count, skipq;
+            if (G == 1 || nbn == 0) {
+                const int cw = (others + G - 1) / G;
+                base = b * cw; count = max(0, min(others, base + cw) - base); skipq = 0;
+            } else if (b == 0) {
+                base = c0; count = nbn; skipq = 0;
+            } else {
+                const int rest = others - nbn, cw = (rest + G - 2) / (G - 1);
+                base = (b - 1) * cw; count = max(0, min(rest, base + cw) - base); skipq = nbn;
+            }
+            auto col_of = [&](int i) -> int {
+                int q = base + i;
+                if (skipq > 0 && q >= c0) q += skipq;
+                return q < c0 ? q : q + nb;
+            };
+            for (int i0 = 0; i0 < count; i0 += MAXC) {
+                const int ncols = min(MAXC, count - i0);
+                for (int e = tid; e < nb * ncols; e += nthr) {
+                    int l = e / ncols, jj = e - l * ncols;
+                    U[l * MAXC + jj] = val(c0 + l, col_of(i0 + jj));
+                }
+                __syncthreads();
+#pragma unroll 1
+                for (int rr = 0; rr < kRowsPerThread; ++rr) {
+                    const int r = tid + rr * nthr;
+                    if (r >= S) break;
+                    const bool pivot_row = r >= c0 && r < c1;
+                    float g[NB];
+                    const float *gr = gcur + (size_t)r * NB;
+#pragma unroll
+                    for (int l = 0; l < NB; ++l) g[l] = (l < nb) ? gr[l] : 0.f;
+                    float acc[MAXC];
+#pragma unroll
+                    for (int jj = 0; jj < MAXC; ++jj)
+                        acc[jj] = (jj < ncols && !pivot_row) ? val(r, col_of(i0 + jj)) : 0.f;
+#pragma unroll
+                    for (int l = 0; l < NB; ++l)
+#pragma unroll
+                        for (int jj = 0; jj < MAXC; ++jj) acc[jj] += g[l] * U[l * MAXC + jj];
+#pragma unroll
+                    for (int jj = 0; jj < MAXC; ++jj)
+                        if (jj < ncols) D[(size_t)r * ld + col_of(i0 + jj)] = acc[jj];
+                }
+                __syncthreads();
+            }
+            // look-ahead: CTA 0 inverts the next diagonal block it has just updated
+            if (b == 0 && nbn > 0 && warp == 0) diag_inverse_warp<NB>(D, ld, c1, nbn, Bs, ctl);
+            (void)nw;
+            if (!grid_barrier(a.bar, ctl)) return;
+        }
+        // the last panel's columns are not updated by any later panel: store its G
+        {
+            const int c0 = (npan - 1) * NB, nb = S - c0;
+            const float *glast = gbuf + (size_t)((npan - 1) & 1) * S * NB;
+            for (long long e = gtid; e < (long long)S * nb; e += gstride) {
+                int r = (int)(e / nb), l = (int)(e - (long long)r * nb);
+                D[(size_t)r * ld + c0 + l] = glast[(size_t)r * NB + l];
+            }
+        }
+        if (!grid_barrier(a.bar, ctl)) return;
+    }
+}
+
 // Forward and back substitution sweeps with the stored inverses.
 //   g_0 = b_0; g_k = b_k - lo_k * (D'^-1_{k-1} g_{k-1})
 //   x_{L-1} = D'^-1_{L-1} g_{L-1}; x_k = D'^-1_k (g_k - up_k * x_{k+1})
@@ -381,6 +557,19 @@ cudaError_t launch_factor<double>(const BlockSys<double> &sys, const FactorPlan 
 {
     if (plan.nb == 8) return launch_factor_nb<double, 8>(sys, plan, ctl, st, skip);
     if (plan.nb == 16) return launch_factor_nb<double, 16>(sys, plan, ctl, st, skip);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_factor_nopivot(const BlockSys<float> &sys, const FactorPlan &plan, float *gbuf, Ctl *ctl,
+                                  cudaStream_t st, const int *skip)
+{
+    BlockSys<float> a = sys;
+    void *args[] = {(void *)&a, (void *)&gbuf, (void *)&ctl, (void *)&skip};
+    count_launches(1);
+    if (plan.nb == 32)
+        return cudaLaunchCooperativeKernel((const void *)k_factor_np<32>, dim3(plan.ctas), dim3(plan.threads), args, 0, st);
+    if (plan.nb == 16)
+        return cudaLaunchCooperativeKernel((const void *)k_factor_np<16>, dim3(plan.ctas), dim3(plan.threads), args, 0, st);
     return cudaErrorInvalidValue;
 }
 

@@ -89,6 +89,7 @@ void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st);
 void launch_unscale(const Col &c, const double *xs, double *delta, cudaStream_t st);
 void launch_begin(Ctl *ctl, cudaStream_t st);
 void launch_set_mixing(const Col &c, const double *f, double *n, cudaStream_t st);
+void launch_convert32(const double *src, size_t lds, float *dst, size_t ldd, size_t rows, size_t cols, cudaStream_t st);
 
 // Block-Thomas factorization and solve (xk_factor.cu)
 struct FactorPlan {
@@ -111,6 +112,9 @@ int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPl
 template <typename T>
 cudaError_t launch_factor(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
                           const int *skip = nullptr);
+// FP32 block inversion without pivoting (mixed-path preconditioner); gbuf: 2 x S x nb floats
+cudaError_t launch_factor_nopivot(const BlockSys<float> &sys, const FactorPlan &plan, float *gbuf, Ctl *ctl,
+                                  cudaStream_t st, const int *skip = nullptr);
 template <typename T>
 cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
                          double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,

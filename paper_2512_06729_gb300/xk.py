@@ -33,7 +33,7 @@ class Config(C.Structure):
         ("grow_max", C.c_double), ("shrink_min", C.c_double), ("neg_tol", C.c_double),
         ("f_floor", C.c_double), ("dt_min", C.c_double), ("ss_dt", C.c_double), ("ss_tol", C.c_double),
         ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int), ("gmres_tol", C.c_double),
-        ("panel_width", C.c_int), ("factor_ctas", C.c_int),
+        ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
     ]
 
 
@@ -80,6 +80,7 @@ SIGNATURES = {
     "xk_eval_residual": (C.c_int, [_vp, _vp, _vp]),
     "xk_eval_jacobian": (C.c_int, [_vp, _vp, C.c_double, _vp, _vp, _vp]),
     "xk_block_solve": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "xk_block_solve32": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "xk_step_delta": (C.c_int, [_vp, _vp, C.c_double, _vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "xk_block_solve_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
@@ -286,6 +287,12 @@ class Column:
         calls = (C.c_longlong * len(PHASES))()
         self._call("xk_profile_read", ms, calls, len(PHASES))
         return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+
+    def block_solve32(self, A, lo, up, f):
+        x = self._dev(self.L, self.S)
+        self._call("xk_block_solve32", self._ptr(A.contiguous()), self._ptr(lo.contiguous()),
+                   self._ptr(up.contiguous()), self._ptr(f.contiguous()), self._ptr(x))
+        return x
 
     def step_delta(self, n, dt):
         d = self._dev(self.L, self.S)

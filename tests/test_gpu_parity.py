@@ -183,6 +183,32 @@ def test_block_solve_late_state_large_dt(pair):
     assert np.max(np.abs(x - ox) / s) < 1e-4
 
 
+@pytest.mark.parametrize("pivoting", [0, 1])
+def test_fp32_block_solve(pivoting):
+    """The FP32 block inversion (the mixed path's preconditioner) on the scaled
+    system diag(1/s) A diag(s), against the oracle's FP64 solve of the same
+    system.  The bound is FP32 rounding (6e-8) times the condition number of the
+    scaled system (about 1e3 at dt = 1e-6 s and 1e5 at dt = 1e-2 s on this
+    column), with a margin; an indexing error would give O(1)."""
+    p = synth.small_column()
+    o = Oracle(p)
+    c = xk.Column(p, "mixed", fp32_pivoting=pivoting)
+    ng = o.grid()[0]
+    n = o.initial_state()
+    s = np.maximum(n, 1e-20 * ng[:, None])
+    rng = np.random.default_rng(2)
+    for dt, tol in ((1e-6, 1e-4), (1e-2, 1e-2)):
+        A, lo, up = o.jacobian(n, dt)
+        As = A * s[:, None, :] / s[:, :, None]
+        los = lo * np.vstack([s[:1], s[:-1]]) / s
+        ups = up * np.vstack([s[1:], s[-1:]]) / s
+        f = rng.normal(size=n.shape)
+        x = cpu(c.block_solve32(dev(As), dev(los), dev(ups), dev(f)))
+        ox = o.block_solve(As, los, ups, f)
+        err = np.max(np.abs(x - ox)) / np.max(np.abs(ox))
+        assert err < tol, (pivoting, dt, err)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_step_delta(precision):
     """One linear step at the initial state (small dt) and at a late state
