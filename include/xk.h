@@ -86,6 +86,10 @@ typedef struct {
     int fp32_pivoting;    /* mixed mode: 0 (default) FP32 inversion without row pivoting (one warp
                              inverts each diagonal panel block; look-ahead, one grid barrier per
                              panel), 1 with implicit partial pivoting */
+    int reuse_factorization; /* mixed mode: 1 = once steps go to FP64, precondition FGMRES on the
+                             current FP64 operator with the last FP64 factorization (rescaled to
+                             the current variables) and refactor only when FGMRES misses its
+                             tolerance; 0 (default) = factor every step */
 } xk_config;
 
 typedef struct {
@@ -207,6 +211,37 @@ XK_API int xk_block_solve32(xk_ctx *ctx, const double *A, const double *lo, cons
  * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed;
  * *iters = -1 when the FP64 fallback solved the step). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
+
+/* ---- batches of columns: continuous batching on one GPU ----
+ * A batch advances many columns together, each on its own stream, with the
+ * persistent block-inversion kernels sized to a share of the SMs so that the
+ * columns' work overlaps on the device.  Columns are admitted by their device
+ * footprint (the workspace bytes of their contexts) against the batch's
+ * budget, and can be admitted or removed between calls to xk_batch_step.
+ *
+ * xk_batch_create: budget_bytes = HBM the batch may hold in column
+ *   workspaces; max_slots = most columns at once (also sets each column's
+ *   share of the SMs: max(1, SMs / max_slots) CTAs per inversion kernel).
+ * xk_batch_add: ctx must have its workspace and state set; its steps start
+ *   from dt0 (> 0) with the context's step policy.  *slot receives the slot
+ *   index.  XK_ENOMEM when the footprint does not fit the remaining budget
+ *   or all slots are taken (nothing is changed then).  While in a batch the
+ *   context issues its work on the batch's stream for that slot; calls on the
+ *   context itself (xk_step, ...) must not be made until it is removed.
+ * xk_batch_step: every admitted column that has not finished takes up to
+ *   nsteps controlled steps; returns when all of them are done (the batch's
+ *   streams are synchronized).  Finished columns take no further steps.
+ * xk_batch_poll: run information of a slot and whether it has finished
+ *   (converged, or stopped with an error recorded in *status).
+ * xk_batch_remove: releases the slot and its budget; the context returns to
+ *   its own stream and factorization plan. */
+typedef struct xk_batch xk_batch;
+XK_API int xk_batch_create(xk_batch **out, int device, size_t budget_bytes, int max_slots);
+XK_API int xk_batch_destroy(xk_batch *batch);
+XK_API int xk_batch_add(xk_batch *batch, xk_ctx *ctx, double dt0, int *slot);
+XK_API int xk_batch_remove(xk_batch *batch, int slot);
+XK_API int xk_batch_step(xk_batch *batch, int nsteps);
+XK_API int xk_batch_poll(xk_batch *batch, int slot, xk_run_info *info, int *finished, int *status);
 
 /* ---- block solve without any device allocation ----
  * The paper has no counterpart: this entry point serves callers that cannot

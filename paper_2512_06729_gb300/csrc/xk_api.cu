@@ -44,6 +44,7 @@ struct xk_ctx {
     double *V = nullptr, *Z = nullptr, *gw = nullptr, *h1 = nullptr, *h2 = nullptr, *red = nullptr, *partials = nullptr;
     double *rowd = nullptr, *bhat = nullptr;   // row equilibration: diagonal of I/dt - J, scaled right-hand side
     float *gbuf = nullptr;                       // panel buffer of the FP32 inversion without pivoting
+    double *s64 = nullptr, *pin = nullptr, *pout = nullptr;   // scaling of the reused FP64 factorization
     unsigned *counter = nullptr;
     GmState *gm = nullptr;
     FactorPlan plan{};     // plan of the context's precision
@@ -239,6 +240,9 @@ size_t layout(xk_ctx *c, char *base)
         c->rowd = b.take<double>(LS);
         c->bhat = b.take<double>(LS);
         c->gbuf = b.take<float>(2 * (size_t)S * 32);
+        c->s64 = b.take<double>(LS);
+        c->pin = b.take<double>(LS);
+        c->pout = b.take<double>(LS);
         c->h1 = b.take<double>(kMaxBasis + 1);
         c->h2 = b.take<double>(kMaxBasis + 1);
         c->red = b.take<double>(8);
@@ -307,11 +311,13 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         if (dt_override > 0.0) return fail(c, XK_EINVAL, "mixed path reads dt from the control block");
         launch_route(ctl, st);
         const int *skip32 = &ctl->skip32;
+        const long long N = (long long)c->L * c->S;
         {
             PhaseMark m(c, XK_PH_JACOBIAN);
-            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, c->rowd, st, skip32);
+            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, nullptr, st, skip32);
             // equations divided by their diagonal: residuals in units of relative change per species
-            launch_rowdiv((long long)c->L * c->S, col.b, c->rowd, c->bhat, st);
+            launch_diag(col, ctl, c->rowd, st);
+            launch_rowdiv(N, col.b, c->rowd, c->bhat, st);
         }
         {
             PhaseMark m(c, XK_PH_FACTOR);
@@ -320,28 +326,41 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
         GmArgs a;
-        a.N = (long long)c->L * c->S;
+        a.N = N;
         a.m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
         a.max_iter = std::max(c->cfg.gmres_max_iter, 1);
         a.tol = c->cfg.gmres_tol;
         a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
         a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
         BlockSys<float> s32 = sys32(c);
-        FactorPlan plan = c->plan;
+        BlockSys<double> s64s = sys64(c);
+        FactorPlan plan = c->plan, plan64 = c->plan64;
         double *gsol = c->gsol;
-        const double *rowd = c->rowd;
+        const double *rowd = c->rowd, *pin = c->pin, *pout = c->pout;
         a.matvec = [col, ctl, rowd](const double *x, double *y, const int *skip, cudaStream_t s) {
             launch_jv(col, ctl, x, y, rowd, skip, s);
         };
+        // FGMRES around the FP32 inversion
+        a.skip_solve = skip32;
+        a.role = 0;
         a.precond = [s32, plan, gsol, ctl, rowd](const double *v, double *z, const int *skip, cudaStream_t s) {
             launch_solve<float>(s32, plan, v, z, gsol, ctl, s, rowd, skip);
         };
         { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
-        // FP64 fallback, gated on the device by ctl->skip64
+        // FGMRES around the last FP64 factorization, rescaled to this step's variables
+        launch_reuse_scales(N, rowd, col.s, c->s64, c->pin, c->pout, ctl, st);
+        a.skip_solve = &ctl->skip_reuse;
+        a.role = 1;
+        a.precond = [s64s, plan64, gsol, ctl, pin, pout](const double *v, double *z, const int *skip, cudaStream_t s) {
+            launch_solve<double>(s64s, plan64, v, z, gsol, ctl, s, pin, skip, pout);
+        };
+        { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
+        // FP64 factorization and direct solve, gated on the device by ctl->skip64
         const int *skip64 = &ctl->skip64;
         { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, 0.0, 1, c->A64, c->lo64, c->up64, st, skip64); }
         { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan64, ctl, st, skip64); }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
+        launch_after_refactor(N, col.s, c->s64, ctl, st);
         {
             PhaseMark m(c, XK_PH_SOLVE);
             e = launch_solve<double>(sys64(c), c->plan64, col.b, col.x, c->gsol, ctl, st, nullptr, skip64);
@@ -577,6 +596,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     Ctl init{};
     init.dt = 1e-8;
     init.dt_fp64 = 1e300;
+    init.reuse_enabled = c->cfg.reuse_factorization;
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
@@ -668,6 +688,8 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
     init.dt = dt0 > 0.0 ? dt0 : h.dt;
     init.t = 0.0;
     init.dt_fp64 = h.dt_fp64;
+    init.reuse_enabled = c->cfg.reuse_factorization;
+    init.have64 = h.have64;
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     int enq = 0;
@@ -860,6 +882,165 @@ int xk_step_delta(xk_ctx *c, const double *n, double dt, double *delta, int *ite
 }
 
 long long xk_launch_count(void) { return launches(); }
+
+// ---------------------------------------------------------------- batches
+
+struct BatchSlot {
+    xk_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;
+    cudaStream_t saved_st = nullptr;
+    FactorPlan saved_plan{}, saved_plan64{};
+    size_t bytes = 0;
+    bool finished = false;
+};
+
+}  // extern "C"
+
+struct xk_batch {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int max_slots = 1;
+    std::vector<BatchSlot> slots;
+};
+
+extern "C" {
+
+int xk_batch_create(xk_batch **out, int device, size_t budget_bytes, int max_slots)
+{
+    if (!out || max_slots <= 0 || budget_bytes == 0) return XK_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return XK_ECUDA;
+    }
+    xk_batch *b = new xk_batch();
+    b->device = device;
+    b->budget = budget_bytes;
+    b->max_slots = max_slots;
+    b->slots.resize(max_slots);
+    *out = b;
+    return XK_OK;
+}
+
+int xk_batch_remove(xk_batch *b, int slot)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx) return XK_EINVAL;
+    BatchSlot &s = b->slots[slot];
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(s.st);
+    s.ctx->st = s.saved_st;
+    s.ctx->plan = s.saved_plan;
+    s.ctx->plan64 = s.saved_plan64;
+    cudaStreamDestroy(s.st);
+    b->used -= s.bytes;
+    s = BatchSlot();
+    return cuda_check(nullptr, "batch_remove");
+}
+
+int xk_batch_destroy(xk_batch *b)
+{
+    if (!b) return XK_EINVAL;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i].ctx) xk_batch_remove(b, i);
+    delete b;
+    return XK_OK;
+}
+
+int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
+{
+    if (!b || !c || !slot || !(dt0 > 0)) return XK_EINVAL;
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (c->cfg.device != b->device) return fail(c, XK_EINVAL, "context and batch are on different devices");
+    for (auto &s : b->slots)
+        if (s.ctx == c) return fail(c, XK_EINVAL, "context is already in this batch");
+    int free_slot = -1;
+    for (int i = 0; i < (int)b->slots.size() && free_slot < 0; ++i)
+        if (!b->slots[i].ctx) free_slot = i;
+    if (free_slot < 0) return fail(c, XK_ENOMEM, "all %d batch slots are taken", b->max_slots);
+    if (b->used + c->ws_bytes > b->budget)
+        return fail(c, XK_ENOMEM, "footprint %zu bytes does not fit the remaining budget %zu", c->ws_bytes,
+                    b->budget - b->used);
+    cudaSetDevice(b->device);
+    BatchSlot &s = b->slots[free_slot];
+    if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_check(c, "batch_add");
+    // a share of the SMs for this column's persistent kernels
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    int share = std::max(1, sms / b->max_slots);
+    FactorPlan p, p64;
+    int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
+    if (factor_plan(c->S, sz, c->plan.nb, share, &p) != 0 || factor_plan(c->S, 8, c->plan64.nb, share, &p64) != 0) {
+        cudaStreamDestroy(s.st);
+        s = BatchSlot();
+        return fail(c, XK_EINVAL, "no factorization plan for a %d-CTA share", share);
+    }
+    s.ctx = c;
+    s.saved_st = c->st;
+    s.saved_plan = c->plan;
+    s.saved_plan64 = c->plan64;
+    s.bytes = c->ws_bytes;
+    s.finished = false;
+    c->st = s.st;
+    c->plan = p;
+    c->plan64 = p64;
+    b->used += s.bytes;
+    Ctl h;
+    if ((rc = read_ctl(c, &h))) return rc;
+    Ctl init{};
+    init.dt = dt0;
+    init.dt_fp64 = 1e300;
+    init.reuse_enabled = c->cfg.reuse_factorization;
+    *c->ctl_host = init;
+    cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+    *slot = free_slot;
+    return cuda_check(c, "batch_add");
+}
+
+int xk_batch_step(xk_batch *b, int nsteps)
+{
+    if (!b || nsteps <= 0) return XK_EINVAL;
+    cudaSetDevice(b->device);
+    // round-robin so that every column's next step is queued before the following ones
+    for (int k = 0; k < nsteps; ++k)
+        for (auto &s : b->slots)
+            if (s.ctx && !s.finished) {
+                int rc = enqueue_step(s.ctx);
+                if (rc) return rc;
+            }
+    for (auto &s : b->slots)
+        if (s.ctx && !s.finished)
+            cudaMemcpyAsync(s.ctx->ctl_host, s.ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s.st);
+    for (auto &s : b->slots)
+        if (s.ctx && !s.finished) {
+            cudaError_t e = cudaStreamSynchronize(s.st);
+            if (e != cudaSuccess) return fail(s.ctx, XK_ECUDA, "batch step: %s", cudaGetErrorString(e));
+            s.finished = s.ctx->ctl_host->finished != 0;
+        }
+    return cuda_check(nullptr, "batch_step");
+}
+
+int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *status)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx) return XK_EINVAL;
+    const Ctl &h = *b->slots[slot].ctx->ctl_host;
+    if (info) {
+        info->converged = h.converged;
+        info->steps = h.steps;
+        info->accepted = h.n_acc;
+        info->rejected = h.n_rej;
+        info->t = h.t;
+        info->dt = h.dt;
+        info->max_rel = h.max_rel;
+        info->solver_iters = h.total_iters;
+        info->fp64_steps = h.fp64_steps;
+    }
+    if (finished) *finished = b->slots[slot].finished ? 1 : 0;
+    if (status) *status = h.err_timeout ? XK_ETIMEOUT : h.status;
+    return XK_OK;
+}
 
 int xk_profile(xk_ctx *c, int enable)
 {

@@ -437,8 +437,56 @@ __global__ void k_check(Col c, Ctl *ctl, Policy pol)
 __global__ void k_route(Ctl *ctl)
 {
     ctl->skip32 = ctl->dt >= ctl->dt_fp64 ? 1 : 0;
-    ctl->skip64 = ctl->skip32 ? 0 : 1;
+    const int reuse = ctl->skip32 && ctl->have64 && ctl->reuse_enabled;
+    ctl->skip_reuse = reuse ? 0 : 1;
+    ctl->skip64 = (ctl->skip32 && !reuse) ? 0 : 1;
     ctl->used_fp64 = ctl->skip32;
+}
+
+// Diagonal of I/dt - dF/dn per (layer, species), from the reaction derivatives and transport.
+__global__ void k_diag(Col c, const Ctl *ctl, double *diag)
+{
+    if (ctl->finished) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int S = c.S, L = c.L;
+    if (idx >= (long long)L * S) return;
+    int k = (int)(idx / S), i = (int)(idx % S);
+    const double *dk = c.d + (long long)k * c.R * 6;
+    double acc = 0.0;
+    for (int e = c.jp[i]; e < c.jp[i + 1]; ++e) {
+        int jc = c.jcol[e];
+        if ((jc & 0xffff) != i) continue;
+        int rs = c.jrs[e];
+        double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+        acc += ((jc >> 16) > 0) ? dv : -dv;
+    }
+    double dg = 1.0 / ctl->dt + acc;
+    if (k + 1 < L) dg += c.u[(long long)k * S + i] / c.dz[k];
+    if (k > 0) dg += c.v[(long long)(k - 1) * S + i] / c.dz[k];
+    diag[idx] = fmax(fabs(dg), 1.0 / ctl->dt);
+}
+
+// Scalings of the reused FP64 factorization: input rowd * s / s64, output s64 / s.
+__global__ void k_reuse_scales(long long N, const double *rowd, const double *s, const double *s64, double *pin,
+                               double *pout, const Ctl *ctl)
+{
+    if (ctl->finished || ctl->skip_reuse) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N) return;
+    pin[idx] = rowd[idx] * s[idx] / s64[idx];
+    pout[idx] = s64[idx] / s[idx];
+}
+
+// After an FP64 factorization: remember its scaling, mark the factors valid.
+__global__ void k_after_refactor(long long N, const double *s, double *s64, Ctl *ctl)
+{
+    if (ctl->finished || ctl->skip64) return;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < N) s64[idx] = s[idx];
+    if (idx == 0) {
+        ctl->have64 = 1;
+        ctl->refactors += 1;
+    }
 }
 
 __global__ void k_begin(Ctl *ctl)
@@ -625,6 +673,25 @@ void launch_decide(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st)
 void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st)
 {
     if (((long long)c.L * c.S) > 0) { count_launches(1); k_apply<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, ctl); }
+}
+
+void launch_diag(const Col &c, const Ctl *ctl, double *diag, cudaStream_t st)
+{
+    count_launches(1);
+    k_diag<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c, ctl, diag);
+}
+
+void launch_reuse_scales(long long N, const double *rowd, const double *s, const double *s64, double *pin, double *pout,
+                         const Ctl *ctl, cudaStream_t st)
+{
+    count_launches(1);
+    k_reuse_scales<<<nblocks(N), kThreads, 0, st>>>(N, rowd, s, s64, pin, pout, ctl);
+}
+
+void launch_after_refactor(long long N, const double *s, double *s64, Ctl *ctl, cudaStream_t st)
+{
+    count_launches(1);
+    k_after_refactor<<<nblocks(N), kThreads, 0, st>>>(N, s, s64, ctl);
 }
 
 void launch_route(Ctl *ctl, cudaStream_t st)

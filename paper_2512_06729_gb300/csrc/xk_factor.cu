@@ -428,7 +428,8 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_np(BlockSys<float>
 //   x_{L-1} = D'^-1_{L-1} g_{L-1}; x_k = D'^-1_k (g_k - up_k * x_{k+1})
 template <typename T>
 __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const double *b, double *x, double *g, Ctl *ctl,
-                                                                  const double *bscale, const int *skip)
+                                                                  const double *bscale, const int *skip,
+                                                                  const double *xscale)
 {
     if (ctl->finished || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -481,6 +482,11 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
             if (lane == 0) x[(size_t)k * S + i] = (double)acc;
         }
         if (!grid_barrier(a.bar, ctl)) return;
+    }
+    if (xscale) {
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)L * S;
+             e += (long long)gridDim.x * blockDim.x)
+            x[e] *= xscale[e];
     }
 }
 
@@ -584,25 +590,28 @@ cudaError_t launch_factor<float>(const BlockSys<float> &sys, const FactorPlan &p
 
 template <typename T>
 cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
-                         double *g, Ctl *ctl, cudaStream_t st, const double *bscale, const int *skip)
+                         double *g, Ctl *ctl, cudaStream_t st, const double *bscale, const int *skip,
+                         const double *xscale)
 {
-    (void)plan;
     auto fn = k_solve<T>;
     size_t smem = ((size_t)sys.S * sizeof(T) + 255) & ~(size_t)255;
     int warps = kSolveThreads / 32;
     int ctas = (sys.S + warps - 1) / warps;
     if (ctas > sm_count()) ctas = sm_count();
+    if (plan.ctas > 0 && ctas > plan.ctas) ctas = plan.ctas;    // stay within the column's share of the SMs
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     BlockSys<T> a = sys;
-    void *args[] = {(void *)&a, (void *)&b, (void *)&x, (void *)&g, (void *)&ctl, (void *)&bscale, (void *)&skip};
+    void *args[] = {(void *)&a, (void *)&b, (void *)&x, (void *)&g, (void *)&ctl, (void *)&bscale, (void *)&skip,
+                    (void *)&xscale};
     count_launches(1);
     return cudaLaunchCooperativeKernel((const void *)fn, dim3(ctas), dim3(kSolveThreads), args, smem, st);
 }
 
 template cudaError_t launch_solve<double>(const BlockSys<double> &, const FactorPlan &, const double *, double *,
-                                          double *, Ctl *, cudaStream_t, const double *, const int *);
+                                          double *, Ctl *, cudaStream_t, const double *, const int *,
+                                          const double *);
 template cudaError_t launch_solve<float>(const BlockSys<float> &, const FactorPlan &, const double *, double *,
-                                         double *, Ctl *, cudaStream_t, const double *, const int *);
+                                         double *, Ctl *, cudaStream_t, const double *, const int *, const double *);
 
 }  // namespace xk

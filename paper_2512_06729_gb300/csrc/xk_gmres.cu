@@ -224,29 +224,32 @@ __global__ void k_gm_init(GmState *gm, double tol)
     gm->bnorm = 0.0;
 }
 
-__global__ void k_zero(double *x, long long N)
+__global__ void k_zero(double *x, long long N, const GmState *gm)
 {
+    if (gm->done) return;               // a skipped solve leaves x to the solve that ran
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x)
         x[n] = 0.0;
 }
 
-__global__ void k_gm_skip_if_finished(GmState *gm, const Ctl *ctl)
+__global__ void k_gm_skip_if_finished(GmState *gm, const Ctl *ctl, const int *skip_solve)
 {
-    if (ctl->finished || ctl->skip32) { gm->done = 1; gm->applied = 1; gm->idle = 1; }
+    if (ctl->finished || (skip_solve && *skip_solve)) { gm->done = 1; gm->applied = 1; gm->idle = 1; }
 }
 
 // Record the solve; a solve that did not reach the tolerance hands the step to
 // the FP64 factorization, and so does every later step at this dt or above.
-__global__ void k_gm_report(const GmState *gm, Ctl *ctl)
+__global__ void k_gm_report(const GmState *gm, Ctl *ctl, const int *skip_solve, int role)
 {
-    if (ctl->finished || ctl->skip32) return;
+    if (ctl->finished || (skip_solve && *skip_solve)) return;
     ctl->solver_iters = gm->iters;
     ctl->solver_resid = gm->resid;
     ctl->total_iters += gm->iters;
     if (gm->failed || !(gm->resid <= gm->tol)) {
-        ctl->skip64 = 0;
+        ctl->skip64 = 0;               // refactor in FP64 and solve directly
         ctl->used_fp64 = 1;
-        if (ctl->dt < ctl->dt_fp64) ctl->dt_fp64 = ctl->dt;
+        if (role == 0 && ctl->dt < ctl->dt_fp64) ctl->dt_fp64 = ctl->dt;
+    } else if (role == 1 && gm->iters > kReuseMaxIters) {
+        ctl->have64 = 0;               // the reused factorization has drifted: refactor at the next step
     }
 }
 
@@ -260,8 +263,8 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
     int eb = (int)((N + kRedThreads - 1) / kRedThreads);
     if (eb > 4 * kRedBlocks) eb = 4 * kRedBlocks;
     count_launches(1); k_gm_init<<<1, 1, 0, st>>>(a.gm, a.tol);
-    count_launches(1); k_gm_skip_if_finished<<<1, 1, 0, st>>>(a.gm, a.ctl);
-    count_launches(1); k_zero<<<eb, kRedThreads, 0, st>>>(a.x, N);
+    count_launches(1); k_gm_skip_if_finished<<<1, 1, 0, st>>>(a.gm, a.ctl, a.skip_solve);
+    count_launches(1); k_zero<<<eb, kRedThreads, 0, st>>>(a.x, N, a.gm);
     for (int cyc = 0; cyc < cycles; ++cyc) {
         double *r = a.V;                       // V_0 slot holds the residual before scaling
         if (cyc == 0) {
@@ -298,7 +301,7 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
     count_launches(1); k_sub<<<eb, kRedThreads, 0, st>>>(a.b, a.w, a.w, N, a.gm);
     count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, a.w, N, a.partials, a.counter, a.red, a.gm, 1);
     count_launches(1); k_final<<<1, 1, 0, st>>>(a.gm, a.red);
-    count_launches(1); k_gm_report<<<1, 1, 0, st>>>(a.gm, a.ctl);
+    count_launches(1); k_gm_report<<<1, 1, 0, st>>>(a.gm, a.ctl, a.skip_solve, a.role);
 }
 
 }  // namespace xk

@@ -9,6 +9,9 @@
 namespace xk {
 
 constexpr int kMaxBasis = 32;
+// a solve with the reused FP64 factorization that needs more iterations than this
+// triggers a fresh factorization at the next step
+constexpr int kReuseMaxIters = 6;
 
 struct GmState {
     double H[(kMaxBasis + 1) * kMaxBasis];   // column-major, leading dimension kMaxBasis + 1
@@ -36,6 +39,8 @@ struct GmArgs {
     unsigned *counter;   // last-block counter (zero on entry)
     GmState *gm;
     Ctl *ctl;
+    const int *skip_solve;   // this solve is skipped when *skip_solve != 0
+    int role;                // 0: FP32-preconditioned attempt, 1: attempt with the reused FP64 factorization
     VecOp matvec;        // y = A x (FP64); must return at once while *skip != 0
     VecOp precond;       // z ~ A^-1 v (low precision); same skip rule
 };

@@ -59,7 +59,11 @@ struct Ctl {
     int err_singular;     // zero pivot met
     // mixed precision routing: skip32 = this step goes straight to FP64; skip64 = FP64 solve not needed
     int skip32, skip64;
+    int skip_reuse;       // 0: this step tries FGMRES preconditioned by the last FP64 factorization
+    int have64;           // the FP64 factors in the workspace are valid
+    int reuse_enabled;
     int used_fp64;        // this step was solved by the FP64 factorization
+    long long refactors;  // FP64 factorizations made
     long long fp64_steps;
     double dt_fp64;       // smallest dt at which the FP32-preconditioned solve did not converge
 };
@@ -83,6 +87,10 @@ void launch_route(Ctl *ctl, cudaStream_t st);
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
                cudaStream_t st);
 void launch_rowdiv(long long N, const double *x, const double *d, double *y, cudaStream_t st);
+void launch_diag(const Col &c, const Ctl *ctl, double *diag, cudaStream_t st);
+void launch_reuse_scales(long long N, const double *rowd, const double *s, const double *s64, double *pin, double *pout,
+                         const Ctl *ctl, cudaStream_t st);
+void launch_after_refactor(long long N, const double *s, double *s64, Ctl *ctl, cudaStream_t st);
 void launch_check(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st);
 void launch_decide(const Col &c, Ctl *ctl, const Policy &pol, cudaStream_t st);
 void launch_apply(const Col &c, Ctl *ctl, cudaStream_t st);
@@ -118,7 +126,7 @@ cudaError_t launch_factor_nopivot(const BlockSys<float> &sys, const FactorPlan &
 template <typename T>
 cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
                          double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,
-                         const int *skip = nullptr);
+                         const int *skip = nullptr, const double *xscale = nullptr);
 size_t barrier_words();
 
 }  // namespace xk

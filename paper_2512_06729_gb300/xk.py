@@ -34,6 +34,7 @@ class Config(C.Structure):
         ("f_floor", C.c_double), ("dt_min", C.c_double), ("ss_dt", C.c_double), ("ss_tol", C.c_double),
         ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int), ("gmres_tol", C.c_double),
         ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
+        ("reuse_factorization", C.c_int),
     ]
 
 
@@ -83,6 +84,12 @@ SIGNATURES = {
     "xk_block_solve32": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "xk_step_delta": (C.c_int, [_vp, _vp, C.c_double, _vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "xk_block_solve_noalloc": (C.c_int, [C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "xk_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_size_t, C.c_int]),
+    "xk_batch_destroy": (C.c_int, [_vp]),
+    "xk_batch_add": (C.c_int, [_vp, _vp, C.c_double, C.POINTER(C.c_int)]),
+    "xk_batch_remove": (C.c_int, [_vp, C.c_int]),
+    "xk_batch_step": (C.c_int, [_vp, C.c_int]),
+    "xk_batch_poll": (C.c_int, [_vp, C.c_int, C.POINTER(RunInfo), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
@@ -300,3 +307,59 @@ class Column:
         res = C.c_double()
         self._call("xk_step_delta", self._ptr(n.contiguous()), float(dt), self._ptr(d), C.byref(it), C.byref(res))
         return d, int(it.value), float(res.value)
+
+
+class Batch:
+    """Continuous batching of columns on one GPU (wraps xk_batch_*)."""
+
+    def __init__(self, budget_bytes, max_slots, device=0):
+        h = _vp()
+        rc = lib().xk_batch_create(C.byref(h), int(device), C.c_size_t(int(budget_bytes)), int(max_slots))
+        if rc != XK_OK:
+            raise XkError("xk_batch_create", rc, "")
+        self.h = h
+        self.cols = {}
+
+    def add(self, col, dt0=1e-8):
+        """Admit a column; returns the slot, or None when it does not fit (footprint or slots)."""
+        slot = C.c_int(-1)
+        rc = lib().xk_batch_add(self.h, col.h, float(dt0), C.byref(slot))
+        if rc == -2:
+            return None
+        if rc != XK_OK:
+            msg = lib().xk_last_error(col.h)
+            raise XkError("xk_batch_add", rc, msg.decode() if msg else "")
+        self.cols[slot.value] = col
+        return slot.value
+
+    def remove(self, slot):
+        rc = lib().xk_batch_remove(self.h, int(slot))
+        if rc != XK_OK:
+            raise XkError("xk_batch_remove", rc, "")
+        return self.cols.pop(slot)
+
+    def step(self, nsteps=1):
+        rc = lib().xk_batch_step(self.h, int(nsteps))
+        if rc != XK_OK:
+            raise XkError("xk_batch_step", rc, "")
+
+    def poll(self, slot):
+        info = RunInfo()
+        fin = C.c_int()
+        st = C.c_int()
+        rc = lib().xk_batch_poll(self.h, int(slot), C.byref(info), C.byref(fin), C.byref(st))
+        if rc != XK_OK:
+            raise XkError("xk_batch_poll", rc, "")
+        return info, bool(fin.value), int(st.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().xk_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

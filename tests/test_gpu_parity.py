@@ -314,16 +314,17 @@ def test_replayed_schedule_tiny_column(precision):
     assert err.max() <= 1e-3, err.max(axis=0)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_run_to_steady_matches_oracle(precision):
+@pytest.mark.parametrize("precision,reuse", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+def test_run_to_steady_matches_oracle(precision, reuse):
     """Adaptive run to the steady-state test on the 40-species column; both
-    sides reach the same state within 1e-6 on species above 1e-20."""
+    sides reach the same state within 1e-6 on species above 1e-20 (also with
+    the FP64 factorization reused as FGMRES preconditioner)."""
     p = synth.small_column()
     o = Oracle(p)
     ng = o.grid()[0]
     on, oinfo = o.run_to_steady(o.initial_state(), dt0=1e-8, max_steps=6000)
     assert oinfo.converged
-    c = xk.Column(p, precision)
+    c = xk.Column(p, precision, reuse_factorization=reuse)
     c.set_mixing_ratios(p.f0)
     info = c.run_to_steady(1e-8, 6000)
     assert info.converged
