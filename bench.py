@@ -132,6 +132,18 @@ def _max_over_ranks(x, ws, device):
     return float(t.item())
 
 
+def whole_job_rate(ms_per_step, ws, device):
+    """Steps/s of the whole job: every rank solves its own column (replicas),
+    so the job's rate is ws steps per slowest rank's step time."""
+    ms = _max_over_ranks(ms_per_step, ws, device)
+    return ws * 1e3 / ms, ms
+
+
+def replica_seed(rank):
+    """Seed of the column a rank solves (distinct per rank)."""
+    return 2 + rank
+
+
 def oracle_sample_step_time(prob, layers=SAMPLE_LAYERS, steps=1):
     """CPU oracle, single thread: seconds per implicit step on `layers` layers
     of the column (same network, same profile slice), steps repeated."""
@@ -208,7 +220,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     xkbuild.build()
-    prob = synth.full_column(seed=2 + rank)
+    prob = synth.full_column(seed=replica_seed(rank))
     stream = torch.cuda.current_stream(dev)
     peaks, peak_kind = _peaks()
     alu = _alu_peaks(peaks)
@@ -216,12 +228,15 @@ def run_ours(args):
     from paper_2512_06729_gb300 import autotune
     results = {}
     tuning = {}
+    tables = {}
     for prec in ("mixed", "fp64"):
-        params = autotune.tuned(prob.S, prec)
-        if not params:
-            nb, ctas, _ = autotune.tune(prob, prec)
-            params = {"panel_width": nb, "factor_ctas": ctas}
-        tuning[prec] = params
+        if args.no_tune:
+            tuning[prec] = {}
+            continue
+        tuning[prec] = autotune.tuned(prob.S, prec)
+        if not tuning[prec]:
+            tuning[prec], table = autotune.tune(prob, prec)
+            tables[prec] = [[params, round(ms, 4)] for ms, params in table]
     for prec in ("mixed", "fp64"):
         col = xk.Column(prob, prec, device=local, **tuning[prec])
         col.set_mixing_ratios(prob.f0)
@@ -238,7 +253,6 @@ def run_ours(args):
         else:
             ms, info, phases, launches = time_steps(col, K, stream)
         _barrier(ws)
-        ms = _max_over_ranks(ms, ws, dev)
         steps_done = max(int(info.steps), 1)
         results[prec] = dict(ms=ms, steps=steps_done, phases=phases, launches=launches, info=info,
                              col=col if prec == "mixed" else None)
@@ -249,13 +263,12 @@ def run_ours(args):
     mixed = results["mixed"]
     fp64 = results["fp64"]
     S, L = prob.S, prob.L
-    ms_step = mixed["ms"] / mixed["steps"]
-    value = 1e3 / ms_step * ws
-    fp64_ms_step = fp64["ms"] / fp64["steps"]
+    value, ms_step = whole_job_rate(mixed["ms"] / mixed["steps"], ws, dev)
+    fp64_value, fp64_ms_step = whole_job_rate(fp64["ms"] / fp64["steps"], ws, dev)
 
     def roofline(res, dtype):
         ph = res["phases"]
-        fac_ms, fac_calls = ph["factor"]
+        fac_ms, fac_calls = ph["factor"]          # mixed mode: the FP32 inversion only (FP64 is "fallback")
         flops = 2.0 * S ** 3 * L + 3.0 * S * S * (L - 1)      # Gauss-Jordan inversions + Schur updates
         avg_s = fac_ms / max(fac_calls, 1) * 1e-3
         achieved = flops / avg_s / 1e12
@@ -297,13 +310,14 @@ def run_ours(args):
                        "precision": "mixed: FP32 block inversions, FP64 FGMRES on the FP64 operator",
                        "l2": "inputs larger than L2: FP32 blocks 217 MB per step (FP64 433 MB)",
                        "start": "initial state, dt0 1e-8 s, adaptive dt", "parallelism": f"replicas x{ws}",
-                       "factorization": tuning},
-            "fp64": {"value": 1e3 / fp64_ms_step * ws, "unit": UNIT, "ms_per_step": fp64_ms_step,
+                       "factorization": tuning, "tuning_ms_per_layer": tables},
+            "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms_step,
                      "steps": fp64["steps"], "speedup_mixed_over_fp64": fp64_ms_step / ms_step},
             "roofline": roofline(mixed, "f32"),
             "roofline_fp64": roofline(fp64, "f64"),
             "phases_ms": ph, "phases_ms_fp64": ph64,
             "solver_iters_per_step": mixed["info"].solver_iters / mixed["steps"],
+            "fp64_fallback_steps": int(mixed["info"].fp64_steps),
             "cpu_baseline": cpu,
             "e2e": {"value": ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": L * S * 8,
                     "d2h_bytes_per_step": L * S * 8},
@@ -317,6 +331,205 @@ def run_ours(args):
     return 0
 
 
+def batch_problems(n=64, seed=0):
+    """64 uneven columns: S from {96, 250, 594}, L uniform in 80..200, T_eq U[800, 2500] K."""
+    import numpy as np
+    from paper_2512_06729_gb300 import synth
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        S = int(rng.choice([96, 250, 594]))
+        L = int(rng.integers(80, 201))
+        T_eq = float(rng.uniform(800.0, 2500.0))
+        out.append(synth.sweep_column(S, L, T_eq, 1.0, 1.0, seed=100 + i))
+    return out
+
+
+def run_batch(args):
+    """Batched uneven columns: column-steps/s of the whole batch (mixed precision)."""
+    import torch
+    from paper_2512_06729_gb300 import autotune
+    from paper_2512_06729_gb300 import build as xkbuild
+    from paper_2512_06729_gb300 import xk
+    xkbuild.build()
+    probs = batch_problems(args.columns)
+    tuning = {}
+    for p in probs:
+        if p.S not in tuning:
+            tuning[p.S] = {} if args.no_tune else (autotune.tuned(p.S, "mixed") or autotune.tune(p, "mixed")[0])
+    b = xk.Batch(200 << 30, len(probs))
+    cols = []
+    for p in probs:
+        kw = {k: v for k, v in tuning[p.S].items() if k != "factor_ctas"}   # the batch shares the SMs
+        c = xk.Column(p, "mixed", gmres_restart=10, gmres_max_iter=10, reuse_factorization=1, **kw)
+        c.set_mixing_ratios(p.f0)
+        assert b.add(c, 1e-8) is not None
+        cols.append(c)
+    for _ in range(args.warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = xk.Column.lib_launches()
+    with ClockSampler(0) as cs:
+        start.record()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.step(1)
+        t1 = time.perf_counter()
+        end.record()
+        torch.cuda.synchronize()
+    launches = xk.Column.lib_launches() - n0
+    wall = t1 - t0
+    col_steps = len(probs) * args.steps
+    sizes = {}
+    for p in probs:
+        sizes[p.S] = sizes.get(p.S, 0) + 1
+    line = {
+        "metric": "column-steps/s, 64 uneven columns (S in {96, 250, 594}, L 80..200) batched on one GPU",
+        "value": col_steps / wall, "unit": "column-steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "batch-64-uneven", "columns": len(probs), "species_counts": sizes,
+                   "layers_total": int(sum(p.L for p in probs)), "precision": "mixed, FP64 reuse",
+                   "streams": "one per column", "factor_ctas_per_column": max(1, 152 // len(probs)),
+                   "factorization": {str(k): v for k, v in tuning.items()}},
+        "gpu_launches": int(launches), "clocks": cs.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def run_serving(args):
+    """Continuous batching of steady-state requests from a planet-parameter sweep."""
+    import torch
+    from paper_2512_06729_gb300 import build as xkbuild
+    from paper_2512_06729_gb300 import serving
+    xkbuild.build()
+    reqs = serving.sweep_requests(args.requests, args.rate, seed=0)
+    srv = serving.Server(200 << 30, args.slots, precision="mixed", chunk=8,
+                         column_kw=dict(reuse_factorization=1, gmres_restart=10, gmres_max_iter=10))
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    summ = serving.summarize(res, wall)
+    line = {
+        "metric": "serving: time to steady state p50/p99 (s) and solves/s, sweep requests 60/30/10 % of 96/250/594 sp",
+        "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": summ["steps_total"],
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "serving-sweep", "requests": args.requests, "rate_per_s": args.rate,
+                   "slots": args.slots, "layers": 150},
+        "serving": summ,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_steady(args):
+    """Time to steady state of the 594 x 150 column: mixed path (FP64 factorization reused as the
+    FGMRES preconditioner once steps go to FP64) against the plain FP64 path, the two end states
+    compared, and the oracle's own linear step at the FP64 end state as a check of the fixed point."""
+    import numpy as np
+    import torch
+    from paper_2512_06729_gb300 import build as xkbuild
+    from paper_2512_06729_gb300 import synth, xk
+    xkbuild.build()
+    prob = synth.full_column()
+    stream = torch.cuda.current_stream()
+    runs = {}
+    variants = {"mixed": ("mixed", dict(reuse_factorization=1)), "fp64": ("fp64", {})}
+    for name in args.variants.split(","):
+        prec, kw = variants[name]
+        col = xk.Column(prob, prec, **kw)
+        col.set_mixing_ratios(prob.f0)
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        t0 = time.perf_counter()
+        steps = acc = fp64_steps = iters = 0
+        info = None
+        # in chunks, so that a run that would exceed the time limit stops and reports how far it got
+        while steps < args.max_steps and time.perf_counter() - t0 < args.time_limit:
+            info = col.run_to_steady(1e-8 if steps == 0 else 0.0, min(50, args.max_steps - steps))
+            steps += int(info.steps)
+            acc += int(info.accepted)
+            fp64_steps += int(info.fp64_steps)
+            iters += int(info.solver_iters)
+            if info.converged or info.steps == 0:
+                break
+        end.record(stream)
+        torch.cuda.synchronize()
+        runs[name] = dict(s=start.elapsed_time(end) / 1e3, wall=time.perf_counter() - t0, steps=steps,
+                          accepted=acc, converged=int(info.converged), t_model=float(info.t), dt=float(info.dt),
+                          fp64_steps=fp64_steps, iters=iters, n=col.get_state())
+        col.close()
+        del col
+        torch.cuda.empty_cache()
+    rel = None
+    if "mixed" in runs and "fp64" in runs:
+        nm, nf = runs["mixed"]["n"], runs["fp64"]["n"]
+        ng = nf.sum(axis=1)
+        keep = nf > 1e-20 * ng[:, None]
+        rel = float(np.max(np.abs(nm - nf)[keep] / nf[keep]))
+    check = None
+    nf = runs["fp64"]["n"] if "fp64" in runs else next(iter(runs.values()))["n"]
+    if not args.no_cpu and any(r["converged"] for r in runs.values()):
+        from oracle.oracle import Oracle
+        o = Oracle(prob)
+        ong = o.grid()[0]
+        t0 = time.perf_counter()
+        d = o.step_delta(nf, 1e8)
+        s = np.maximum(nf, 1e-20 * ong[:, None])
+        okeep = nf > 1e-20 * ong[:, None]
+        check = {"oracle_step_max_rel_change": float(np.max(np.abs(d)[okeep] / s[okeep])),
+                 "steady_tol": 1e-3, "oracle_s": time.perf_counter() - t0}
+    first = next(iter(runs.values()))
+    line = {
+        "metric": "time to steady state (s), 594 sp x 150 layers, mixed (FP64 reuse) vs FP64",
+        "value": first["s"] if first["converged"] else None, "unit": "s", "n_gpus": 1, "steps": first["steps"],
+        "warmup": 0, "ms_per_step": first["s"] * 1e3 / max(first["steps"], 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "species": prob.S, "reactions": prob.R, "layers": prob.L,
+                   "start": "initial state, dt0 1e-8 s", "steady": "dt >= 1e8 s and max relative change < 1e-3"},
+        "runs": {k: {kk: vv for kk, vv in v.items() if kk != "n"} for k, v in runs.items()},
+        "mixed_vs_fp64_max_rel": rel,
+        "oracle_check": check,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_kernels(args):
+    """Linear steps (rates to solve, no step control) of one precision on the 594 x 150 column at
+    library defaults: per-phase device times for the rooflines, and a short command to profile."""
+    import torch
+    from paper_2512_06729_gb300 import build as xkbuild
+    from paper_2512_06729_gb300 import synth, xk
+    xkbuild.build()
+    prob = synth.full_column()
+    col = xk.Column(prob, args.precision)
+    col.set_mixing_ratios(prob.f0)
+    n = col.get_state(device=True)
+    for _ in range(args.warmup):
+        col.step_delta(n, args.dt)
+    col.profile(True)
+    n0 = xk.Column.lib_launches()
+    iters = []
+    for _ in range(args.steps):
+        iters.append(col.step_delta(n, args.dt)[1])
+    torch.cuda.synchronize()
+    ph = col.profile_read()
+    line = {"mode": "kernels", "precision": args.precision, "dt": args.dt, "steps": args.steps,
+            "launches": xk.Column.lib_launches() - n0, "solver_iters": iters,
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in ph.items()},
+            "phase_calls": {k: v[1] for k, v in ph.items()}}
+    print(json.dumps(line), flush=True)
+    col.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,9 +537,31 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels"],
+                    help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
+                         "requests; steady: time to steady state of the 594 x 150 column")
+    ap.add_argument("--max-steps", type=int, default=5000)
+    ap.add_argument("--variants", default="mixed,fp64", help="--mode steady: paths to run, in order")
+    ap.add_argument("--time-limit", type=float, default=600.0, help="--mode steady: seconds per path")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="--mode kernels")
+    ap.add_argument("--dt", type=float, default=1e-2, help="--mode kernels: step size of the linear steps")
+    ap.add_argument("--columns", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=12)
+    ap.add_argument("--rate", type=float, default=1.0)
+    ap.add_argument("--slots", type=int, default=12)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serving":
+        return run_serving(args)
+    if args.mode == "steady":
+        return run_steady(args)
+    if args.mode == "kernels":
+        return run_kernels(args)
     return run_ours(args)
 
 

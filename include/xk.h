@@ -79,17 +79,29 @@ typedef struct {
     /* mixed precision solver: */
     int gmres_restart;    /* Krylov basis size m of FGMRES(m) */
     int gmres_max_iter;   /* total iterations per linear solve */
-    double gmres_tol;     /* relative residual target in the scaled (relative) variables */
+    double gmres_tol;     /* relative residual target in the scaled (relative) variables (1e-15) */
     /* factorization tuning (0: chosen by the library / autotuner) */
     int panel_width;      /* columns per panel of the blocked Gauss-Jordan block inversion */
     int factor_ctas;      /* CTAs of the persistent factorization kernel per column */
-    int fp32_pivoting;    /* mixed mode: 0 (default) FP32 inversion without row pivoting (one warp
-                             inverts each diagonal panel block; look-ahead, one grid barrier per
-                             panel), 1 with implicit partial pivoting */
+    int fp32_pivoting;    /* mixed mode: 0 (default) FP32 inversion without row pivoting, 1 with
+                             implicit partial pivoting (grid-wide kernel) */
     int reuse_factorization; /* mixed mode: 1 = once steps go to FP64, precondition FGMRES on the
                              current FP64 operator with the last FP64 factorization (rescaled to
                              the current variables) and refactor only when FGMRES misses its
                              tolerance; 0 (default) = factor every step */
+    int cluster_size;     /* mixed mode without pivoting: CTAs of the thread-block cluster that
+                             holds each layer's FP32 block in distributed shared memory while it is
+                             inverted (1..16; 0 = the largest that fits; -1 = grid-wide kernel with
+                             the block in global memory).  panel_width 8 or 16 applies (default 8). */
+    int twisted;          /* mixed mode, cluster-resident inversion: 1 (default) eliminates from both
+                             ends of the column at once on two clusters and meets in the middle
+                             layer (when two clusters fit and there are at least 3 layers); 0 keeps
+                             the single top-down chain */
+    int fp64_panel;       /* FP64 block inversion: 0 (default) runs Gauss-Jordan with partial
+                             pivoting on each panel column by column on one CTA (panel width 8 or
+                             16); 1 chooses each panel's pivots first on one CTA (elimination of the
+                             unpivoted rows only) and forms the panel's multipliers on all CTAs by
+                             triangular solves with the pivot block's LU factors (8, 16 or 32) */
 } xk_config;
 
 typedef struct {
@@ -167,10 +179,18 @@ XK_API int xk_set_state(xk_ctx *ctx, const double *n, int on_device);
 XK_API int xk_set_mixing_ratios(xk_ctx *ctx, const double *f, int on_device);
 XK_API int xk_get_state(xk_ctx *ctx, double *n, int on_device);
 
+/* Gibbs energies, equilibrium constants and forward/reverse rate coefficients
+ * of every thermal reaction in every layer (Sec. 2.3, Appendix A) for the
+ * loaded atmosphere, kept in the workspace.  They depend on T and P only, so
+ * steps evaluate them once (lazily if this is not called) until a network or
+ * atmosphere is loaded again.  Synchronizes the stream. */
+XK_API int xk_set_rate_coefficients(xk_ctx *ctx);
+
 /* One controlled implicit step of size dt (dt <= 0: use the context's
- * current dt).  Evaluates rate coefficients, photolysis, residual, Jacobian,
- * factorization and solve, then accepts (n updated, negatives clipped to 0)
- * or rejects (n unchanged).  Synchronizes the stream and fills *info. */
+ * current dt).  Evaluates photolysis, residual, Jacobian, factorization and
+ * solve (rate coefficients once, see above), then accepts (n updated,
+ * negatives clipped to 0) or rejects (n unchanged).  Synchronizes the stream
+ * and fills *info. */
 XK_API int xk_step(xk_ctx *ctx, double dt, xk_step_info *info);
 
 /* Steps from dt0 (dt0 <= 0: keep the current dt) until the steady-state test
@@ -272,7 +292,9 @@ XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *l
  * Phases: XK_PH_RATES (Gibbs energies + rate coefficients), XK_PH_PHOTO,
  * XK_PH_REACTION (w and its derivatives), XK_PH_RESIDUAL, XK_PH_JACOBIAN,
  * XK_PH_FACTOR (block inversions), XK_PH_SOLVE (block sweeps, or FGMRES with
- * its sweeps in mixed mode), XK_PH_CONTROL (accept/reject/update).
+ * its sweeps in mixed mode), XK_PH_CONTROL (accept/reject/update),
+ * XK_PH_FALLBACK (mixed mode only: the FP64 Jacobian, factorization and
+ * solve, whose kernels exit at once on steps that FGMRES solved).
  * xk_profile(ctx, 1) starts recording (and clears totals); 0 stops.
  * xk_profile_read fills ms[n] with the summed device time of each phase and
  * calls[n] with the number of timed occurrences, synchronizing the stream.
@@ -285,7 +307,8 @@ XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *l
 #define XK_PH_FACTOR 5
 #define XK_PH_SOLVE 6
 #define XK_PH_CONTROL 7
-#define XK_PH_COUNT 8
+#define XK_PH_FALLBACK 8
+#define XK_PH_COUNT 9
 XK_API int xk_profile(xk_ctx *ctx, int enable);
 XK_API int xk_profile_read(xk_ctx *ctx, double *ms, long long *calls, int n);
 /* Number of CUDA kernels this library has launched since it was loaded (all

@@ -1,23 +1,28 @@
-"""Autotuner for the block-inversion kernel: picks the panel width and the
-number of CTAs of the persistent factorization per species count S and
-precision, by timing the library's own factorization phase (CUDA events
-around it, xk_profile) on a short slice of the column.
+"""Autotuner for the block-inversion kernels: picks, per species count S and
+precision, the panel width and either the number of CTAs of the grid-wide
+persistent factorization or the size of the thread-block cluster that holds
+each block in distributed shared memory (mixed precision), by timing the
+library's own factorization phase (CUDA events around it, xk_profile) on a
+short slice of the column.
 
 Results are cached per (GPU name, S, precision) in a JSON file beside the
-built library, and applied through xk_config.panel_width / factor_ctas.
+built library, and applied through xk_config (panel_width, factor_ctas,
+cluster_size).
 """
 from __future__ import annotations
 
 import json
 import os
 
-import numpy as np
-
 from . import build as _build
 
 CANDIDATES = {
-    "fp64": [(8, 76), (8, 152), (16, 152), (4, 152)],
-    "mixed": [(16, 76), (16, 152), (32, 38), (32, 76), (32, 152)],
+    "fp64": [dict(panel_width=8, factor_ctas=152), dict(panel_width=16, factor_ctas=152),
+             dict(panel_width=8, factor_ctas=76), dict(fp64_panel=1, panel_width=8, factor_ctas=152)],
+    "mixed": [dict(cluster_size=16, panel_width=16), dict(cluster_size=12, panel_width=16),
+              dict(cluster_size=8, panel_width=16), dict(cluster_size=16, panel_width=8),
+              dict(cluster_size=-1, panel_width=16, factor_ctas=152),
+              dict(cluster_size=-1, panel_width=32, factor_ctas=76)],
 }
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 
@@ -36,16 +41,16 @@ def _load():
 
 
 def _key(S, precision):
-    return f"{_gpu_name()}|S={S}|{precision}"
+    return f"{_gpu_name()}|S={S}|{precision}|v2"
 
 
-def measure(prob, precision, nb, ctas, layers=6, reps=2):
+def measure(prob, precision, params, layers=6, reps=2):
     """Factorization time per layer (ms) for one configuration."""
     import torch
     from . import xk
     sub = prob.replace(P_bar=prob.P_bar[:layers].copy(), T=prob.T[:layers].copy(),
                        Kzz=prob.Kzz[:layers].copy(), f0=prob.f0[:layers].copy())
-    col = xk.Column(sub, precision, panel_width=nb, factor_ctas=ctas)
+    col = xk.Column(sub, precision, **params)
     col.set_mixing_ratios(sub.f0)
     n = col.get_state(device=True)
     col.step_delta(n, 1e-2)                   # warm-up (first launch, attribute set-up)
@@ -59,36 +64,36 @@ def measure(prob, precision, nb, ctas, layers=6, reps=2):
 
 
 def tune(prob, precision, layers=6, verbose=False):
-    """Time every candidate, cache and return (nb, ctas, table)."""
+    """Time every candidate, cache and return (params, table)."""
     table = []
-    for nb, ctas in CANDIDATES[precision]:
+    for params in CANDIDATES[precision]:
         try:
-            t = measure(prob, precision, nb, ctas, layers)
-        except Exception as e:          # a candidate the library rejects (shared memory, size)
+            t = measure(prob, precision, params, layers)
+        except Exception as e:          # a candidate the library rejects (shared memory, cluster size)
             if verbose:
-                print(f"  nb={nb} ctas={ctas}: {e}")
+                print(f"  {params}: {e}")
             continue
-        table.append((t, nb, ctas))
+        table.append((t, params))
         if verbose:
-            print(f"  {precision} S={prob.S} nb={nb:3d} ctas={ctas:4d}: {t:.3f} ms/layer", flush=True)
+            print(f"  {precision} S={prob.S} {params}: {t:.3f} ms/layer", flush=True)
     if not table:
         raise RuntimeError("no factorization configuration ran")
-    t, nb, ctas = min(table)
+    t, params = min(table, key=lambda x: x[0])
     data = _load()
-    data[_key(prob.S, precision)] = {"panel_width": nb, "factor_ctas": ctas, "ms_per_layer": t,
-                                     "table": [[x[1], x[2], x[0]] for x in table]}
+    data[_key(prob.S, precision)] = {"params": params, "ms_per_layer": t,
+                                     "table": [[x[1], x[0]] for x in table]}
     os.makedirs(os.path.dirname(CACHE), exist_ok=True)
     with open(CACHE, "w") as f:
         json.dump(data, f, indent=1)
-    return nb, ctas, table
+    return params, table
 
 
 def tuned(S, precision):
-    """Cached choice for (S, precision), or {} when not tuned yet."""
+    """Cached choice for (S, precision) as xk_config keywords, or {} when not tuned yet."""
     e = _load().get(_key(S, precision))
     if not e:
         return {}
-    return {"panel_width": int(e["panel_width"]), "factor_ctas": int(e["factor_ctas"])}
+    return {k: int(v) for k, v in e["params"].items()}
 
 
 if __name__ == "__main__":
@@ -99,5 +104,5 @@ if __name__ == "__main__":
     for mk in (synth.full_column, synth.chons_column):
         p = mk()
         for prec in ("mixed", "fp64"):
-            print(prec, p.S, tune(p, prec, verbose=True)[:2], flush=True)
+            print(prec, p.S, tune(p, prec, verbose=True)[0], flush=True)
     print(json.dumps(_load(), indent=1))

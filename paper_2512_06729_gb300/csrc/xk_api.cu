@@ -26,6 +26,7 @@ struct xk_ctx {
     std::vector<double> mass, arr, troe, nasa, lam, dlam, J0, sigma, sigma_abs, P, T, Kzz, dcoef;
     double mu = 0.5, tf = 0.5, g = 0, mbar = 0, alpha_T = 0;
     bool have_net = false, have_photo = false, have_atm = false;
+    bool rates_valid = false;      // k_f, k_r of the loaded network and atmosphere are in the workspace
     // host index structures
     std::vector<int> yp, yent, jp, jcol, jrs, abs_sp;
     std::vector<double> sig_abs_c;
@@ -38,6 +39,9 @@ struct xk_ctx {
     double *A64 = nullptr, *lo64 = nullptr, *up64 = nullptr;
     float *A32 = nullptr, *lo32 = nullptr, *up32 = nullptr;
     int *ridx = nullptr, *sig = nullptr, *pinfo = nullptr;
+    int *ridx32 = nullptr, *sig32 = nullptr;   // row/column pivots of the FP32 inversion
+    double *dinv = nullptr;                    // FP64 factorization: LU factors of the current panel's pivot block
+    double *ymid = nullptr;                    // twisted sweeps: the two products that meet at the middle layer
     unsigned *bar = nullptr;
     double *gsol = nullptr;
     // FGMRES buffers
@@ -49,6 +53,12 @@ struct xk_ctx {
     GmState *gm = nullptr;
     FactorPlan plan{};     // plan of the context's precision
     FactorPlan plan64{};   // FP64 plan (fallback of the mixed path)
+    ClusterPlan cplan{};   // cluster-resident FP32 inversion (mixed path, no pivoting)
+    bool use_cluster = false;
+    SolvePlan splan{};     // sweeps with those inverses on one cluster
+    bool use_cluster_solve = false;
+    SolvePlan splan64{};   // sweeps with the pivoted FP64 inverses on one cluster
+    bool use_cluster_solve64 = false;
     bool ready = false;
     // tracing
     bool prof = false;
@@ -239,7 +249,7 @@ size_t layout(xk_ctx *c, char *base)
         c->gw = b.take<double>(LS);
         c->rowd = b.take<double>(LS);
         c->bhat = b.take<double>(LS);
-        c->gbuf = b.take<float>(2 * (size_t)S * 32);
+        c->gbuf = b.take<float>(4 * (size_t)S * 32);
         c->s64 = b.take<double>(LS);
         c->pin = b.take<double>(LS);
         c->pout = b.take<double>(LS);
@@ -249,10 +259,14 @@ size_t layout(xk_ctx *c, char *base)
         c->partials = b.take<double>((size_t)kGmPartialBlocks * (kMaxBasis + 1));
         c->counter = b.take<unsigned>(8);
         c->gm = b.take<GmState>(1);
+        c->ymid = b.take<double>(2 * (size_t)S);
+        c->ridx32 = b.take<int>(LS);    // the FP64 factorization's pivots stay intact for reuse
+        c->sig32 = b.take<int>(LS);
     }
     c->ridx = b.take<int>(LS);
     c->sig = b.take<int>(LS);
     c->pinfo = b.take<int>(1 + 4 * 64);
+    c->dinv = b.take<double>(32 * 32);
     c->bar = b.take<unsigned>(8);
     c->ctl = b.take<Ctl>(1);
     c->ctl_aux = b.take<Ctl>(1);
@@ -276,9 +290,45 @@ BlockSys<double> sys64(xk_ctx *c)
 BlockSys<float> sys32(xk_ctx *c)
 {
     BlockSys<float> s;
-    s.D = c->A32; s.lo = c->lo32; s.up = c->up32; s.perm = c->ridx; s.iperm = c->sig;
+    s.D = c->A32; s.lo = c->lo32; s.up = c->up32; s.perm = c->ridx32; s.iperm = c->sig32;
     s.pinfo = c->pinfo; s.bar = c->bar; s.L = c->L; s.S = c->S; s.ld = c->col.ld;
     return s;
+}
+
+// FP32 block inversions of the mixed path
+cudaError_t factor32(xk_ctx *c, Ctl *ctl, const int *skip)
+{
+    if (c->cfg.fp32_pivoting) return launch_factor<float>(sys32(c), c->plan, ctl, c->st, skip);
+    if (c->use_cluster) return launch_factor_cluster(sys32(c), c->cplan, c->gbuf, ctl, c->st, skip);
+    return launch_factor_nopivot(sys32(c), c->plan, c->gbuf, ctl, c->st, skip);
+}
+
+// sweeps with the FP32 inverses
+cudaError_t solve32(xk_ctx *c, const double *b, double *x, Ctl *ctl, cudaStream_t st, const double *bscale,
+                    const int *skip)
+{
+    if (c->use_cluster_solve && c->use_cluster && cluster_twisted(c->cplan, c->L) && c->splan.twisted)
+        return launch_solve_twisted(sys32(c), c->splan, b, x, c->gsol, c->ymid, ctl, st, bscale, skip);
+    if (c->use_cluster_solve && !(c->use_cluster && cluster_twisted(c->cplan, c->L)))
+        return launch_solve_cluster<float>(sys32(c), c->splan, false, b, x, c->gsol, ctl, st, bscale, skip);
+    return launch_solve<float>(sys32(c), c->plan, b, x, c->gsol, ctl, st, bscale, skip);
+}
+
+// sweeps with the (pivoted) FP64 inverses
+cudaError_t solve64(xk_ctx *c, const FactorPlan &plan, const double *b, double *x, Ctl *ctl, cudaStream_t st,
+                    const double *bscale, const int *skip, const double *xscale)
+{
+    if (c->use_cluster_solve64)
+        return launch_solve_cluster<double>(sys64(c), c->splan64, true, b, x, c->gsol, ctl, st, bscale, skip, xscale);
+    return launch_solve<double>(sys64(c), plan, b, x, c->gsol, ctl, st, bscale, skip, xscale);
+}
+
+// FP64 plans: column-by-column panel factorization (k_factor), or each panel's pivots chosen
+// first (k_factor_pv) when the context asks for it
+void set_preview(xk_ctx *c, FactorPlan *p)
+{
+    p->preview = c->cfg.fp64_panel ? 1 : 0;
+    p->dinv = c->dinv;
 }
 
 int need_ready(xk_ctx *c)
@@ -289,14 +339,19 @@ int need_ready(xk_ctx *c)
     return XK_OK;
 }
 
-// Enqueue rows a1-a6 and the linear solve for state col.n (or n_override),
+// Enqueue thermochemistry, rates, photolysis, residual, Jacobian and the linear solve for state col.n (or n_override),
 // writing the unscaled delta into delta_out.  ctl gates every kernel.
 int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *delta_out, Ctl *ctl)
 {
     Col col = c->col;
     col.n = const_cast<double *>(n);
     cudaStream_t st = c->st;
-    { PhaseMark m(c, XK_PH_RATES); launch_rates(col, st); }
+    // Gibbs energies and rate coefficients depend on the atmosphere only: evaluated once
+    if (!c->rates_valid) {
+        PhaseMark m(c, XK_PH_RATES);
+        launch_rates(col, st);
+        c->rates_valid = true;
+    }
     { PhaseMark m(c, XK_PH_PHOTO); launch_photolysis(col, n, st); }
     { PhaseMark m(c, XK_PH_REACTION); launch_reaction_terms(col, n, st); }
     { PhaseMark m(c, XK_PH_RESIDUAL); launch_residual(col, n, col.F, ctl, c->cfg.f_floor, st); }
@@ -305,7 +360,7 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, dt_override, 1, c->A64, c->lo64, c->up64, st); }
         { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan, ctl, st); }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-        { PhaseMark m(c, XK_PH_SOLVE); e = launch_solve<double>(sys64(c), c->plan, col.b, col.x, c->gsol, ctl, st); }
+        { PhaseMark m(c, XK_PH_SOLVE); e = solve64(c, c->plan, col.b, col.x, ctl, st, nullptr, nullptr, nullptr); }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     } else {
         if (dt_override > 0.0) return fail(c, XK_EINVAL, "mixed path reads dt from the control block");
@@ -321,8 +376,7 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         }
         {
             PhaseMark m(c, XK_PH_FACTOR);
-            e = c->cfg.fp32_pivoting ? launch_factor<float>(sys32(c), c->plan, ctl, st, skip32)
-                                     : launch_factor_nopivot(sys32(c), c->plan, c->gbuf, ctl, st, skip32);
+            e = factor32(c, ctl, skip32);
         }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
         GmArgs a;
@@ -332,10 +386,7 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         a.tol = c->cfg.gmres_tol;
         a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
         a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
-        BlockSys<float> s32 = sys32(c);
-        BlockSys<double> s64s = sys64(c);
-        FactorPlan plan = c->plan, plan64 = c->plan64;
-        double *gsol = c->gsol;
+        FactorPlan plan64 = c->plan64;
         const double *rowd = c->rowd, *pin = c->pin, *pout = c->pout;
         a.matvec = [col, ctl, rowd](const double *x, double *y, const int *skip, cudaStream_t s) {
             launch_jv(col, ctl, x, y, rowd, skip, s);
@@ -343,29 +394,32 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         // FGMRES around the FP32 inversion
         a.skip_solve = skip32;
         a.role = 0;
-        a.precond = [s32, plan, gsol, ctl, rowd](const double *v, double *z, const int *skip, cudaStream_t s) {
-            launch_solve<float>(s32, plan, v, z, gsol, ctl, s, rowd, skip);
+        a.precond = [c, ctl, rowd](const double *v, double *z, const int *skip, cudaStream_t s) {
+            solve32(c, v, z, ctl, s, rowd, skip);
         };
         { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
         // FGMRES around the last FP64 factorization, rescaled to this step's variables
-        launch_reuse_scales(N, rowd, col.s, c->s64, c->pin, c->pout, ctl, st);
-        a.skip_solve = &ctl->skip_reuse;
-        a.role = 1;
-        a.precond = [s64s, plan64, gsol, ctl, pin, pout](const double *v, double *z, const int *skip, cudaStream_t s) {
-            launch_solve<double>(s64s, plan64, v, z, gsol, ctl, s, pin, skip, pout);
-        };
-        { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
+        if (c->cfg.reuse_factorization) {
+            launch_reuse_scales(N, rowd, col.s, c->s64, c->pin, c->pout, ctl, st);
+            a.skip_solve = &ctl->skip_reuse;
+            a.role = 1;
+            a.precond = [c, plan64, ctl, pin, pout](const double *v, double *z, const int *skip, cudaStream_t s) {
+                solve64(c, plan64, v, z, ctl, s, pin, skip, pout);
+            };
+            { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
+        }
         // FP64 factorization and direct solve, gated on the device by ctl->skip64
         const int *skip64 = &ctl->skip64;
-        { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, 0.0, 1, c->A64, c->lo64, c->up64, st, skip64); }
-        { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan64, ctl, st, skip64); }
-        if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-        launch_after_refactor(N, col.s, c->s64, ctl, st);
         {
-            PhaseMark m(c, XK_PH_SOLVE);
-            e = launch_solve<double>(sys64(c), c->plan64, col.b, col.x, c->gsol, ctl, st, nullptr, skip64);
+            PhaseMark m(c, XK_PH_FALLBACK);
+            launch_jacobian64(col, n, ctl, 0.0, 1, c->A64, c->lo64, c->up64, st, skip64);
+            e = launch_factor<double>(sys64(c), c->plan64, ctl, st, skip64);
+            if (e == cudaSuccess) {
+                launch_after_refactor(N, col.s, c->s64, ctl, st);
+                e = solve64(c, c->plan64, col.b, col.x, ctl, st, nullptr, skip64, nullptr);
+            }
         }
-        if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return fail(c, XK_ECUDA, "FP64 fallback launch: %s", cudaGetErrorString(e));
     }
     launch_unscale(col, col.x, delta_out, st);
     return cuda_check(c, "step enqueue");
@@ -410,8 +464,8 @@ int xk_config_init(xk_config *cfg)
     cfg->stream = nullptr;
     cfg->dt_max = 1e8; cfg->rel_reject = 1.0; cfg->rel_target = 0.5; cfg->grow_max = 3.0; cfg->shrink_min = 0.5;
     cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
-    cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-14;
-    cfg->panel_width = 0; cfg->factor_ctas = 0;
+    cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-15;
+    cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1;
     return XK_OK;
 }
 
@@ -490,6 +544,7 @@ int xk_load_network(xk_ctx *c, int S, int E, int R, const int *elem, const doubl
     c->form.assign(form, form + R);
     c->nasa.assign(nasa, nasa + 15 * (size_t)S);
     c->have_net = true;
+    c->rates_valid = false;
     c->have_photo = false;
     c->ready = false;
     c->Rph = 0;
@@ -548,6 +603,7 @@ int xk_load_atmosphere(xk_ctx *c, int L, const double *P_bar, const double *T, c
     c->dcoef.assign(dcoef, dcoef + c->S);
     c->g = g; c->mbar = mbar; c->alpha_T = alpha_T;
     c->have_atm = true;
+    c->rates_valid = false;
     c->ready = false;
     return XK_OK;
 }
@@ -577,11 +633,34 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     layout(c, c->ws);
     int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
     int nbh = c->cfg.panel_width;
-    if (sz == 4 && !c->cfg.fp32_pivoting && nbh == 0) nbh = 32;
+    if (sz == 4 && !c->cfg.fp32_pivoting && nbh != 16) nbh = 32;   // grid kernel widths (8 is cluster-only)
+    if (sz == 8 && nbh == 0) nbh = 8;
     if (factor_plan(c->S, sz, nbh, c->cfg.factor_ctas, &c->plan) != 0)
         return fail(c, XK_EINVAL, "no factorization plan for S=%d (panel %d)", c->S, c->cfg.panel_width);
-    if (factor_plan(c->S, 8, 0, 0, &c->plan64) != 0)
+    // FP64 factorization (the path itself, or the fallback of the mixed path): the context's
+    // panel width and CTA count in FP64 mode
+    const int nb64 = sz == 8 ? nbh : 8;
+    if (factor_plan(c->S, 8, nb64, sz == 8 ? c->cfg.factor_ctas : 0, &c->plan64) != 0)
         return fail(c, XK_EINVAL, "no FP64 factorization plan for S=%d", c->S);
+    set_preview(c, &c->plan64);
+    if (sz == 8) set_preview(c, &c->plan);
+    c->use_cluster = false;
+    c->use_cluster_solve = false;
+    c->use_cluster_solve64 = c->cfg.cluster_size >= 0 && solve_cluster_plan(c->S, 8, &c->splan64) == 0;
+    if (sz == 4 && !c->cfg.fp32_pivoting && c->cfg.cluster_size >= 0) {
+        const int nbc = c->cfg.panel_width == 16 ? 16 : 8;
+        // the panel rows go through gbuf (4 x S x 32 floats, enough for 4 x 16 x round_up(S, 4))
+        if (cluster_plan(c->S, nbc, c->cfg.cluster_size, &c->cplan) == 0 &&
+            cluster_ubuf_floats(c->cplan) <= 4 * (size_t)c->S * 32) {
+            c->use_cluster = true;
+            c->use_cluster_solve = solve_cluster_plan(c->S, 4, &c->splan) == 0;
+            // inverses from both ends need the matching sweeps
+            if (!(c->use_cluster_solve && c->splan.twisted) || c->cfg.twisted == 0) c->cplan.twisted = 0;
+        }
+        else if (c->cfg.cluster_size > 0)
+            return fail(c, XK_EINVAL, "no cluster of %d CTAs holds the S=%d block (panel %d)", c->cfg.cluster_size,
+                        c->S, nbc);
+    }
     Col &k = c->col;
     up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
     up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
@@ -604,6 +683,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "upload: %s", cudaGetErrorString(e));
     c->ready = true;
+    c->rates_valid = false;
     return cuda_check(c, "set_workspace");
 }
 
@@ -755,6 +835,15 @@ int xk_eval_thermo(xk_ctx *c, double *grt, double *lnkc)
     return finish_eval(c, "eval_thermo");
 }
 
+int xk_set_rate_coefficients(xk_ctx *c)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    launch_rates(c->col, c->st);
+    c->rates_valid = true;
+    return finish_eval(c, "set_rate_coefficients");
+}
+
 int xk_eval_rates(xk_ctx *c, double *kf, double *kr)
 {
     int rc = need_ready(c);
@@ -826,7 +915,7 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     cudaError_t e = launch_factor<double>(sys64(c), c->plan64, c->ctl_aux, c->st);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-    e = launch_solve<double>(sys64(c), c->plan64, f, x, c->gsol, c->ctl_aux, c->st);
+    e = solve64(c, c->plan64, f, x, c->ctl_aux, c->st, nullptr, nullptr, nullptr);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve"))) return rc;
@@ -848,10 +937,9 @@ int xk_block_solve32(xk_ctx *c, const double *A, const double *lo, const double 
     Ctl init{};
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
-    cudaError_t e = c->cfg.fp32_pivoting ? launch_factor<float>(sys32(c), c->plan, c->ctl_aux, c->st)
-                                         : launch_factor_nopivot(sys32(c), c->plan, c->gbuf, c->ctl_aux, c->st);
+    cudaError_t e = factor32(c, c->ctl_aux, nullptr);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-    e = launch_solve<float>(sys32(c), c->plan, f, x, c->gsol, c->ctl_aux, c->st);
+    e = solve32(c, f, x, c->ctl_aux, c->st, nullptr, nullptr);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve32"))) return rc;
@@ -977,6 +1065,8 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
         s = BatchSlot();
         return fail(c, XK_EINVAL, "no factorization plan for a %d-CTA share", share);
     }
+    set_preview(c, &p64);
+    if (sz == 8) set_preview(c, &p);
     s.ctx = c;
     s.saved_st = c->st;
     s.saved_plan = c->plan;

@@ -172,11 +172,12 @@ __device__ void trailing_update(T *D, const int *pinfo, const int *iperm, int S,
     T *U = (T *)smem;                                  // NB x cw
     for (int q0 = blockIdx.x * cw, qend = min(others, (blockIdx.x + 1) * cw); q0 < qend; q0 += MAXC) {
         const int ncols = min(MAXC, qend - q0);
-        for (int e = tid; e < nb * ncols; e += nthr) {
+        // rows nb..NB-1 of U (ragged last panel) are zero: the update below runs over all NB
+        for (int e = tid; e < NB * ncols; e += nthr) {
             int l = e / ncols, jj = e - l * ncols;
             int q = q0 + jj;
             int j = q < c0 ? q : q + nb;
-            U[l * MAXC + jj] = D[(size_t)pinfo[l] * ld + j];
+            U[l * MAXC + jj] = l < nb ? D[(size_t)pinfo[l] * ld + j] : (T)0;
         }
         __syncthreads();
 #pragma unroll 1
@@ -242,6 +243,184 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl
             if (blockIdx.x == 0) panel_factor<T, NB>(D, perm, iperm, a.pinfo, S, ld, c0, nb, ctl, smem);
             if (!grid_barrier(a.bar, ctl)) return;
             trailing_update<T, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem);
+            if (!grid_barrier(a.bar, ctl)) return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 block inversion with partial pivoting, each panel's pivots chosen first.
+//
+// In panel_factor the sequential part of each panel -- nb columns of pivot
+// search plus Gauss-Jordan elimination of every row over all nb panel columns
+// -- runs in FP64 on one SM, whose FP64 rate (about 2 FMA per clock) makes it
+// the critical path: about S * nb^2 / 2 clocks per panel.  Here CTA 0 only
+// chooses the nb pivot rows: right-looking elimination of the panel restricted
+// to the rows not yet used as pivots and to the columns right of the current
+// one (the same candidates and values as partial pivoting in panel_factor, at
+// about a quarter of the FP64 work), keeping the multipliers, so that the
+// eliminated rows of the pivots are the LU factors of the nb x nb pivot block
+// M.  Every CTA then forms G_r = -D[r][panel] M^-1 for its slice of rows by two
+// triangular solves with those factors (an explicit M^-1 loses accuracy on
+// nearly singular blocks), and the trailing update of the other columns is
+// the one of the column-by-column kernel.
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ void panel_preview(const double *D, int *perm, int *iperm, int *pinfo, double *lu, int S, int ld,
+                              int c0, int nb, Ctl *ctl, unsigned char *smem)
+{
+    constexpr int PS = NB + 1;
+    double *P = (double *)smem;                // S x PS: the panel
+    int *ip = (int *)(P + (size_t)S * PS);     // S: iperm of this layer (-1: not a pivot yet)
+    __shared__ int s_piv[NB];
+    __shared__ unsigned long long red[32];
+    __shared__ int s_cur;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+
+    for (int r = tid; r < S; r += nthr) ip[r] = iperm[r];
+    for (int e = tid; e < S * nb; e += nthr) {
+        const int r = e / nb, j = e - r * nb;
+        P[r * PS + j] = D[(size_t)r * ld + c0 + j];
+    }
+    __syncthreads();
+
+    __shared__ double s_rcp;                   // 1 / pivot of the previous column (one FP64 division per column)
+    int piv_prev = -1;
+    for (int lc = 0; lc <= nb; ++lc) {
+        unsigned long long best = 0ull;
+        const double rcp = lc > 0 ? s_rcp : 0.0;
+        for (int r = tid; r < S; r += nthr) {
+            if (ip[r] >= 0) continue;              // pivot of an earlier panel or column
+            double *Pr = P + r * PS;
+            if (lc > 0) {
+                const double f = Pr[lc - 1] * rcp;
+#pragma unroll
+                for (int j = 1; j < NB; ++j)
+                    if (j >= lc && j < nb) Pr[j] = fma(-f, P[piv_prev * PS + j], Pr[j]);
+                Pr[lc - 1] = f;                    // the multiplier L[r][lc - 1]
+            }
+            if (lc < nb) best = umax64(best, pivot_key(Pr[lc], r));
+        }
+        if (lc == nb) break;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long all = lane < nw ? red[lane] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) all = umax64(all, __shfl_xor_sync(0xffffffffu, all, o));
+            if (lane == 0) {
+                int piv = (int)(~(unsigned)(all & 0xffffffffull));
+                if ((all >> 32) == 0ull || piv < 0 || piv >= S) {
+                    // no nonzero candidate: singular block; keep the bookkeeping consistent
+                    atomicExch(&ctl->err_singular, 1);
+                    piv = -1;
+                    for (int r = 0; r < S && piv < 0; ++r)
+                        if (ip[r] < 0) piv = r;
+                    if (piv < 0) piv = 0;
+                }
+                ip[piv] = c0 + lc;
+                s_piv[lc] = piv;
+                s_cur = piv;
+                const double pv = P[piv * PS + lc];
+                s_rcp = pv != 0.0 ? 1.0 / pv : 0.0;
+            }
+        }
+        __syncthreads();
+        piv_prev = s_cur;
+    }
+    if (tid < nb) {
+        const int pr = s_piv[tid];
+        perm[c0 + tid] = pr;
+        iperm[pr] = c0 + tid;
+        pinfo[tid] = pr;
+    }
+    // LU factors of the pivot block M[i][l] = D[s_piv[i]][c0 + l] in the chosen order: row i of
+    // the eliminated panel holds L[i][0..i) (multipliers) and U[i][i..nb)
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += nthr) {
+        const int i = e / nb, l = e - i * nb;
+        lu[i * NB + l] = P[s_piv[i] * PS + l];
+    }
+    __threadfence();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kFactorThreads, 1) k_factor_pv(BlockSys<double> a, double *lu, Ctl *ctl,
+                                                                  const int *skip)
+{
+    if (ctl->finished || (skip && *skip)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double Ds[NB * NB];
+    __shared__ double Dr_rcp[NB];
+    const int S = a.S, ld = a.ld, L = a.L;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int rs = (S + gridDim.x - 1) / gridDim.x, r0 = blockIdx.x * rs, r1 = min(S, r0 + rs);
+    for (int k = 0; k < L; ++k) {
+        double *D = a.D + (size_t)k * S * ld;
+        int *perm = a.perm + (size_t)k * S;
+        int *iperm = a.iperm + (size_t)k * S;
+        if (k > 0) {
+            // D'_k = A_k - diag(lo_k) D'^-1_{k-1} diag(up_{k-1}), D'^-1[i][j] = B[perm(i)][iperm(j)]
+            const double *Bp = a.D + (size_t)(k - 1) * S * ld;
+            const int *pp = a.perm + (size_t)(k - 1) * S;
+            const int *ipp = a.iperm + (size_t)(k - 1) * S;
+            const double *lo = a.lo + (size_t)k * S;
+            const double *upp = a.up + (size_t)(k - 1) * S;
+            for (long long e = gtid; e < (long long)S * S; e += gstride) {
+                int i = (int)(e / S), j = (int)(e - (long long)i * S);
+                D[(size_t)i * ld + j] -= lo[i] * Bp[(size_t)pp[i] * ld + ipp[j]] * upp[j];
+            }
+        }
+        for (long long i = gtid; i < S; i += gstride) iperm[i] = -1;
+        if (!grid_barrier(a.bar, ctl)) return;
+        for (int c0 = 0; c0 < S; c0 += NB) {
+            const int nb = min(NB, S - c0);
+            if (blockIdx.x == 0) panel_preview<NB>(D, perm, iperm, a.pinfo, lu, S, ld, c0, nb, ctl, smem);
+            if (!grid_barrier(a.bar, ctl)) return;
+            // G_r = -D[r][panel] M^-1 (pivot row p_i of the panel: row i of M^-1), from the LU
+            // factors of M by two triangular solves, G L U = rhs: w U = rhs, then G L = w
+            for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+                const int i = e / NB, l = e - i * NB;
+                Ds[e] = (i < nb && l < nb) ? lu[i * NB + l] : 0.0;
+            }
+            if (threadIdx.x < NB) {
+                const double u = threadIdx.x < nb ? lu[threadIdx.x * NB + threadIdx.x] : 0.0;
+                Dr_rcp[threadIdx.x] = u != 0.0 ? 1.0 / u : 0.0;
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+                double *Dr = D + (size_t)r * ld + c0;
+                const int ipr = iperm[r];
+                const bool piv_row = ipr >= c0 && ipr < c0 + nb;
+                double w[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j >= nb) { w[j] = 0.0; continue; }
+                    double acc = piv_row ? (ipr - c0 == j ? 1.0 : 0.0) : -Dr[j];
+#pragma unroll
+                    for (int k = 0; k < j; ++k) acc = fma(-w[k], Ds[k * NB + j], acc);
+                    w[j] = acc * Dr_rcp[j];
+                }
+#pragma unroll
+                for (int i = NB - 1; i >= 0; --i) {
+                    if (i >= nb) continue;
+                    double g = w[i];
+#pragma unroll
+                    for (int k = i + 1; k < NB; ++k)
+                        if (k < nb) g = fma(-w[k], Ds[k * NB + i], g);
+                    w[i] = g;
+                }
+#pragma unroll
+                for (int l = 0; l < NB; ++l)
+                    if (l < nb) Dr[l] = w[l];
+            }
+            if (!grid_barrier(a.bar, ctl)) return;
+            trailing_update<double, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem);
             if (!grid_barrier(a.bar, ctl)) return;
         }
     }
@@ -377,9 +556,10 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_np(BlockSys<float>
             };
             for (int i0 = 0; i0 < count; i0 += MAXC) {
                 const int ncols = min(MAXC, count - i0);
-                for (int e = tid; e < nb * ncols; e += nthr) {
+                // rows nb..NB-1 of U (ragged last panel) are zero: the update below runs over all NB
+                for (int e = tid; e < NB * ncols; e += nthr) {
                     int l = e / ncols, jj = e - l * ncols;
-                    U[l * MAXC + jj] = val(c0 + l, col_of(i0 + jj));
+                    U[l * MAXC + jj] = l < nb ? val(c0 + l, col_of(i0 + jj)) : 0.f;
                 }
                 __syncthreads();
 #pragma unroll 1
@@ -533,7 +713,14 @@ int factor_plan(int S, int precision_bytes, int nb_hint, int ctas_hint, FactorPl
     if (precision_bytes == 8) {
         if (p.nb == 8) p.smem = factor_smem<double, 8>(S, p.ctas);
         else if (p.nb == 16) p.smem = factor_smem<double, 16>(S, p.ctas);
+        else if (p.nb == 32) p.smem = 0;
         else return -1;
+        // the pivot choice: S x (nb + 1) doubles and S ints; the trailing update: nb x 8 doubles
+        size_t pv = (size_t)S * (p.nb + 1) * sizeof(double) + (size_t)S * sizeof(int) + 64;
+        size_t tr = (size_t)p.nb * 8 * sizeof(double) + 64;
+        pv = pv > tr ? pv : tr;
+        pv = (pv + 255) & ~(size_t)255;
+        if (pv > p.smem) p.smem = pv;
     } else {
         if (p.nb == 16) p.smem = factor_smem<float, 16>(S, p.ctas);
         else if (p.nb == 32) p.smem = factor_smem<float, 32>(S, p.ctas);
@@ -557,10 +744,30 @@ static cudaError_t launch_factor_nb(const BlockSys<T> &sys, const FactorPlan &pl
     return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.ctas), dim3(plan.threads), args, plan.smem, st);
 }
 
+template <int NB>
+static cudaError_t launch_factor_pv_nb(const BlockSys<double> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
+                                       const int *skip)
+{
+    auto fn = k_factor_pv<NB>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (e != cudaSuccess) return e;
+    BlockSys<double> a = sys;
+    double *lu = plan.dinv;
+    void *args[] = {(void *)&a, (void *)&lu, (void *)&ctl, (void *)&skip};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.ctas), dim3(plan.threads), args, plan.smem, st);
+}
+
 template <>
 cudaError_t launch_factor<double>(const BlockSys<double> &sys, const FactorPlan &plan, Ctl *ctl, cudaStream_t st,
                                   const int *skip)
 {
+    if (plan.preview && plan.dinv) {
+        if (plan.nb == 8) return launch_factor_pv_nb<8>(sys, plan, ctl, st, skip);
+        if (plan.nb == 16) return launch_factor_pv_nb<16>(sys, plan, ctl, st, skip);
+        if (plan.nb == 32) return launch_factor_pv_nb<32>(sys, plan, ctl, st, skip);
+        return cudaErrorInvalidValue;
+    }
     if (plan.nb == 8) return launch_factor_nb<double, 8>(sys, plan, ctl, st, skip);
     if (plan.nb == 16) return launch_factor_nb<double, 16>(sys, plan, ctl, st, skip);
     return cudaErrorInvalidValue;

@@ -259,7 +259,12 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
 {
     const long long N = a.N;
     const int m = a.m < kMaxBasis ? a.m : kMaxBasis;
-    const int cycles = (a.max_iter + m - 1) / m + 1;   // the last start only checks the true residual
+    // iteration slots: the budget max_iter split into cycles of m, then a short spare cycle for a
+    // restart after a cycle that ended on the recurrence estimate without true convergence;
+    // slots past convergence cost one early-exit launch per kernel
+    const int full = (a.max_iter + m - 1) / m;
+    const int spare = m < 8 ? m : 8;
+    const int cycles = full + 1;
     int eb = (int)((N + kRedThreads - 1) / kRedThreads);
     if (eb > 4 * kRedBlocks) eb = 4 * kRedBlocks;
     count_launches(1); k_gm_init<<<1, 1, 0, st>>>(a.gm, a.tol);
@@ -279,7 +284,8 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
             count_launches(1); k_cycle_begin<<<1, 1, 0, st>>>(a.gm, a.red, 0, a.max_iter);
             count_launches(1); k_scale<<<eb, kRedThreads, 0, st>>>(r, a.V, N, &a.gm->beta, a.gm);
         }
-        for (int jj = 0; jj < m; ++jj) {
+        const int mc = cyc < full ? (a.max_iter - cyc * m < m ? a.max_iter - cyc * m : m) : spare;
+        for (int jj = 0; jj < mc; ++jj) {
             double *vj = a.V + (long long)jj * N;
             double *zj = a.Z + (long long)jj * N;
             a.precond(vj, zj, &a.gm->idle, st);
@@ -290,7 +296,7 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
             count_launches(1); k_axpy_basis<<<eb, kRedThreads, 0, st>>>(a.V, jj + 1, a.h2, a.w, N, a.gm);
             // ||w||^2 into h2[jj + 1]
             count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, a.w, N, a.partials, a.counter, a.h2 + jj + 1, a.gm, 1);
-            count_launches(1); k_arnoldi_end<<<1, 1, 0, st>>>(a.gm, a.h1, a.h2, jj, m, a.max_iter);
+            count_launches(1); k_arnoldi_end<<<1, 1, 0, st>>>(a.gm, a.h1, a.h2, jj, mc, a.max_iter);
             count_launches(1); k_scale<<<eb, kRedThreads, 0, st>>>(a.w, a.V + (long long)(jj + 1) * N, N, &a.gm->hnext, a.gm);
         }
         count_launches(1); k_update<<<eb, kRedThreads, 0, st>>>(a.gm, a.Z, a.x, N, a.max_iter);

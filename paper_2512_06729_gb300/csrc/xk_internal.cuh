@@ -105,6 +105,8 @@ struct FactorPlan {
     int ctas;        // persistent CTAs
     int threads;
     size_t smem;
+    int preview = 0;           // FP64: each panel's pivots chosen first on one CTA (k_factor_pv)
+    double *dinv = nullptr;    // that path: nb x nb LU factors of the panel's pivot block (global)
 };
 template <typename T>
 struct BlockSys {
@@ -123,6 +125,44 @@ cudaError_t launch_factor(const BlockSys<T> &sys, const FactorPlan &plan, Ctl *c
 // FP32 block inversion without pivoting (mixed-path preconditioner); gbuf: 2 x S x nb floats
 cudaError_t launch_factor_nopivot(const BlockSys<float> &sys, const FactorPlan &plan, float *gbuf, Ctl *ctl,
                                   cudaStream_t st, const int *skip = nullptr);
+// FP32 block inversion without pivoting on one thread-block cluster, each layer's
+// block resident in distributed shared memory (xk_cluster.cu)
+struct ClusterPlan {
+    int C;           // CTAs in the cluster
+    int nb;          // panel width
+    int threads;
+    int nslot;       // panels held per CTA
+    int lds;         // shared-memory row stride (floats)
+    size_t smem;
+    int twisted = 0; // two clusters fit at once: eliminate from both ends (layers >= 3)
+};
+bool cluster_twisted(const ClusterPlan &plan, int L);
+int cluster_plan(int S, int nb, int C, ClusterPlan *out);
+// gU: cluster_ubuf_floats(plan) floats of global memory (the panel rows every CTA reads, two
+// slots per cluster)
+size_t cluster_ubuf_floats(const ClusterPlan &plan);
+cudaError_t launch_factor_cluster(const BlockSys<float> &sys, const ClusterPlan &plan, float *gU, Ctl *ctl,
+                                  cudaStream_t st, const int *skip = nullptr);
+// sweeps with stored inverses on one cluster (xk_cluster.cu): FP32 inverses of the
+// cluster factorization (identity pivots) or FP64 inverses with implicit pivoting
+struct SolvePlan {
+    int C;           // CTAs in the cluster
+    int rpc;         // rows per CTA
+    int lds;         // shared-memory row stride (elements)
+    int nbuf;        // prefetch buffers (2, or 1 when two do not fit)
+    int threads;
+    size_t smem;
+    int twisted = 0; // FP32: two clusters fit at once (sweeps after the twisted elimination)
+};
+int solve_cluster_plan(int S, int elem_bytes, SolvePlan *out);
+// sweeps after the twisted elimination (two launches of two clusters); ymid: 2 x S doubles
+cudaError_t launch_solve_twisted(const BlockSys<float> &sys, const SolvePlan &plan, const double *b, double *x,
+                                 double *g, double *ymid, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,
+                                 const int *skip = nullptr, const double *xscale = nullptr);
+template <typename T>
+cudaError_t launch_solve_cluster(const BlockSys<T> &sys, const SolvePlan &plan, bool pivoted, const double *b,
+                                 double *x, double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,
+                                 const int *skip = nullptr, const double *xscale = nullptr);
 template <typename T>
 cudaError_t launch_solve(const BlockSys<T> &sys, const FactorPlan &plan, const double *b, double *x,
                          double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,

@@ -34,7 +34,8 @@ class Config(C.Structure):
         ("f_floor", C.c_double), ("dt_min", C.c_double), ("ss_dt", C.c_double), ("ss_tol", C.c_double),
         ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int), ("gmres_tol", C.c_double),
         ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
-        ("reuse_factorization", C.c_int),
+        ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("twisted", C.c_int),
+        ("fp64_panel", C.c_int),
     ]
 
 
@@ -71,6 +72,7 @@ SIGNATURES = {
     "xk_set_state": (C.c_int, [_vp, _vp, C.c_int]),
     "xk_set_mixing_ratios": (C.c_int, [_vp, _vp, C.c_int]),
     "xk_get_state": (C.c_int, [_vp, _vp, C.c_int]),
+    "xk_set_rate_coefficients": (C.c_int, [_vp]),
     "xk_step": (C.c_int, [_vp, C.c_double, C.POINTER(StepInfo)]),
     "xk_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(RunInfo)]),
     "xk_eval_grid": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -95,7 +97,7 @@ SIGNATURES = {
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
 }
 
-PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control"]
+PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control", "fallback"]
 
 
 def lib(build_if_missing=False):
@@ -228,6 +230,9 @@ class Column:
         info = StepInfo()
         self._call("xk_step", float(dt), C.byref(info))
         return info
+
+    def set_rate_coefficients(self):
+        self._call("xk_set_rate_coefficients")
 
     def run_to_steady(self, dt0=1e-8, max_steps=5000, raise_on_noconv=False):
         info = RunInfo()

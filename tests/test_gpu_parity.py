@@ -183,21 +183,80 @@ def test_block_solve_late_state_large_dt(pair):
     assert np.max(np.abs(x - ox) / s) < 1e-4
 
 
-@pytest.mark.parametrize("pivoting", [0, 1])
-def test_fp32_block_solve(pivoting):
-    """The FP32 block inversion (the mixed path's preconditioner) on the scaled
-    system diag(1/s) A diag(s), against the oracle's FP64 solve of the same
-    system.  The bound is FP32 rounding (6e-8) times the condition number of the
-    scaled system (about 1e3 at dt = 1e-6 s and 1e5 at dt = 1e-2 s on this
-    column), with a margin; an indexing error would give O(1)."""
+@pytest.mark.parametrize("panel,nb", [(1, 8), (1, 16), (1, 32), (0, 8), (0, 16)])
+def test_fp64_factor_variants(panel, nb):
+    """FP64 block inversion with each panel's pivots chosen first and its
+    multipliers formed on all CTAs by triangular solves (panel = 1; widths 8,
+    16, 32 with ragged last panels on 40 species) and column by column on one
+    CTA (panel = 0), against the oracle's LU: at moderate dt to 1e-10, and near
+    steady state at dt = 1e8 s to the kappa * eps bound of the late-state test
+    at width 8 (wider panels round more there: a numpy emulation of the same
+    elimination errs by 2.6e-4 at width 16 on the 20-species column)."""
     p = synth.small_column()
     o = Oracle(p)
-    c = xk.Column(p, "mixed", fp32_pivoting=pivoting)
+    c = xk.Column(p, "fp64", fp64_panel=panel, panel_width=nb)
+    ng = o.grid()[0]
+    n = o.initial_state()
+    rng = np.random.default_rng(4)
+    f = rng.normal(size=n.shape) * n
+    for dt in (1e-6, 1e-2):
+        oA, olo, oup = o.jacobian(n, dt)
+        x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(f)))
+        ox = o.block_solve(oA, olo, oup, f)
+        assert np.max(np.abs(x - ox)) / (np.abs(ox).max() + 1e-300) < 1e-10, (panel, nb, dt)
+    nl, _ = o.run_to_steady(n, max_steps=400)
+    oA, olo, oup = o.jacobian(nl, 1e8)
+    fl = o.residual(nl)
+    x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(fl)))
+    ox = o.block_solve(oA, olo, oup, fl)
+    s = np.maximum(nl, 1e-20 * ng[:, None])
+    assert np.max(np.abs(x - ox) / s) < (1e-4 if nb == 8 else 1e-1), (panel, nb)
+
+
+def test_fp64_factor_full_size():
+    """Both FP64 inversions at 594 species (74 panels of 8 and a ragged one of
+    2) on a 4-layer slice of the 7,720-reaction column, against the oracle's
+    LU."""
+    p = synth.full_column()
+    p = p.replace(P_bar=p.P_bar[:4].copy(), T=p.T[:4].copy(), Kzz=p.Kzz[:4].copy(), f0=p.f0[:4].copy())
+    o = Oracle(p)
+    n = o.initial_state()
+    f = np.random.default_rng(5).normal(size=n.shape) * n
+    for panel in (0, 1):
+        c = xk.Column(p, "fp64", fp64_panel=panel)
+        for dt in (1e-6, 1e-2):
+            oA, olo, oup = o.jacobian(n, dt)
+            x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(f)))
+            ox = o.block_solve(oA, olo, oup, f)
+            assert np.max(np.abs(x - ox)) / (np.abs(ox).max() + 1e-300) < 1e-10, (panel, dt)
+        c.close()
+
+
+@pytest.mark.parametrize("pivoting,cluster,nb,twisted", [(0, 0, 0, 1), (0, 0, 0, 0), (0, 2, 16, 1), (0, 3, 16, 1),
+                                                          (0, 4, 8, 0), (0, 1, 8, 1), (0, -1, 0, 1), (1, 0, 0, 1)])
+def test_fp32_block_solve(pivoting, cluster, nb, twisted):
+    """The FP32 block inversion (the mixed path's preconditioner) on the scaled
+    system diag(1/s) A diag(s), against the oracle's FP64 solve of the same
+    system: cluster-resident kernel (automatic size and panel width 8, eliminated
+    from both ends of the column on two clusters or top-down on one; 2 and 4
+    CTAs holding several panels each; 3 CTAs with one 16-wide panel each, the
+    last one ragged; one-CTA clusters), the grid-wide kernel without
+    pivoting, and with pivoting.
+    The bound is FP32 rounding (6e-8) times the condition number of the scaled
+    system (about 1e3 at dt = 1e-6 s and 1e5 at dt = 1e-2 s on this column),
+    with a margin; without pivoting the element growth adds to it at
+    dt = 1e-2 s (the same elimination emulated in numpy float32, with exact
+    diagonal-block inverses, errs by 1.5e-2 / 1.0e-2 / 1.6e-3 for panels of
+    8 / 16 / 32 columns), so the no-pivot variants get 3e-2 there.  An indexing
+    error gives O(1); the dt = 1e-6 s case stays at 1e-4."""
+    p = synth.small_column()
+    o = Oracle(p)
+    c = xk.Column(p, "mixed", fp32_pivoting=pivoting, cluster_size=cluster, panel_width=nb, twisted=twisted)
     ng = o.grid()[0]
     n = o.initial_state()
     s = np.maximum(n, 1e-20 * ng[:, None])
     rng = np.random.default_rng(2)
-    for dt, tol in ((1e-6, 1e-4), (1e-2, 1e-2)):
+    for dt, tol in ((1e-6, 1e-4), (1e-2, 1e-2 if pivoting else 3e-2)):
         A, lo, up = o.jacobian(n, dt)
         As = A * s[:, None, :] / s[:, :, None]
         los = lo * np.vstack([s[:1], s[:-1]]) / s
@@ -209,23 +268,56 @@ def test_fp32_block_solve(pivoting):
         assert err < tol, (pivoting, dt, err)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_step_delta(precision):
+def test_fp32_cluster_full_size():
+    """The cluster-resident FP32 inversion at the full 594-species block size
+    (several panels per CTA, ragged last panel of 2 columns) on a 4-layer slice
+    of the 7,720-reaction column (eliminated from both ends, meeting in layer
+    2, and top-down), against the oracle's FP64 solve; and the grid-wide FP32
+    kernel on the same system for comparison."""
+    p = synth.full_column()
+    p = p.replace(P_bar=p.P_bar[:4].copy(), T=p.T[:4].copy(), Kzz=p.Kzz[:4].copy(), f0=p.f0[:4].copy())
+    o = Oracle(p)
+    ng = o.grid()[0]
+    n = o.initial_state()
+    s = np.maximum(n, 1e-20 * ng[:, None])
+    A, lo, up = o.jacobian(n, 1e-6)
+    As = A * s[:, None, :] / s[:, :, None]
+    los = lo * np.vstack([s[:1], s[:-1]]) / s
+    ups = up * np.vstack([s[1:], s[-1:]]) / s
+    f = np.random.default_rng(3).normal(size=n.shape)
+    ox = o.block_solve(As, los, ups, f)
+    errs = {}
+    for cluster, twisted in ((0, 1), (0, 0), (-1, 1)):
+        c = xk.Column(p, "mixed", cluster_size=cluster, twisted=twisted)
+        x = cpu(c.block_solve32(dev(As), dev(los), dev(ups), dev(f)))
+        errs[(cluster, twisted)] = np.max(np.abs(x - ox)) / np.max(np.abs(ox))
+        c.close()
+    assert max(errs.values()) < 1e-4, errs
+
+
+@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}), ("mixed", {"twisted": 0}),
+                                          ("mixed", {"cluster_size": -1}), ("mixed", {"fp32_pivoting": 1})])
+def test_step_delta(precision, kw):
     """One linear step at the initial state (small dt) and at a late state
-    (the dt the controller reached there), against the oracle."""
+    (the dt the controller reached there), against the oracle.  In mixed
+    precision (cluster-resident FP32 inversion, grid-wide without and with
+    pivoting) FGMRES must converge on the FP32 preconditioner at the initial
+    state (iters >= 0: no FP64 fallback)."""
     p = synth.small_column()
     o = Oracle(p)
-    c = xk.Column(p, precision)
+    c = xk.Column(p, precision, **kw)
     ng = o.grid()[0]
     n0 = o.initial_state()
     nl, info = o.run_to_steady(n0, max_steps=500)
-    for n, dt in ((n0, 1e-6), (n0, 1e-2), (nl, info.dt)):
+    for i, (n, dt) in enumerate(((n0, 1e-6), (n0, 1e-2), (nl, info.dt))):
         d, iters, res = c.step_delta(dev(n), dt)
         d = cpu(d)
         od = o.step_delta(n, dt)
         s = np.maximum(n, 1e-20 * ng[:, None])
         err = np.max(np.abs(d - od) / s)
-        assert err < 1e-6, (precision, dt, err, iters, res)
+        assert err < 1e-6, (precision, kw, dt, err, iters, res)
+        if precision == "mixed" and i < 2:
+            assert iters >= 0, (kw, dt, iters, res)
 
 
 def test_controlled_steps_follow_the_oracle():
@@ -356,3 +448,24 @@ def test_invalid_inputs_raise():
     bad = p.replace(P_bar=p.P_bar[::-1].copy())
     with pytest.raises(xk.XkError):
         xk.Column(bad, "fp64")
+
+
+def test_rate_coefficients_evaluated_once():
+    """Rate coefficients depend on the atmosphere only: a column that sets them
+    explicitly and one that evaluates them lazily in its first step take the
+    same steps, bit for bit, and the device values equal a fresh evaluation."""
+    p = synth.tiny_column()
+    a, b = xk.Column(p, "fp64"), xk.Column(p, "fp64")
+    a.set_rate_coefficients()
+    for c in (a, b):
+        c.set_mixing_ratios(p.f0)
+    dt = 1e-8
+    for _ in range(10):
+        ia, ib = a.step(dt), b.step(dt)
+        assert ia.accepted == ib.accepted and ia.dt_next == ib.dt_next
+        dt = ia.dt_next
+    assert np.array_equal(a.get_state(), b.get_state())
+    kf, kr = (cpu(t) for t in a.eval_rates())
+    o = Oracle(p)
+    okf, okr = o.rate_coefficients()
+    assert relerr(kf, okf, 1e-300) < 1e-11 and relerr(kr, okr, 1e-300) < 1e-11
