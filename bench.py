@@ -33,6 +33,15 @@ WORKLOAD = "xodiac-594sp-7720rx-150L"
 SAMPLE_LAYERS = 24          # CPU oracle sample: this many layers of the same column
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant
+# kernels, from the ncu captures summarized in profiles/, for the configuration captured there;
+# a run in another configuration reports null.
+PROFILED_TRAFFIC = {
+    ("mixed", 16, 8, 1): (371.3e6, "k_factor_cluster<8>, two-chain launch (profiles/k_factor_cluster_594x150.txt)"),
+    ("fp64", 152, 8, 0): (833.5e6, "k_factor<double, 8> (profiles/k_factor_fp64_594x150.txt)"),
+}
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -254,8 +263,12 @@ def run_ours(args):
             ms, info, phases, launches = time_steps(col, K, stream)
         _barrier(ws)
         steps_done = max(int(info.steps), 1)
+        t = tuning[prec]
+        col_cfg = {"cluster": t.get("cluster_size", 16), "nb": t.get("panel_width", 8) or 8,
+                   "twisted": t.get("twisted", 1), "ctas": t.get("factor_ctas", 152) or 152,
+                   "panel": t.get("fp64_panel", 0)}
         results[prec] = dict(ms=ms, steps=steps_done, phases=phases, launches=launches, info=info,
-                             col=col if prec == "mixed" else None)
+                             col=col if prec == "mixed" else None, col_cfg=col_cfg)
         if prec == "fp64":
             del col
             torch.cuda.empty_cache()
@@ -273,10 +286,20 @@ def run_ours(args):
         avg_s = fac_ms / max(fac_calls, 1) * 1e-3
         achieved = flops / avg_s / 1e12
         peak = alu[dtype]
-        return {"kernel": f"k_factor<{'double' if dtype == 'f64' else 'float'}>", "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": f"derived from {peak_kind} bf16 x nominal ratio",
-                "flops_per_launch": flops, "launch_ms": avg_s * 1e3}
+        cfg = res["col_cfg"]
+        if dtype == "f32":
+            twisted = int(cfg["twisted"] and cfg["cluster"] > 0 and L >= 3)
+            key = ("mixed", cfg["cluster"], cfg["nb"], twisted)
+            name = (f"k_factor_cluster<{cfg['nb']}> ({cfg['cluster']}-CTA clusters"
+                    + (", two-chain launch + middle-layer launch per factorization)" if twisted else ")"))
+        else:
+            key = ("fp64", cfg["ctas"], cfg["nb"], cfg["panel"])
+            name = f"k_factor<double, {cfg['nb']}>" if not cfg["panel"] else f"k_factor_pv<{cfg['nb']}>"
+        traffic, source = PROFILED_TRAFFIC.get(key, (None, None))
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": source,
+                "peak_kind": f"derived from {peak_kind} bf16 x nominal ratio",
+                "flops_per_factorization": flops, "ms_per_factorization": avg_s * 1e3}
 
     # end to end through the C-ABI with host buffers: host state in, step, host state out
     col = mixed["col"]
