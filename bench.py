@@ -38,7 +38,7 @@ SAMPLE_LAYERS = 24          # CPU oracle sample: this many layers of the same co
 # a run in another configuration reports null.
 PROFILED_TRAFFIC = {
     ("mixed", 16, 8, 1): (371.3e6, "k_factor_cluster<8>, two-chain launch (profiles/k_factor_cluster_594x150.txt)"),
-    ("fp64", 152, 8, 0): (833.5e6, "k_factor<double, 8> (profiles/k_factor_fp64_594x150.txt)"),
+    ("fp64", 152, 8, 0, 0): (833.5e6, "k_factor<double, 8> (profiles/k_factor_fp64_594x150.txt)"),
 }
 
 
@@ -293,8 +293,11 @@ def run_ours(args):
             name = (f"k_factor_cluster<{cfg['nb']}> ({cfg['cluster']}-CTA clusters"
                     + (", two-chain launch + middle-layer launch per factorization)" if twisted else ")"))
         else:
-            key = ("fp64", cfg["ctas"], cfg["nb"], cfg["panel"])
+            twisted = int(cfg["twisted"] and not cfg["panel"] and L >= 3)
+            key = ("fp64", cfg["ctas"], cfg["nb"], cfg["panel"], twisted)
             name = f"k_factor<double, {cfg['nb']}>" if not cfg["panel"] else f"k_factor_pv<{cfg['nb']}>"
+            if twisted:
+                name += " (two grid halves, then the middle layer on the whole grid)"
         traffic, source = PROFILED_TRAFFIC.get(key, (None, None))
         return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_source": source,

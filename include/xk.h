@@ -93,6 +93,10 @@ typedef struct {
                              holds each layer's FP32 block in distributed shared memory while it is
                              inverted (1..16; 0 = the largest that fits; -1 = grid-wide kernel with
                              the block in global memory).  panel_width 8 or 16 applies (default 8). */
+    int reuse_max_iters;  /* with reuse_factorization: a solve on the reused FP64 factorization that
+                             needs more FGMRES iterations than this (default 20; an iteration costs
+                             about one FP64 sweep pair, a fresh factorization a few hundred) makes
+                             the next FP64 step refactor */
     int twisted;          /* mixed mode, cluster-resident inversion: 1 (default) eliminates from both
                              ends of the column at once on two clusters and meets in the middle
                              layer (when two clusters fit and there are at least 3 layers); 0 keeps
@@ -254,7 +258,9 @@ XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta,
  * xk_batch_poll: run information of a slot and whether it has finished
  *   (converged, or stopped with an error recorded in *status).
  * xk_batch_remove: releases the slot and its budget; the context returns to
- *   its own stream and factorization plan. */
+ *   its own stream and factorization plan.
+ * xk_batch_last_error: message of the last failed batch call (the failing
+ *   column's, for xk_batch_step); owned by the batch, valid until the next call. */
 typedef struct xk_batch xk_batch;
 XK_API int xk_batch_create(xk_batch **out, int device, size_t budget_bytes, int max_slots);
 XK_API int xk_batch_destroy(xk_batch *batch);
@@ -262,6 +268,7 @@ XK_API int xk_batch_add(xk_batch *batch, xk_ctx *ctx, double dt0, int *slot);
 XK_API int xk_batch_remove(xk_batch *batch, int slot);
 XK_API int xk_batch_step(xk_batch *batch, int nsteps);
 XK_API int xk_batch_poll(xk_batch *batch, int slot, xk_run_info *info, int *finished, int *status);
+XK_API const char *xk_batch_last_error(xk_batch *batch);
 
 /* ---- block solve without any device allocation ----
  * The paper has no counterpart: this entry point serves callers that cannot

@@ -259,7 +259,6 @@ size_t layout(xk_ctx *c, char *base)
         c->partials = b.take<double>((size_t)kGmPartialBlocks * (kMaxBasis + 1));
         c->counter = b.take<unsigned>(8);
         c->gm = b.take<GmState>(1);
-        c->ymid = b.take<double>(2 * (size_t)S);
         c->ridx32 = b.take<int>(LS);    // the FP64 factorization's pivots stay intact for reuse
         c->sig32 = b.take<int>(LS);
     }
@@ -267,6 +266,7 @@ size_t layout(xk_ctx *c, char *base)
     c->sig = b.take<int>(LS);
     c->pinfo = b.take<int>(1 + 4 * 64);
     c->dinv = b.take<double>(32 * 32);
+    c->ymid = b.take<double>(2 * (size_t)S);
     c->bar = b.take<unsigned>(8);
     c->ctl = b.take<Ctl>(1);
     c->ctl_aux = b.take<Ctl>(1);
@@ -308,7 +308,7 @@ cudaError_t solve32(xk_ctx *c, const double *b, double *x, Ctl *ctl, cudaStream_
                     const int *skip)
 {
     if (c->use_cluster_solve && c->use_cluster && cluster_twisted(c->cplan, c->L) && c->splan.twisted)
-        return launch_solve_twisted(sys32(c), c->splan, b, x, c->gsol, c->ymid, ctl, st, bscale, skip);
+        return launch_solve_twisted<float>(sys32(c), c->splan, false, b, x, c->gsol, c->ymid, ctl, st, bscale, skip);
     if (c->use_cluster_solve && !(c->use_cluster && cluster_twisted(c->cplan, c->L)))
         return launch_solve_cluster<float>(sys32(c), c->splan, false, b, x, c->gsol, ctl, st, bscale, skip);
     return launch_solve<float>(sys32(c), c->plan, b, x, c->gsol, ctl, st, bscale, skip);
@@ -318,6 +318,9 @@ cudaError_t solve32(xk_ctx *c, const double *b, double *x, Ctl *ctl, cudaStream_
 cudaError_t solve64(xk_ctx *c, const FactorPlan &plan, const double *b, double *x, Ctl *ctl, cudaStream_t st,
                     const double *bscale, const int *skip, const double *xscale)
 {
+    if (c->use_cluster_solve64 && plan.twisted && c->L >= 3 && plan.ctas >= 2)
+        return launch_solve_twisted<double>(sys64(c), c->splan64, true, b, x, c->gsol, c->ymid, ctl, st, bscale, skip,
+                                            xscale);
     if (c->use_cluster_solve64)
         return launch_solve_cluster<double>(sys64(c), c->splan64, true, b, x, c->gsol, ctl, st, bscale, skip, xscale);
     return launch_solve<double>(sys64(c), plan, b, x, c->gsol, ctl, st, bscale, skip, xscale);
@@ -329,6 +332,8 @@ void set_preview(xk_ctx *c, FactorPlan *p)
 {
     p->preview = c->cfg.fp64_panel ? 1 : 0;
     p->dinv = c->dinv;
+    // both ends at once (column-by-column kernel) when the sweeps can follow on two clusters
+    p->twisted = (c->cfg.twisted && !p->preview && c->use_cluster_solve64 && c->splan64.twisted) ? 1 : 0;
 }
 
 int need_ready(xk_ctx *c)
@@ -386,6 +391,7 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         a.tol = c->cfg.gmres_tol;
         a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
         a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
+        a.reuse_max_iters = c->cfg.reuse_max_iters > 0 ? c->cfg.reuse_max_iters : 20;
         FactorPlan plan64 = c->plan64;
         const double *rowd = c->rowd, *pin = c->pin, *pout = c->pout;
         a.matvec = [col, ctl, rowd](const double *x, double *y, const int *skip, cudaStream_t s) {
@@ -465,7 +471,7 @@ int xk_config_init(xk_config *cfg)
     cfg->dt_max = 1e8; cfg->rel_reject = 1.0; cfg->rel_target = 0.5; cfg->grow_max = 3.0; cfg->shrink_min = 0.5;
     cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
     cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-15;
-    cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1;
+    cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1; cfg->reuse_max_iters = 20;
     return XK_OK;
 }
 
@@ -642,11 +648,11 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     const int nb64 = sz == 8 ? nbh : 8;
     if (factor_plan(c->S, 8, nb64, sz == 8 ? c->cfg.factor_ctas : 0, &c->plan64) != 0)
         return fail(c, XK_EINVAL, "no FP64 factorization plan for S=%d", c->S);
-    set_preview(c, &c->plan64);
-    if (sz == 8) set_preview(c, &c->plan);
     c->use_cluster = false;
     c->use_cluster_solve = false;
     c->use_cluster_solve64 = c->cfg.cluster_size >= 0 && solve_cluster_plan(c->S, 8, &c->splan64) == 0;
+    set_preview(c, &c->plan64);
+    if (sz == 8) set_preview(c, &c->plan);
     if (sz == 4 && !c->cfg.fp32_pivoting && c->cfg.cluster_size >= 0) {
         const int nbc = c->cfg.panel_width == 16 ? 16 : 8;
         // the panel rows go through gbuf (4 x S x 32 floats, enough for 4 x 16 x round_up(S, 4))
@@ -989,6 +995,7 @@ struct xk_batch {
     size_t budget = 0, used = 0;
     int max_slots = 1;
     std::vector<BatchSlot> slots;
+    std::string err;
 };
 
 extern "C" {
@@ -1094,11 +1101,15 @@ int xk_batch_step(xk_batch *b, int nsteps)
     if (!b || nsteps <= 0) return XK_EINVAL;
     cudaSetDevice(b->device);
     // round-robin so that every column's next step is queued before the following ones
+    b->err.clear();
     for (int k = 0; k < nsteps; ++k)
         for (auto &s : b->slots)
             if (s.ctx && !s.finished) {
                 int rc = enqueue_step(s.ctx);
-                if (rc) return rc;
+                if (rc) {
+                    b->err = s.ctx->err;
+                    return rc;
+                }
             }
     for (auto &s : b->slots)
         if (s.ctx && !s.finished)
@@ -1106,11 +1117,17 @@ int xk_batch_step(xk_batch *b, int nsteps)
     for (auto &s : b->slots)
         if (s.ctx && !s.finished) {
             cudaError_t e = cudaStreamSynchronize(s.st);
-            if (e != cudaSuccess) return fail(s.ctx, XK_ECUDA, "batch step: %s", cudaGetErrorString(e));
+            if (e != cudaSuccess) {
+                int rc = fail(s.ctx, XK_ECUDA, "batch step: %s", cudaGetErrorString(e));
+                b->err = s.ctx->err;
+                return rc;
+            }
             s.finished = s.ctx->ctl_host->finished != 0;
         }
     return cuda_check(nullptr, "batch_step");
 }
+
+const char *xk_batch_last_error(xk_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *status)
 {

@@ -442,7 +442,7 @@ k_solve_cluster(BlockSys<T> a, const int *perm, const double *b, double *x, doub
     }
 }
 
-// Sweeps after the twisted elimination, on two clusters (FP32 inverses, identity pivots).
+// Sweeps after the twisted elimination, on two clusters.
 // phase 0 (forward, both ends at once):
 //   cluster 0: g_0 = b_0, g_k = b_k - lo_k (B_{k-1} g_{k-1}) for 0 < k < mid, y_top = B_{mid-1} g_{mid-1}
 //   cluster 1: h_{L-1} = b_{L-1}, h_k = b_k - up_k (C_{k+1} h_{k+1}) for mid < k < L-1,
@@ -452,9 +452,12 @@ k_solve_cluster(BlockSys<T> a, const int *perm, const double *b, double *x, doub
 //   cluster 0: x_k = B_k (g_k - up_k x_{k+1}) for k < mid
 //   cluster 1: x_k = C_k (h_k - lo_k x_{k-1}) for k > mid
 // (B: inverses from the top, C: from the bottom, both stored in place of the blocks; g and h share
-// the vector g; y_top and y_bot go through ymid.)  Prefetch and exchange as in k_solve_cluster.
+// the vector g; y_top and y_bot go through ymid.)  With implicit pivots (perm != null) a product
+// with layer k's stored block reads rows perm_k(i) and takes the vector in the order perm_k, as in
+// k_solve_cluster.  Prefetch and exchange as there.
+template <typename T>
 __global__ void __launch_bounds__(kSolveClusterThreads, 1)
-k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double *ymid, Ctl *ctl,
+k_solve_twisted(BlockSys<T> a, const int *perm, const double *b, double *x, double *g, double *ymid, Ctl *ctl,
                 const double *bscale, const int *skip, const double *xscale, int rpc, int lds, int nbuf, int phase,
                 int mid)
 {
@@ -465,11 +468,12 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
     const int cq = blockIdx.x / C;
     const int S = a.S, ld = a.ld, L = a.L;
     const int r0 = me * rpc, r1 = min(S, r0 + rpc), nr = max(0, r1 - r0);
-    const int Q = lds / 4;
+    constexpr int E = 16 / sizeof(T);
+    const int Q = lds / E;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
     extern __shared__ __align__(16) unsigned char smraw[];
-    float *buf = (float *)smraw;                        // nbuf x rpc x lds
-    float *vec = buf + (size_t)nbuf * rpc * lds;        // lds
+    T *buf = (T *)smraw;                                // nbuf x rpc x lds
+    T *vec = buf + (size_t)nbuf * rpc * lds;            // lds
     double *mine = (double *)(vec + lds);               // 2 x rpc
     const int dk = cq == 0 ? 1 : -1;
     const int nuse = phase == 0 ? (cq == 0 ? mid : L - 1 - mid) : (cq == 0 ? mid + 1 : L - mid);
@@ -477,13 +481,15 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
         if (phase == 0) return cq == 0 ? t : L - 1 - t;
         return cq == 0 ? mid - t : mid + t;
     };
+    auto pk = [&](int layer, int m) -> int { return perm ? perm[(size_t)layer * S + m] : m; };
     auto stage = [&](int t) {
         if (t < nuse) {
-            const float *B = a.D + (size_t)use_layer(t) * S * ld;
-            float *dst = buf + (size_t)(t % nbuf) * rpc * lds;
+            const int layer = use_layer(t);
+            const T *B = a.D + (size_t)layer * S * ld;
+            T *dst = buf + (size_t)(t % nbuf) * rpc * lds;
             for (int e = tid; e < nr * Q; e += blockDim.x) {
                 const int i = e / Q, qq = e - i * Q;
-                cp_async16(dst + (size_t)i * lds + qq * 4, B + (size_t)(r0 + i) * ld + qq * 4);
+                cp_async16(dst + (size_t)i * lds + qq * E, B + (size_t)pk(layer, r0 + i) * ld + qq * E);
             }
         }
         cp_async_commit();
@@ -491,17 +497,17 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
     auto ready = [&](int t) {
         if (nbuf == 2) cp_async_wait1(); else cp_async_wait0();
         __syncthreads();
-        float *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
+        T *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
         if (lds > S)
             for (int e = tid; e < nr * (lds - S); e += blockDim.x) {
                 const int i = e / (lds - S), j = S + (e - i * (lds - S));
-                Bt[(size_t)i * lds + j] = 0.f;
+                Bt[(size_t)i * lds + j] = (T)0;
             }
         __syncthreads();
     };
-    auto rowdot = [&](const float *Bi) -> float {
-        float acc = 0.f;
-        for (int j = lane; j < S; j += 32) acc = fmaf(Bi[j], vec[j], acc);
+    auto rowdot = [&](const T *Bi) -> T {
+        T acc = (T)0;
+        for (int j = lane; j < S; j += 32) acc = fma(Bi[j], vec[j], acc);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         return acc;
@@ -526,15 +532,15 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
             mine[i] = gi;
         }
         cl.sync();
-        for (int m = tid; m < lds; m += blockDim.x) vec[m] = m < S ? (float)remote(0, m) : 0.f;
+        for (int m = tid; m < lds; m += blockDim.x) vec[m] = m < S ? (T)remote(0, pk(use_layer(0), m)) : (T)0;
         for (int t = 0; t < nuse; ++t) {
             ready(t);
-            const float *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
+            const T *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
             const bool last = t == nuse - 1;
             const int kn = use_layer(t) + dk;          // the layer whose vector this product feeds
-            const float *cf = dk > 0 ? a.lo : a.up;
+            const T *cf = dk > 0 ? a.lo : a.up;
             for (int i = warp; i < nr; i += nw) {
-                const float acc = rowdot(Bt + (size_t)i * lds);
+                const T acc = rowdot(Bt + (size_t)i * lds);
                 if (lane == 0) {
                     if (last) {
                         ymid[(size_t)cq * S + r0 + i] = (double)acc;
@@ -550,15 +556,18 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
             stage(t + nbuf);
             cl.sync();
             if (!last) {
-                for (int m = tid; m < lds; m += blockDim.x) vec[m] = m < S ? (float)remote((t + 1) & 1, m) : 0.f;
+                const int ln = use_layer(t + 1);
+                for (int m = tid; m < lds; m += blockDim.x)
+                    vec[m] = m < S ? (T)remote((t + 1) & 1, pk(ln, m)) : (T)0;
             }
         }
     } else {
         for (int m = tid; m < lds; m += blockDim.x) {
-            float v = 0.f;
+            T v = (T)0;
             if (m < S) {
-                const size_t e = (size_t)mid * S + m;
-                v = (float)(bval(mid, m) - (double)a.lo[e] * ymid[m] - (double)a.up[e] * ymid[(size_t)S + m]);
+                const int o = pk(mid, m);
+                const size_t e = (size_t)mid * S + o;
+                v = (T)(bval(mid, o) - (double)a.lo[e] * ymid[o] - (double)a.up[e] * ymid[(size_t)S + o]);
             }
             vec[m] = v;
         }
@@ -566,20 +575,21 @@ k_solve_twisted(BlockSys<float> a, const double *b, double *x, double *g, double
             const int k = use_layer(t);
             if (t > 0) {
                 // h = g_k - c_k x_prev, x_prev's rows from their owners (slot of the previous use)
-                const float *cb = cq == 0 ? a.up : a.lo;
+                const T *cb = cq == 0 ? a.up : a.lo;
                 for (int m = tid; m < lds; m += blockDim.x) {
-                    float v = 0.f;
+                    T v = (T)0;
                     if (m < S) {
-                        const size_t e = (size_t)k * S + m;
-                        v = (float)(g[e] - (double)cb[e] * remote((t - 1) & 1, m));
+                        const int o = pk(k, m);
+                        const size_t e = (size_t)k * S + o;
+                        v = (T)(g[e] - (double)cb[e] * remote((t - 1) & 1, o));
                     }
                     vec[m] = v;
                 }
             }
             ready(t);                 // includes the block barrier that publishes vec
-            const float *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
+            const T *Bt = buf + (size_t)(t % nbuf) * rpc * lds;
             for (int i = warp; i < nr; i += nw) {
-                const float acc = rowdot(Bt + (size_t)i * lds);
+                const T acc = rowdot(Bt + (size_t)i * lds);
                 if (lane == 0) {
                     if (t > 0 || cq == 0) x[(size_t)k * S + r0 + i] = (double)acc;
                     mine[(size_t)(t & 1) * rpc + i] = (double)acc;
@@ -620,6 +630,9 @@ template <int NB>
 cudaError_t launch_nb(const BlockSys<float> &sys, const ClusterPlan &plan, float *gU, Ctl *ctl, cudaStream_t st,
                       const int *skip, int mode, int mid, int nclusters)
 {
+    // the shared-memory limit is a property of the function: contexts of other sizes may have set it
+    cudaError_t ea = set_attrs<NB>(plan.smem);
+    if (ea != cudaSuccess) return ea;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(plan.C * nclusters);
     cfg.blockDim = dim3(plan.threads);
@@ -757,9 +770,9 @@ int solve_plan_t(int S, SolvePlan *out)
                 continue;
             }
             p.twisted = 0;
-            if (sizeof(T) == 4 && nclusters >= 2) {
+            if (nclusters >= 2) {
                 int n2 = 0;
-                auto ft = k_solve_twisted;
+                auto ft = k_solve_twisted<T>;
                 if (cudaFuncSetAttribute(ft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) == cudaSuccess &&
                     cudaFuncSetAttribute(ft, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
                     cudaOccupancyMaxActiveClusters(&n2, ft, &cfg) == cudaSuccess && n2 >= 2)
@@ -800,15 +813,22 @@ cudaError_t launch_solve_cluster(const BlockSys<T> &sys, const SolvePlan &plan, 
     cfg.numAttrs = 1;
     count_launches(1);
     const int *perm = pivoted ? sys.perm : nullptr;
+    // the shared-memory limit is a property of the function: contexts of other sizes may have set it
+    cudaError_t ea = cudaFuncSetAttribute(k_solve_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (ea != cudaSuccess) return ea;
     return cudaLaunchKernelEx(&cfg, k_solve_cluster<T>, sys, perm, b, x, g, ctl, bscale, skip, xscale, plan.rpc,
                               plan.lds, plan.nbuf);
 }
 
-cudaError_t launch_solve_twisted(const BlockSys<float> &sys, const SolvePlan &plan, const double *b, double *x,
-                                 double *g, double *ymid, Ctl *ctl, cudaStream_t st, const double *bscale,
+template <typename T>
+cudaError_t launch_solve_twisted(const BlockSys<T> &sys, const SolvePlan &plan, bool pivoted, const double *b,
+                                 double *x, double *g, double *ymid, Ctl *ctl, cudaStream_t st, const double *bscale,
                                  const int *skip, const double *xscale)
 {
     const int mid = sys.L / 2;
+    const int *perm = pivoted ? sys.perm : nullptr;
+    cudaError_t ea = cudaFuncSetAttribute(k_solve_twisted<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    if (ea != cudaSuccess) return ea;
     for (int phase = 0; phase < 2; ++phase) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * plan.C);
@@ -823,12 +843,19 @@ cudaError_t launch_solve_twisted(const BlockSys<float> &sys, const SolvePlan &pl
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         count_launches(1);
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_twisted, sys, b, x, g, ymid, ctl, bscale, skip, xscale,
-                                           plan.rpc, plan.lds, plan.nbuf, phase, mid);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_solve_twisted<T>, sys, perm, b, x, g, ymid, ctl, bscale, skip,
+                                           xscale, plan.rpc, plan.lds, plan.nbuf, phase, mid);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
+
+template cudaError_t launch_solve_twisted<float>(const BlockSys<float> &, const SolvePlan &, bool, const double *,
+                                                 double *, double *, double *, Ctl *, cudaStream_t, const double *,
+                                                 const int *, const double *);
+template cudaError_t launch_solve_twisted<double>(const BlockSys<double> &, const SolvePlan &, bool, const double *,
+                                                  double *, double *, double *, Ctl *, cudaStream_t,
+                                                  const double *, const int *, const double *);
 
 template cudaError_t launch_solve_cluster<float>(const BlockSys<float> &, const SolvePlan &, bool, const double *,
                                                  double *, double *, Ctl *, cudaStream_t, const double *,

@@ -23,15 +23,17 @@ constexpr int kFactorThreads = 512;
 constexpr int kSolveThreads = 512;
 constexpr unsigned long long kSpinLimit = 1ull << 24;   // ~1-2 s with the sleep below
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl)
+// Barrier over the nblk CTAs that share the counter pair bar[0..1] (the whole grid by default).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl, unsigned nblk = 0)
 {
+    if (nblk == 0) nblk = gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned *vgen = bar + 1;
         unsigned gen = *vgen;
         __threadfence();
         unsigned prev = atomicAdd(bar, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == nblk - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -163,14 +165,14 @@ __device__ void panel_factor(T *D, int *perm, int *iperm, int *pinfo, int S, int
 // row of G in registers.
 template <typename T, int NB>
 __device__ void trailing_update(T *D, const int *pinfo, const int *iperm, int S, int ld, int c0, int nb,
-                                unsigned char *smem)
+                                unsigned char *smem, int bid, int nblk)
 {
     constexpr int MAXC = 8;                            // columns per CTA handled in registers
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int others = S - nb;
-    const int cw = (others + gridDim.x - 1) / gridDim.x;
+    const int cw = (others + nblk - 1) / nblk;
     T *U = (T *)smem;                                  // NB x cw
-    for (int q0 = blockIdx.x * cw, qend = min(others, (blockIdx.x + 1) * cw); q0 < qend; q0 += MAXC) {
+    for (int q0 = bid * cw, qend = min(others, (bid + 1) * cw); q0 < qend; q0 += MAXC) {
         const int ncols = min(MAXC, qend - q0);
         // rows nb..NB-1 of U (ragged last panel) are zero: the update below runs over all NB
         for (int e = tid; e < NB * ncols; e += nthr) {
@@ -212,38 +214,64 @@ __device__ void trailing_update(T *D, const int *pinfo, const int *iperm, int S,
     }
 }
 
+// mode 0: all layers top-down on the whole grid.  mode 1 (twisted): the grid splits in two halves
+// with their own barrier counters and panel scratch; the first half eliminates layers 0..mid-1
+// top-down, the second layers L-1..mid+1 bottom-up (E'_k = A_k - diag(up_k) E'^-1_{k+1}
+// diag(lo_{k+1})).  mode 2: the middle layer on the whole grid, with both Schur terms.
 template <typename T, int NB>
-__global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl *ctl, const int *skip)
+__global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl *ctl, const int *skip, int mode,
+                                                               int mid)
 {
     if (ctl->finished || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = a.S, ld = a.ld, L = a.L;
-    const long long gstride = (long long)gridDim.x * blockDim.x;
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int k = 0; k < L; ++k) {
+    const int half = mode == 1 ? (int)(blockIdx.x >= gridDim.x / 2) : 0;
+    const int nblk = mode == 1 ? (int)gridDim.x / 2 : (int)gridDim.x;
+    const int bid = (int)blockIdx.x - half * nblk;
+    unsigned *bar = a.bar + 2 * half;
+    int *pinfo = a.pinfo + 64 * half;
+    const long long gstride = (long long)nblk * blockDim.x;
+    const long long gtid = (long long)bid * blockDim.x + threadIdx.x;
+    int nsteps = L, k0 = 0, dk = 1;
+    if (mode == 1) {
+        nsteps = half == 0 ? mid : L - 1 - mid;
+        k0 = half == 0 ? 0 : L - 1;
+        dk = half == 0 ? 1 : -1;
+    } else if (mode == 2) {
+        nsteps = 1;
+        k0 = mid;
+        dk = 0;
+    }
+    for (int step = 0; step < nsteps; ++step) {
+        const int k = k0 + step * dk;
         T *D = a.D + (size_t)k * S * ld;
         int *perm = a.perm + (size_t)k * S;
         int *iperm = a.iperm + (size_t)k * S;
-        if (k > 0) {
-            // D'_k = A_k - diag(lo_k) D'^-1_{k-1} diag(up_{k-1}), D'^-1[i][j] = B[perm(i)][iperm(j)]
-            const T *Bp = a.D + (size_t)(k - 1) * S * ld;
-            const int *pp = a.perm + (size_t)(k - 1) * S;
-            const int *ipp = a.iperm + (size_t)(k - 1) * S;
-            const T *lo = a.lo + (size_t)k * S;
-            const T *upp = a.up + (size_t)(k - 1) * S;
+        // Schur terms: D'^-1 of a neighbour n is B_n[perm_n(i)][iperm_n(j)]
+        auto schur = [&](int nbr, const T *rowc, const T *colc) {
+            const T *Bn = a.D + (size_t)nbr * S * ld;
+            const int *pn = a.perm + (size_t)nbr * S;
+            const int *ipn = a.iperm + (size_t)nbr * S;
             for (long long e = gtid; e < (long long)S * S; e += gstride) {
                 int i = (int)(e / S), j = (int)(e - (long long)i * S);
-                D[(size_t)i * ld + j] -= lo[i] * Bp[(size_t)pp[i] * ld + ipp[j]] * upp[j];
+                D[(size_t)i * ld + j] -= rowc[i] * Bn[(size_t)pn[i] * ld + ipn[j]] * colc[j];
             }
+        };
+        if (mode == 2) {
+            if (k > 0) schur(k - 1, a.lo + (size_t)k * S, a.up + (size_t)(k - 1) * S);
+            if (k + 1 < L) schur(k + 1, a.up + (size_t)k * S, a.lo + (size_t)(k + 1) * S);
+        } else if (step > 0) {
+            if (dk > 0) schur(k - 1, a.lo + (size_t)k * S, a.up + (size_t)(k - 1) * S);
+            else schur(k + 1, a.up + (size_t)k * S, a.lo + (size_t)(k + 1) * S);
         }
         for (long long i = gtid; i < S; i += gstride) iperm[i] = -1;
-        if (!grid_barrier(a.bar, ctl)) return;
+        if (!grid_barrier(bar, ctl, nblk)) return;
         for (int c0 = 0; c0 < S; c0 += NB) {
             const int nb = min(NB, S - c0);
-            if (blockIdx.x == 0) panel_factor<T, NB>(D, perm, iperm, a.pinfo, S, ld, c0, nb, ctl, smem);
-            if (!grid_barrier(a.bar, ctl)) return;
-            trailing_update<T, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem);
-            if (!grid_barrier(a.bar, ctl)) return;
+            if (bid == 0) panel_factor<T, NB>(D, perm, iperm, pinfo, S, ld, c0, nb, ctl, smem);
+            if (!grid_barrier(bar, ctl, nblk)) return;
+            trailing_update<T, NB>(D, pinfo, iperm, S, ld, c0, nb, smem, bid, nblk);
+            if (!grid_barrier(bar, ctl, nblk)) return;
         }
     }
 }
@@ -420,7 +448,7 @@ __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_pv(BlockSys<double
                     if (l < nb) Dr[l] = w[l];
             }
             if (!grid_barrier(a.bar, ctl)) return;
-            trailing_update<double, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem);
+            trailing_update<double, NB>(D, a.pinfo, iperm, S, ld, c0, nb, smem, blockIdx.x, gridDim.x);
             if (!grid_barrier(a.bar, ctl)) return;
         }
     }
@@ -739,9 +767,17 @@ static cudaError_t launch_factor_nb(const BlockSys<T> &sys, const FactorPlan &pl
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return e;
     BlockSys<T> a = sys;
-    void *args[] = {(void *)&a, (void *)&ctl, (void *)&skip};
-    count_launches(1);
-    return cudaLaunchCooperativeKernel((const void *)fn, dim3(plan.ctas), dim3(plan.threads), args, plan.smem, st);
+    auto go = [&](int mode, int mid, int ctas) -> cudaError_t {
+        void *args[] = {(void *)&a, (void *)&ctl, (void *)&skip, (void *)&mode, (void *)&mid};
+        count_launches(1);
+        return cudaLaunchCooperativeKernel((const void *)fn, dim3(ctas), dim3(plan.threads), args, plan.smem, st);
+    };
+    if (!(plan.twisted && sys.L >= 3 && plan.ctas >= 2)) return go(0, 0, plan.ctas);
+    // twisted elimination: both ends at once on the two halves of the grid, then the middle layer
+    const int mid = sys.L / 2;
+    e = go(1, mid, plan.ctas & ~1);
+    if (e == cudaSuccess) e = go(2, mid, plan.ctas);
+    return e;
 }
 
 template <int NB>

@@ -238,7 +238,7 @@ __global__ void k_gm_skip_if_finished(GmState *gm, const Ctl *ctl, const int *sk
 
 // Record the solve; a solve that did not reach the tolerance hands the step to
 // the FP64 factorization, and so does every later step at this dt or above.
-__global__ void k_gm_report(const GmState *gm, Ctl *ctl, const int *skip_solve, int role)
+__global__ void k_gm_report(const GmState *gm, Ctl *ctl, const int *skip_solve, int role, int reuse_max_iters)
 {
     if (ctl->finished || (skip_solve && *skip_solve)) return;
     ctl->solver_iters = gm->iters;
@@ -248,7 +248,7 @@ __global__ void k_gm_report(const GmState *gm, Ctl *ctl, const int *skip_solve, 
         ctl->skip64 = 0;               // refactor in FP64 and solve directly
         ctl->used_fp64 = 1;
         if (role == 0 && ctl->dt < ctl->dt_fp64) ctl->dt_fp64 = ctl->dt;
-    } else if (role == 1 && gm->iters > kReuseMaxIters) {
+    } else if (role == 1 && gm->iters > reuse_max_iters) {
         ctl->have64 = 0;               // the reused factorization has drifted: refactor at the next step
     }
 }
@@ -307,7 +307,7 @@ void enqueue_fgmres(const GmArgs &a, cudaStream_t st)
     count_launches(1); k_sub<<<eb, kRedThreads, 0, st>>>(a.b, a.w, a.w, N, a.gm);
     count_launches(1); k_dots<<<kRedBlocks, kRedThreads, 0, st>>>(a.V, 0, a.w, N, a.partials, a.counter, a.red, a.gm, 1);
     count_launches(1); k_final<<<1, 1, 0, st>>>(a.gm, a.red);
-    count_launches(1); k_gm_report<<<1, 1, 0, st>>>(a.gm, a.ctl, a.skip_solve, a.role);
+    count_launches(1); k_gm_report<<<1, 1, 0, st>>>(a.gm, a.ctl, a.skip_solve, a.role, a.reuse_max_iters);
 }
 
 }  // namespace xk

@@ -9,9 +9,6 @@
 namespace xk {
 
 constexpr int kMaxBasis = 32;
-// a solve with the reused FP64 factorization that needs more iterations than this
-// triggers a fresh factorization at the next step
-constexpr int kReuseMaxIters = 6;
 
 struct GmState {
     double H[(kMaxBasis + 1) * kMaxBasis];   // column-major, leading dimension kMaxBasis + 1
@@ -41,6 +38,7 @@ struct GmArgs {
     Ctl *ctl;
     const int *skip_solve;   // this solve is skipped when *skip_solve != 0
     int role;                // 0: FP32-preconditioned attempt, 1: attempt with the reused FP64 factorization
+    int reuse_max_iters;     // role 1: more iterations than this trigger a fresh factorization next step
     VecOp matvec;        // y = A x (FP64); must return at once while *skip != 0
     VecOp precond;       // z ~ A^-1 v (low precision); same skip rule
 };

@@ -105,6 +105,7 @@ struct FactorPlan {
     int ctas;        // persistent CTAs
     int threads;
     size_t smem;
+    int twisted = 0;           // k_factor: eliminate from both ends on the two halves of the grid
     int preview = 0;           // FP64: each panel's pivots chosen first on one CTA (k_factor_pv)
     double *dinv = nullptr;    // that path: nb x nb LU factors of the panel's pivot block (global)
 };
@@ -152,13 +153,15 @@ struct SolvePlan {
     int nbuf;        // prefetch buffers (2, or 1 when two do not fit)
     int threads;
     size_t smem;
-    int twisted = 0; // FP32: two clusters fit at once (sweeps after the twisted elimination)
+    int twisted = 0; // two clusters fit at once (sweeps after the twisted elimination)
 };
 int solve_cluster_plan(int S, int elem_bytes, SolvePlan *out);
 // sweeps after the twisted elimination (two launches of two clusters); ymid: 2 x S doubles
-cudaError_t launch_solve_twisted(const BlockSys<float> &sys, const SolvePlan &plan, const double *b, double *x,
-                                 double *g, double *ymid, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,
-                                 const int *skip = nullptr, const double *xscale = nullptr);
+template <typename T>
+cudaError_t launch_solve_twisted(const BlockSys<T> &sys, const SolvePlan &plan, bool pivoted, const double *b,
+                                 double *x, double *g, double *ymid, Ctl *ctl, cudaStream_t st,
+                                 const double *bscale = nullptr, const int *skip = nullptr,
+                                 const double *xscale = nullptr);
 template <typename T>
 cudaError_t launch_solve_cluster(const BlockSys<T> &sys, const SolvePlan &plan, bool pivoted, const double *b,
                                  double *x, double *g, Ctl *ctl, cudaStream_t st, const double *bscale = nullptr,

@@ -34,7 +34,8 @@ class Config(C.Structure):
         ("f_floor", C.c_double), ("dt_min", C.c_double), ("ss_dt", C.c_double), ("ss_tol", C.c_double),
         ("gmres_restart", C.c_int), ("gmres_max_iter", C.c_int), ("gmres_tol", C.c_double),
         ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
-        ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("twisted", C.c_int),
+        ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("reuse_max_iters", C.c_int),
+        ("twisted", C.c_int),
         ("fp64_panel", C.c_int),
     ]
 
@@ -92,6 +93,7 @@ SIGNATURES = {
     "xk_batch_remove": (C.c_int, [_vp, C.c_int]),
     "xk_batch_step": (C.c_int, [_vp, C.c_int]),
     "xk_batch_poll": (C.c_int, [_vp, C.c_int, C.POINTER(RunInfo), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "xk_batch_last_error": (C.c_char_p, [_vp]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
@@ -346,7 +348,8 @@ class Batch:
     def step(self, nsteps=1):
         rc = lib().xk_batch_step(self.h, int(nsteps))
         if rc != XK_OK:
-            raise XkError("xk_batch_step", rc, "")
+            msg = lib().xk_batch_last_error(self.h)
+            raise XkError("xk_batch_step", rc, msg.decode() if msg else "")
 
     def poll(self, slot):
         info = RunInfo()

@@ -33,9 +33,15 @@ def _alone(p, precision, steps, **kw):
     return c.get_state(), info
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_results_equal_alone(precision):
+@pytest.mark.parametrize("precision,largest_first", [("fp64", False), ("mixed", False), ("mixed", True),
+                                                     ("fp64", True)])
+def test_batch_results_equal_alone(precision, largest_first):
+    """Columns of 20 to 96 species stepped together; created largest first, the
+    last-planned (smallest) column must not shrink the shared-memory limit the
+    others' kernels launch with."""
     probs = _problems()
+    if largest_first:
+        probs = probs[::-1]
     b = xk.Batch(64 << 30, 8)
     cols, slots = [], []
     for p in probs:

@@ -183,18 +183,20 @@ def test_block_solve_late_state_large_dt(pair):
     assert np.max(np.abs(x - ox) / s) < 1e-4
 
 
-@pytest.mark.parametrize("panel,nb", [(1, 8), (1, 16), (1, 32), (0, 8), (0, 16)])
-def test_fp64_factor_variants(panel, nb):
+@pytest.mark.parametrize("panel,nb,twisted", [(1, 8, 0), (1, 16, 0), (1, 32, 0), (0, 8, 1), (0, 8, 0), (0, 16, 1)])
+def test_fp64_factor_variants(panel, nb, twisted):
     """FP64 block inversion with each panel's pivots chosen first and its
     multipliers formed on all CTAs by triangular solves (panel = 1; widths 8,
     16, 32 with ragged last panels on 40 species) and column by column on one
-    CTA (panel = 0), against the oracle's LU: at moderate dt to 1e-10, and near
-    steady state at dt = 1e8 s to the kappa * eps bound of the late-state test
-    at width 8 (wider panels round more there: a numpy emulation of the same
-    elimination errs by 2.6e-4 at width 16 on the 20-species column)."""
+    CTA (panel = 0; top-down, or from both ends on the two halves of the grid
+    meeting in the middle layer, with the matching two-cluster sweeps), against
+    the oracle's LU: at moderate dt to 1e-10, and near steady state at
+    dt = 1e8 s to the kappa * eps bound of the late-state test at width 8
+    (wider panels round more there: a numpy emulation of the same elimination
+    errs by 2.6e-4 at width 16 on the 20-species column)."""
     p = synth.small_column()
     o = Oracle(p)
-    c = xk.Column(p, "fp64", fp64_panel=panel, panel_width=nb)
+    c = xk.Column(p, "fp64", fp64_panel=panel, panel_width=nb, twisted=twisted)
     ng = o.grid()[0]
     n = o.initial_state()
     rng = np.random.default_rng(4)
@@ -210,7 +212,7 @@ def test_fp64_factor_variants(panel, nb):
     x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(fl)))
     ox = o.block_solve(oA, olo, oup, fl)
     s = np.maximum(nl, 1e-20 * ng[:, None])
-    assert np.max(np.abs(x - ox) / s) < (1e-4 if nb == 8 else 1e-1), (panel, nb)
+    assert np.max(np.abs(x - ox) / s) < (1e-4 if nb == 8 else 1e-1), (panel, nb, twisted)
 
 
 def test_fp64_factor_full_size():
@@ -222,13 +224,13 @@ def test_fp64_factor_full_size():
     o = Oracle(p)
     n = o.initial_state()
     f = np.random.default_rng(5).normal(size=n.shape) * n
-    for panel in (0, 1):
-        c = xk.Column(p, "fp64", fp64_panel=panel)
+    for panel, twisted in ((0, 1), (0, 0), (1, 0)):
+        c = xk.Column(p, "fp64", fp64_panel=panel, twisted=twisted)
         for dt in (1e-6, 1e-2):
             oA, olo, oup = o.jacobian(n, dt)
             x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(f)))
             ox = o.block_solve(oA, olo, oup, f)
-            assert np.max(np.abs(x - ox)) / (np.abs(ox).max() + 1e-300) < 1e-10, (panel, dt)
+            assert np.max(np.abs(x - ox)) / (np.abs(ox).max() + 1e-300) < 1e-10, (panel, twisted, dt)
         c.close()
 
 
