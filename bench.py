@@ -39,6 +39,7 @@ SAMPLE_LAYERS = 24          # CPU oracle sample: this many layers of the same co
 PROFILED_TRAFFIC = {
     ("mixed", 16, 8, 1): (371.3e6, "k_factor_cluster<8>, two-chain launch (profiles/k_factor_cluster_594x150.txt)"),
     ("fp64", 152, 8, 0, 0): (833.5e6, "k_factor<double, 8> (profiles/k_factor_fp64_594x150.txt)"),
+    ("fp64", 152, 8, 0, 1): (818.6e6, "k_factor<double, 8>, two-chain launch (profiles/k_factor_fp64_594x150.txt)"),
 }
 
 
@@ -436,7 +437,7 @@ def run_serving(args):
     srv = serving.Server(200 << 30, args.slots, precision="mixed", chunk=8,
                          column_kw=dict(reuse_factorization=1, gmres_restart=10, gmres_max_iter=10))
     t0 = time.perf_counter()
-    res = srv.run(reqs)
+    res = srv.run(reqs, deadline=args.time_limit)
     wall = time.perf_counter() - t0
     srv.close()
     summ = serving.summarize(res, wall)
@@ -446,7 +447,11 @@ def run_serving(args):
         "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "serving-sweep", "requests": args.requests, "rate_per_s": args.rate,
-                   "slots": args.slots, "layers": 150},
+                   "slots": args.slots, "layers": 150, "deadline_s": args.time_limit,
+                   "species": [r.problem.S for r in reqs]},
+        "per_request": [{"S": r.problem.S, "arrival_s": round(x.arrival, 3),
+                         "latency_s": None if x.finished is None else round(x.latency, 3),
+                         "steps": x.steps, "fp64_steps": x.fp64_steps} for r, x in zip(reqs, res)],
         "serving": summ,
     }
     print(json.dumps(line), flush=True)
@@ -474,7 +479,8 @@ def run_steady(args):
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
         t0 = time.perf_counter()
-        steps = acc = fp64_steps = iters = 0
+        steps = acc = fp64_steps = iters = refactors = 0
+        t_model = 0.0
         info = None
         # in chunks, so that a run that would exceed the time limit stops and reports how far it got
         while steps < args.max_steps and time.perf_counter() - t0 < args.time_limit:
@@ -483,13 +489,15 @@ def run_steady(args):
             acc += int(info.accepted)
             fp64_steps += int(info.fp64_steps)
             iters += int(info.solver_iters)
+            refactors += int(info.refactors)
+            t_model += float(info.t)            # each call starts its model clock at 0
             if info.converged or info.steps == 0:
                 break
         end.record(stream)
         torch.cuda.synchronize()
         runs[name] = dict(s=start.elapsed_time(end) / 1e3, wall=time.perf_counter() - t0, steps=steps,
-                          accepted=acc, converged=int(info.converged), t_model=float(info.t), dt=float(info.dt),
-                          fp64_steps=fp64_steps, iters=iters, n=col.get_state())
+                          accepted=acc, converged=int(info.converged), t_model=t_model, dt=float(info.dt),
+                          fp64_steps=fp64_steps, refactors=refactors, iters=iters, n=col.get_state())
         col.close()
         del col
         torch.cuda.empty_cache()
@@ -570,7 +578,8 @@ def main():
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
     ap.add_argument("--variants", default="mixed,fp64", help="--mode steady: paths to run, in order")
-    ap.add_argument("--time-limit", type=float, default=600.0, help="--mode steady: seconds per path")
+    ap.add_argument("--time-limit", type=float, default=600.0,
+                    help="--mode steady: seconds per path; --mode serving: deadline of the serving loop")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="--mode kernels")
     ap.add_argument("--dt", type=float, default=1e-2, help="--mode kernels: step size of the linear steps")
     ap.add_argument("--columns", type=int, default=64)

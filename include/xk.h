@@ -123,6 +123,7 @@ typedef struct {
     double t, dt, max_rel;
     long long solver_iters;   /* total FGMRES iterations */
     long long fp64_steps;     /* mixed mode: steps solved by the FP64 factorization */
+    long long refactors;      /* mixed mode: FP64 factorizations computed (the others reused one) */
 } xk_run_info;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -260,7 +261,14 @@ XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta,
  * xk_batch_remove: releases the slot and its budget; the context returns to
  *   its own stream and factorization plan.
  * xk_batch_last_error: message of the last failed batch call (the failing
- *   column's, for xk_batch_step); owned by the batch, valid until the next call. */
+ *   column's, for xk_batch_step); owned by the batch, valid until the next call.
+ * xk_batch_submit / xk_batch_query: the asynchronous form, so that every column
+ *   advances at its own pace: submit enqueues nsteps controlled steps for one
+ *   slot on its stream and returns (XK_EINVAL if that slot's previous
+ *   submission has not been queried done); query sets *done to 1 once they have
+ *   run (then xk_batch_poll reads that slot's new state) and to 0 before,
+ *   without blocking.  xk_batch_step refuses to run while a submission is in
+ *   flight; xk_batch_remove waits for it. */
 typedef struct xk_batch xk_batch;
 XK_API int xk_batch_create(xk_batch **out, int device, size_t budget_bytes, int max_slots);
 XK_API int xk_batch_destroy(xk_batch *batch);
@@ -269,6 +277,8 @@ XK_API int xk_batch_remove(xk_batch *batch, int slot);
 XK_API int xk_batch_step(xk_batch *batch, int nsteps);
 XK_API int xk_batch_poll(xk_batch *batch, int slot, xk_run_info *info, int *finished, int *status);
 XK_API const char *xk_batch_last_error(xk_batch *batch);
+XK_API int xk_batch_submit(xk_batch *batch, int slot, int nsteps);
+XK_API int xk_batch_query(xk_batch *batch, int slot, int *done);
 
 /* ---- block solve without any device allocation ----
  * The paper has no counterpart: this entry point serves callers that cannot

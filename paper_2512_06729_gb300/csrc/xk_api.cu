@@ -798,6 +798,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
         info->max_rel = h.max_rel;
         info->solver_iters = h.total_iters;
         info->fp64_steps = h.fp64_steps;
+        info->refactors = h.refactors;
     }
     if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
     if (h.status) return fail(c, h.status, "run stopped with status %d", h.status);
@@ -982,6 +983,8 @@ long long xk_launch_count(void) { return launches(); }
 struct BatchSlot {
     xk_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;      // end of the steps submitted last (xk_batch_submit)
+    bool inflight = false;
     cudaStream_t saved_st = nullptr;
     FactorPlan saved_plan{}, saved_plan64{};
     size_t bytes = 0;
@@ -1027,6 +1030,7 @@ int xk_batch_remove(xk_batch *b, int slot)
     s.ctx->st = s.saved_st;
     s.ctx->plan = s.saved_plan;
     s.ctx->plan64 = s.saved_plan64;
+    if (s.ev) cudaEventDestroy(s.ev);
     cudaStreamDestroy(s.st);
     b->used -= s.bytes;
     s = BatchSlot();
@@ -1061,6 +1065,11 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
     BatchSlot &s = b->slots[free_slot];
     if (cudaStreamSynchronize(c->st) != cudaSuccess || cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_check(c, "batch_add");
+    if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(s.st);
+        s = BatchSlot();
+        return cuda_check(c, "batch_add");
+    }
     // a share of the SMs for this column's persistent kernels
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -1068,6 +1077,7 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
     FactorPlan p, p64;
     int sz = c->cfg.precision == XK_PREC_FP64 ? 8 : 4;
     if (factor_plan(c->S, sz, c->plan.nb, share, &p) != 0 || factor_plan(c->S, 8, c->plan64.nb, share, &p64) != 0) {
+        cudaEventDestroy(s.ev);
         cudaStreamDestroy(s.st);
         s = BatchSlot();
         return fail(c, XK_EINVAL, "no factorization plan for a %d-CTA share", share);
@@ -1102,6 +1112,11 @@ int xk_batch_step(xk_batch *b, int nsteps)
     cudaSetDevice(b->device);
     // round-robin so that every column's next step is queued before the following ones
     b->err.clear();
+    for (auto &s : b->slots)
+        if (s.ctx && s.inflight) {
+            b->err = "a slot has submitted steps in flight (query it first)";
+            return XK_EINVAL;
+        }
     for (int k = 0; k < nsteps; ++k)
         for (auto &s : b->slots)
             if (s.ctx && !s.finished) {
@@ -1129,6 +1144,56 @@ int xk_batch_step(xk_batch *b, int nsteps)
 
 const char *xk_batch_last_error(xk_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
+int xk_batch_submit(xk_batch *b, int slot, int nsteps)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx || nsteps <= 0) return XK_EINVAL;
+    BatchSlot &s = b->slots[slot];
+    if (s.inflight) {
+        b->err = "steps already submitted to this slot";
+        return XK_EINVAL;
+    }
+    if (s.finished) return XK_OK;
+    cudaSetDevice(b->device);
+    b->err.clear();
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = enqueue_step(s.ctx);
+        if (rc) {
+            b->err = s.ctx->err;
+            return rc;
+        }
+    }
+    cudaMemcpyAsync(s.ctx->ctl_host, s.ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s.st);
+    if (cudaEventRecord(s.ev, s.st) != cudaSuccess) {
+        int rc = fail(s.ctx, XK_ECUDA, "batch submit: %s", cudaGetErrorString(cudaGetLastError()));
+        b->err = s.ctx->err;
+        return rc;
+    }
+    s.inflight = true;
+    return XK_OK;
+}
+
+int xk_batch_query(xk_batch *b, int slot, int *done)
+{
+    if (!b || !done || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx) return XK_EINVAL;
+    BatchSlot &s = b->slots[slot];
+    *done = 1;
+    if (!s.inflight) return XK_OK;
+    cudaError_t e = cudaEventQuery(s.ev);
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        *done = 0;
+        return XK_OK;
+    }
+    s.inflight = false;
+    if (e != cudaSuccess) {
+        int rc = fail(s.ctx, XK_ECUDA, "batch query: %s", cudaGetErrorString(e));
+        b->err = s.ctx->err;
+        return rc;
+    }
+    s.finished = s.ctx->ctl_host->finished != 0;
+    return XK_OK;
+}
+
 int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *status)
 {
     if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx) return XK_EINVAL;
@@ -1143,6 +1208,7 @@ int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *
         info->max_rel = h.max_rel;
         info->solver_iters = h.total_iters;
         info->fp64_steps = h.fp64_steps;
+        info->refactors = h.refactors;
     }
     if (finished) *finished = b->slots[slot].finished ? 1 : 0;
     if (status) *status = h.err_timeout ? XK_ETIMEOUT : h.status;

@@ -29,8 +29,8 @@ class Request:
 class Result:
     rid: int
     arrival: float
-    admitted: float
-    finished: float
+    admitted: float | None      # None: never admitted before the deadline
+    finished: float | None      # None: not finished before the deadline
     converged: bool
     steps: int
     fp64_steps: int
@@ -64,8 +64,10 @@ def sweep_requests(n, rate, seed=0, mix=((96, 0.6), (250, 0.3), (594, 0.1)), lay
 
 
 class Server:
-    """Admission by HBM footprint into a fixed number of slots; steps of
-    `chunk` controlled steps per batch iteration."""
+    """Admission by HBM footprint into a fixed number of slots; each admitted
+    column gets `chunk` controlled steps at a time on its own stream, the next
+    chunk as soon as the previous one has run, so that small columns are not
+    paced by large ones."""
 
     def __init__(self, budget_bytes, max_slots, precision="mixed", device=0, chunk=4, max_steps=4000,
                  keep_states=False, column_kw=None):
@@ -80,17 +82,34 @@ class Server:
         self.column_kw = column_kw or {}
         self.budget = budget_bytes
 
-    def run(self, requests, clock=None):
+    def run(self, requests, clock=None, deadline=None):
         """Serve all requests; arrival times are honoured against a wall clock
-        that starts now.  Returns the list of Results in request order."""
+        that starts now.  Returns the list of Results in request order; with a
+        deadline (seconds) the loop stops there and the requests not finished
+        by then are returned with finished=None."""
         clock = clock or time.perf_counter
         t0 = clock()
         pending = sorted(requests, key=lambda r: r.arrival)
         waiting = []
         active = {}            # slot -> (request, column, admitted time)
+        inflight = set()       # slots with submitted steps not yet seen done
         results = {}
         while pending or waiting or active:
             now = clock() - t0
+            if deadline is not None and now >= deadline:
+                for slot in list(active):
+                    req, col, adm = active.pop(slot)
+                    while slot in inflight and not self.batch.query(slot):
+                        time.sleep(0.0005)
+                    inflight.discard(slot)
+                    info, _, _ = self.batch.poll(slot)
+                    self.batch.remove(slot)
+                    results[req.rid] = Result(req.rid, req.arrival, adm, None, False, int(info.steps),
+                                              int(info.fp64_steps), None)
+                    col.close()
+                for req in waiting + pending:
+                    results[req.rid] = Result(req.rid, req.arrival, None, None, False, 0, 0, None)
+                break
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.pop(0))
             # admit in arrival order while slots and budget allow
@@ -109,8 +128,17 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - (clock() - t0))))
                 continue
-            self.batch.step(self.chunk)
+            # every column advances at its own pace: a slot whose last chunk has run gets the next
+            for slot in active:
+                if slot not in inflight:
+                    self.batch.submit(slot, self.chunk)
+                    inflight.add(slot)
+            progressed = False
             for slot in list(active):
+                if not self.batch.query(slot):
+                    continue
+                inflight.discard(slot)
+                progressed = True
                 info, finished, status = self.batch.poll(slot)
                 if finished or info.steps >= self.max_steps:
                     req, col, adm = active.pop(slot)
@@ -120,6 +148,8 @@ class Server:
                                               int(info.steps), int(info.fp64_steps), state)
                     col.close()
                     del col
+            if not progressed:
+                time.sleep(0.0005)
         return [results[r.rid] for r in requests]
 
     def close(self):
@@ -127,14 +157,16 @@ class Server:
 
 
 def summarize(results, wall):
-    lat = np.array([r.latency for r in results])
+    done = [r for r in results if r.finished is not None]
+    lat = np.array([r.latency for r in done]) if done else np.array([np.nan])
     return {
         "requests": len(results),
+        "finished": len(done),
         "converged": int(sum(r.converged for r in results)),
         "p50_s": float(np.percentile(lat, 50)),
         "p99_s": float(np.percentile(lat, 99)),
         "mean_s": float(lat.mean()),
-        "solves_per_s": len(results) / wall,
+        "solves_per_s": len(done) / wall,
         "steps_total": int(sum(r.steps for r in results)),
         "fp64_steps_total": int(sum(r.fp64_steps for r in results)),
     }

@@ -49,7 +49,7 @@ class StepInfo(C.Structure):
 class RunInfo(C.Structure):
     _fields_ = [("converged", C.c_int), ("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int),
                 ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double), ("solver_iters", C.c_longlong),
-                ("fp64_steps", C.c_longlong)]
+                ("fp64_steps", C.c_longlong), ("refactors", C.c_longlong)]
 
 
 class XkError(RuntimeError):
@@ -94,6 +94,8 @@ SIGNATURES = {
     "xk_batch_step": (C.c_int, [_vp, C.c_int]),
     "xk_batch_poll": (C.c_int, [_vp, C.c_int, C.POINTER(RunInfo), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "xk_batch_last_error": (C.c_char_p, [_vp]),
+    "xk_batch_submit": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "xk_batch_query": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
@@ -350,6 +352,24 @@ class Batch:
         if rc != XK_OK:
             msg = lib().xk_batch_last_error(self.h)
             raise XkError("xk_batch_step", rc, msg.decode() if msg else "")
+
+    def _raise(self, name, rc):
+        msg = lib().xk_batch_last_error(self.h)
+        raise XkError(name, rc, msg.decode() if msg else "")
+
+    def submit(self, slot, nsteps):
+        """Enqueue nsteps controlled steps for one slot without waiting."""
+        rc = lib().xk_batch_submit(self.h, int(slot), int(nsteps))
+        if rc != XK_OK:
+            self._raise("xk_batch_submit", rc)
+
+    def query(self, slot):
+        """True once the slot's submitted steps have run (then poll() is current)."""
+        done = C.c_int(0)
+        rc = lib().xk_batch_query(self.h, int(slot), C.byref(done))
+        if rc != XK_OK:
+            self._raise("xk_batch_query", rc)
+        return bool(done.value)
 
     def poll(self, slot):
         info = RunInfo()

@@ -96,3 +96,26 @@ def test_serving_results_equal_alone():
         assert r.finished >= r.admitted >= r.arrival - 1e-9
     s = serving.summarize(res, max(r.finished for r in res))
     assert s["requests"] == 4 and s["converged"] == 4 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_batch_submit_query():
+    """Asynchronous form: a slot's submitted steps run on its own stream; the
+    synchronous step refuses while they are in flight; after query reports
+    them done, poll shows exactly that many steps."""
+    p = synth.tiny_column()
+    b = xk.Batch(8 << 30, 2)
+    c = xk.Column(p, "fp64")
+    c.set_mixing_ratios(p.f0)
+    slot = b.add(c, 1e-8)
+    b.submit(slot, 4)
+    with pytest.raises(xk.XkError):
+        b.submit(slot, 1)
+    with pytest.raises(xk.XkError):
+        b.step(1)
+    while not b.query(slot):
+        pass
+    info, finished, status = b.poll(slot)
+    assert info.steps == 4 and status == 0 and not finished
+    b.step(2)
+    assert b.poll(slot)[0].steps == 6
+    b.close()

@@ -43,6 +43,12 @@ class FakeBatch:
         for v in self.active.values():
             v[1] += n
 
+    def submit(self, slot, n):
+        self.active[slot][1] += n
+
+    def query(self, slot):
+        return True
+
     def poll(self, slot):
         col, steps = self.active[slot]
         need = col.prob.S // 10          # fake work: proportional to the size
@@ -102,3 +108,26 @@ def test_sweep_requests_shape():
     assert T.min() >= 800 and T.max() <= 2500
     met = np.array([c[3] for c in calls])
     assert met.min() >= 1 and met.max() <= 100
+
+
+def test_deadline_reports_unfinished(monkeypatch):
+    """With a deadline the loop stops there: finished requests keep their
+    latency, active and waiting ones are returned unfinished, and the summary
+    counts only the finished ones."""
+    monkeypatch.setattr(serving.xk, "Column", FakeColumn)
+    monkeypatch.setattr(serving.xk, "Batch", FakeBatch)
+    probs = [types.SimpleNamespace(name=f"r{i}", S=s, f0=None) for i, s in enumerate([40, 10 ** 6, 40, 40])]
+    reqs = [serving.Request(i, 0.0, p) for i, p in enumerate(probs)]
+    t = [0.0]
+
+    def clock():
+        t[0] += 0.001
+        return t[0]
+
+    srv = serving.Server(budget_bytes=10 ** 9, max_slots=1, chunk=2)
+    res = srv.run(reqs, clock=clock, deadline=0.5)
+    assert res[0].finished is not None and res[0].converged
+    assert res[1].finished is None and res[1].admitted is not None     # the long one was running
+    assert res[2].finished is None and res[2].admitted is None         # never admitted
+    s = serving.summarize(res, t[0])
+    assert s["requests"] == 4 and s["finished"] == 1
