@@ -215,13 +215,24 @@ class Column:
         self._call("xk_set_mixing_ratios", self._ptr(t), 1)
 
     def set_state(self, n):
+        """n: numpy array or torch tensor (host, e.g. pinned, or on this device), [L, S] FP64."""
         if isinstance(n, np.ndarray):
             a = _np(n, np.float64)
             self._call("xk_set_state", _vp(a.ctypes.data), 0)
         else:
-            self._call("xk_set_state", self._ptr(n.contiguous()), 1)
+            t = n.contiguous()
+            if t.dtype != self._torch.float64 or t.numel() != self.L * self.S:
+                raise ValueError("state must be FP64 with L x S entries")
+            self._call("xk_set_state", _vp(t.data_ptr()), 0 if t.device.type == "cpu" else 1)
 
-    def get_state(self, device=False):
+    def get_state(self, device=False, out=None):
+        """The state [L, S]: a new numpy array, a new device tensor (device=True), or into `out`
+        (a contiguous FP64 torch tensor on the host, e.g. pinned, or on this device)."""
+        if out is not None:
+            if out.dtype != self._torch.float64 or out.numel() != self.L * self.S or not out.is_contiguous():
+                raise ValueError("out must be a contiguous FP64 tensor with L x S entries")
+            self._call("xk_get_state", _vp(out.data_ptr()), 0 if out.device.type == "cpu" else 1)
+            return out
         if device:
             out = self._dev(self.L, self.S)
             self._call("xk_get_state", self._ptr(out), 1)
