@@ -19,12 +19,13 @@ from . import build as _build
 CANDIDATES = {
     "fp64": [dict(panel_width=8, factor_ctas=152), dict(panel_width=16, factor_ctas=152),
              dict(panel_width=8, factor_ctas=76), dict(fp64_panel=1, panel_width=8, factor_ctas=152)],
-    "mixed": [dict(cluster_size=16, panel_width=16), dict(cluster_size=12, panel_width=16),
-              dict(cluster_size=8, panel_width=16), dict(cluster_size=16, panel_width=8),
+    "mixed": [dict(cluster_size=16, panel_width=8), dict(cluster_size=16, panel_width=16),
+              dict(cluster_size=12, panel_width=16), dict(cluster_size=8, panel_width=16),
               dict(cluster_size=-1, panel_width=16, factor_ctas=152),
               dict(cluster_size=-1, panel_width=32, factor_ctas=76)],
 }
 CACHE = os.path.join(_build.BUILD, "autotune.json")
+TIE = 1.03
 
 
 def _gpu_name():
@@ -78,7 +79,10 @@ def tune(prob, precision, layers=6, verbose=False):
             print(f"  {precision} S={prob.S} {params}: {t:.3f} ms/layer", flush=True)
     if not table:
         raise RuntimeError("no factorization configuration ran")
-    t, params = min(table, key=lambda x: x[0])
+    # the first candidate (in the list's order of preference) within 3 % of the fastest: timing
+    # noise should not flip the choice between runs
+    best = min(x[0] for x in table)
+    t, params = next(x for x in table if x[0] <= best * TIE)
     data = _load()
     data[_key(prob.S, precision)] = {"params": params, "ms_per_layer": t,
                                      "table": [[x[1], x[0]] for x in table]}
