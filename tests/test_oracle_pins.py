@@ -423,3 +423,99 @@ def test_step_rejects_and_halves_on_large_change():
     np.testing.assert_array_equal(m, n)
     m, info = o.step(n, 1e-12)
     assert info.accepted == 1 and info.dt_next == pytest.approx(3e-12)
+
+
+# ------------------------------------------------- non-isothermal transport and grid (Sec. 2.1, Eq. 2)
+
+def test_hydrostatic_grid_for_temperature_linear_in_log_pressure():
+    """With T linear in x = ln(P_0 / P), hydrostatic balance dz = k_B T / (mbar g) dx
+    integrates to z = k_B / (mbar g) (T_0 x + a x^2 / 2) exactly; the grid takes
+    each step with the interface temperature, which is exact for a linear T.
+    Unevenly spaced pressures make the check sensitive to which temperature
+    each step uses."""
+    rng = np.random.default_rng(7)
+    L = 31
+    x = np.concatenate([[0.0], np.cumsum(rng.uniform(0.1, 0.8, L - 1))])
+    P0, T0, a = 30.0, 1900.0, -60.0
+    P = P0 * np.exp(-x)
+    T = T0 + a * x
+    p = custom_problem(np.eye(2, dtype=np.int32), [2.0, 4.0], [], np.stack([nasa_const_cp(2.5, 0, 0)] * 2),
+                       P, T, Kzz=np.full(L, 1e8), mbar=2.3, g=2.0e3)
+    ngas, z, dz, dzi = Oracle(p).grid()
+    c = KB / (2.3 * AMU * 2.0e3)
+    np.testing.assert_allclose(z, c * (T0 * x + 0.5 * a * x * x), rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(dzi, np.diff(z), rtol=1e-12)
+    np.testing.assert_allclose(ngas, P * 1e6 / (KB * T), rtol=1e-14)
+
+
+def _thermal_column(L, alpha_T, m_y, P0=1.0, Ptop=1e-3, Tbot=1800.0, Ttop=1000.0, mbar=2.3):
+    """One trace species with molecular diffusion only (K = 0) on a column whose
+    temperature falls linearly in ln P from Tbot to Ttop."""
+    P = np.geomspace(P0, Ptop, L)
+    x = np.log(P0 / P)
+    T = Tbot + (Ttop - Tbot) * x / x[-1]
+    f0 = np.full((L, 1), 1e-6)
+    return custom_problem(np.eye(1, dtype=np.int32), [m_y], [], np.stack([nasa_const_cp(2.5, 0, 0)]),
+                          P, T, Kzz=np.zeros(L), dcoef=np.full(1, 1e17), f0=f0, mbar=mbar, alpha_T=alpha_T)
+
+
+@pytest.mark.parametrize("alpha_T,m_y", [(0.0, 4.0), (-0.35, 4.0), (0.25, 3.0)])
+def test_molecular_diffusion_equilibrium_non_isothermal(alpha_T, m_y):
+    """K = 0 on a column with a steep temperature gradient: zero molecular flux
+    in Eq. 2, dn/dz + n (1/H_y + (1 + alpha_T) T'/T) = 0 with H_y = k_B T /
+    (m_y g), integrates under hydrostatic balance (dz = k_B T / (mbar g) d ln(1/P))
+    to n_y T^(1 + alpha_T) proportional to P^(m_y / mbar).  The oracle's own
+    relaxed steady state must follow that profile to the discretisation error
+    (O(h^2), h the layer spacing in scale heights); a flipped or dropped
+    thermal term changes the top-to-bottom ratio by a factor 1.8^2 or 1.8
+    (the centred flux errs by (h/H_y)^3 / 12 per layer: 4e-4 over the column
+    for these masses)."""
+    L = 600
+    p = _thermal_column(L, alpha_T, m_y)
+    o = Oracle(p)
+    n0 = o.initial_state()
+    pol = default_policy(dt_max=1e30, ss_dt=1e30, ss_tol=1e-13, rel_reject=1e300, grow_max=1e6)
+    n, info = o.run_to_steady(n0, dt0=1e6, max_steps=200, policy=pol)
+    assert info.converged
+    prof = (p.P_bar / p.P_bar[0]) ** (m_y / p.mbar) * (p.T[0] / p.T) ** (1.0 + alpha_T)
+    shape = n[:, 0] / n[0, 0]
+    np.testing.assert_allclose(shape, prof, rtol=1e-3)
+    # the column content is conserved by the zero-flux boundaries
+    dz = o.grid()[2]
+    assert np.sum(dz * n[:, 0]) == pytest.approx(np.sum(dz * n0[:, 0]), rel=1e-9)
+
+
+def test_three_body_reverse_rate_keeps_equilibrium_in_fall_off():
+    """A + B (+M) <-> C in the fall-off regime with Troe broadening (at the
+    centre of the fall-off curve, F = F_cent = 0.25): the reverse rate is the fall-off-corrected k_f
+    divided by K_c (Sec. 2.3.2, 2.3.4), so the closed layer still relaxes to
+    p_C p0 / (p_A p_B) = exp(-dG/RT) whatever the broadening; and k_f / k_r
+    equals K_c in concentration units, K_p k_B T / p0 (one fewer product)."""
+    T = 1300.0
+    nasa = np.stack([nasa_const_cp(2.5, 3000.0, 5.0), nasa_const_cp(3.0, -2000.0, 8.0),
+                     nasa_const_cp(4.5, -45000.0, 2.0)])
+    elem = np.array([[1, 0], [0, 1], [1, 1]], np.int32)
+    a0 = [2e-30, -1.0, 100.0]
+    ai = [3e-11, 0.5, 50.0]
+    troe = [0.6, 100.0, 1500.0, 0.0]
+    k0 = a0[0] * (T / 300) ** a0[1] * math.exp(-a0[2] / T)
+    ki = ai[0] * (T / 300) ** ai[1] * math.exp(-ai[2] / T)
+    Fc = 0.4 * math.exp(-T / 100.0) + 0.6 * math.exp(-T / 1500.0)
+    M = 10 ** (0.4 + 0.67 * math.log10(Fc)) * ki / k0  # the centre of the fall-off curve: F = F_cent
+    P_bar = M * KB * T / 1e6
+    rx = [dict(type=1, reac=[0, 1], prod=[2], arr=[0, 0, 0] + a0 + ai, troe=troe)]
+    f0 = np.array([[0.3, 0.3, 0.4]])
+    p = custom_problem(elem, [10.0, 12.0, 22.0], rx, nasa, [P_bar], [T], f0=f0)
+    o = Oracle(p)
+    kf, kr = o.rate_coefficients()
+    lind = k0 * M / (1 + k0 * M / ki)
+    assert kf[0, 0] / lind == pytest.approx(Fc, rel=1e-9)
+    g = [gibbs_rt(nasa[i], T) for i in range(3)]
+    Kp = math.exp(-(g[2] - g[0] - g[1]))
+    assert kf[0, 0] / kr[0, 0] == pytest.approx(Kp * KB * T / 1e6, rel=1e-12)
+    # relaxes within ~1 s; much larger steps meet the conserved directions at condition numbers near 1e20
+    n, info = o.run_to_steady(o.initial_state(), policy=default_policy(ss_tol=1e-12, dt_max=1e4, ss_dt=1e4),
+                              max_steps=4000)
+    assert info.converged
+    pr = n[0] * KB * T / 1e6
+    assert pr[2] / (pr[0] * pr[1]) == pytest.approx(Kp, rel=1e-8)
