@@ -106,6 +106,16 @@ typedef struct {
                              16); 1 chooses each panel's pivots first on one CTA (elimination of the
                              unpivoted rows only) and forms the panel's multipliers on all CTAs by
                              triangular solves with the pivot block's LU factors (8, 16 or 32) */
+    int refine_max_iter;  /* FGMRES iterations in FP64 on the exact FP64 operator around an FP64
+                             factorization, used as the preconditioner: the plain FP64 path and the
+                             mixed path's FP64 route (default 10; stops at gmres_tol).  A direct solve
+                             with stored block inverses carries their backward error times the
+                             system's condition number; the iterations bring the residual down to
+                             gmres_tol.  0 = direct solve only */
+    long long wait_polls; /* every device-side wait on other CTAs (the grid barriers of the FP64
+                             factorization) gives up after this many polls, about 0.1 us each, and
+                             the call returns XK_ETIMEOUT with the context still usable (0: 2^24
+                             polls, one to two seconds) */
 } xk_config;
 
 typedef struct {
@@ -131,7 +141,8 @@ XK_API int xk_version(void);
 
 /* Fill cfg with the default policy: FP64, dt_max 1e8 s, rel_reject 1.0,
  * rel_target 0.5, grow 3, shrink 0.5, neg_tol 1e-12, f_floor 1e-20,
- * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 40 iterations, 1e-14. */
+ * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 40 iterations, tolerance
+ * 1e-15, 10 refinement iterations around FP64 factorizations. */
 XK_API int xk_config_init(xk_config *cfg);
 
 /* Create a context for one atmospheric column on cfg->device.  *out is set
@@ -233,8 +244,9 @@ XK_API int xk_block_solve(xk_ctx *ctx, const double *A, const double *lo, const 
 XK_API int xk_block_solve32(xk_ctx *ctx, const double *A, const double *lo, const double *up,
                             const double *f, double *x);
 /* delta solving (I/dt - J(n)) delta = F(n) with the context's precision
- * mode (device n, delta).  *iters / *resid report the FGMRES work (mixed;
- * *iters = -1 when the FP64 fallback solved the step). */
+ * mode (device n, delta).  *iters / *resid report the FGMRES work (in mixed
+ * mode *iters = -1 when the FP64 route solved the step; in FP64 mode the
+ * refinement iterations around the FP64 factorization). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
 
 /* ---- batches of columns: continuous batching on one GPU ----
@@ -287,7 +299,9 @@ XK_API int xk_batch_query(xk_batch *batch, int slot, int *done);
  * while other streams are captured).  It solves the same block-tridiagonal
  * system as xk_block_solve with the same FP64 kernels, without a context or
  * a workspace.  A [L*S*S], lo [L*S], up [L*S], f [L*S] and x [L*S] are
- * caller-owned device pointers of the current device; A is not modified;
+ * caller-owned device pointers of the current device (anything else, a host
+ * pointer for instance, is refused with XK_EINVAL before any work is queued;
+ * the caller answers for their extents); A is not modified;
  * stream is a cudaStream_t (NULL: legacy default stream).  The call
  * synchronizes the stream.
  * Scratch lives in one file-scope device array of XK_NOALLOC_SCRATCH_BYTES
@@ -300,7 +314,9 @@ XK_API int xk_batch_query(xk_batch *batch, int slot, int *done);
  * call's contents (the control flags and barrier words are cleared at the
  * start of each call), so calls that overlap on the GPU, from any thread or
  * stream, race and must be serialized by the caller.
- * Returns XK_OK, XK_EINVAL, XK_ENOMEM, XK_ESINGULAR, XK_ETIMEOUT or XK_ECUDA. */
+ * A refused copy or clear of the scratch returns XK_ECUDA without launching
+ * anything.  Returns XK_OK, XK_EINVAL, XK_ENOMEM, XK_ESINGULAR, XK_ETIMEOUT or
+ * XK_ECUDA. */
 #define XK_NOALLOC_SCRATCH_BYTES (32u << 20)
 XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *lo, const double *up,
                                   const double *f, double *x, void *stream);
@@ -328,6 +344,15 @@ XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *l
 #define XK_PH_COUNT 9
 XK_API int xk_profile(xk_ctx *ctx, int enable);
 XK_API int xk_profile_read(xk_ctx *ctx, double *ms, long long *calls, int n);
+/* Testing aid for the bounded waits: makes the next grid barrier of the
+ * context's FP64 factorization unreachable (its arrival count is raised past
+ * any grid), as if a CTA never arrived.  The waiting CTAs give up after
+ * cfg.wait_polls polls, the call that ran the factorization returns
+ * XK_ETIMEOUT, and the library clears the barrier words, so that the next call
+ * on the context runs normally.  Nothing faults: the kernels that follow a
+ * timed-out factorization return at once. */
+XK_API int xk_hold_next_barrier(xk_ctx *ctx);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all
  * contexts of the process; kernels that exit at once because their solve or
  * step has finished are counted too). */

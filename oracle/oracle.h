@@ -84,7 +84,12 @@ void ora_jacobian(const ora_problem *p, const double *kf, const double *kr, cons
 /* Block Thomas with partial-pivot LU per block; A is overwritten.  Returns 0 or -1 (singular). */
 int ora_block_solve(int L, int S, double *A, const double *lo, const double *up,
                     const double *f, double *x);
-/* One linearly implicit backward-Euler step of size dt: delta solves (I/dt - J) delta = F. */
+/* The same solve followed by `sweeps` rounds of FP64 iterative refinement with the
+ * stored factors (A, lo, up unchanged). */
+int ora_block_solve_refined(int L, int S, const double *A, const double *lo, const double *up,
+                            const double *f, double *x, int sweeps);
+/* One linearly implicit backward-Euler step of size dt: delta solves (I/dt - J) delta = F
+ * (block Thomas plus FP64 iterative refinement). */
 int ora_step_delta(const ora_problem *p, const double *n, double dt, double *delta);
 /* One controlled step: accept/reject, clip, next dt.  n is updated when accepted. */
 int ora_step(const ora_problem *p, const ora_policy *pol, double *n, double dt, ora_step_info *info);

@@ -88,6 +88,8 @@ def lib():
         l.ora_block_solve.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp]
         l.ora_block_solve.restype = C.c_int
         l.ora_step_delta.argtypes = [P, _dp, C.c_double, _dp]; l.ora_step_delta.restype = C.c_int
+        l.ora_block_solve_refined.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_int]
+        l.ora_block_solve_refined.restype = C.c_int
         l.ora_step.argtypes = [P, C.POINTER(Policy), _dp, C.c_double, C.POINTER(StepInfo)]
         l.ora_run_to_steady.argtypes = [P, C.POINTER(Policy), _dp, C.c_double, C.c_int, C.POINTER(RunInfo)]
         l.ora_run_to_steady.restype = C.c_int
@@ -191,6 +193,15 @@ class Oracle:
         x = np.zeros((self.L, self.S))
         rc = lib().ora_block_solve(self.L, self.S, _d(A), _d(np.ascontiguousarray(lo)),
                                    _d(np.ascontiguousarray(up)), _d(np.ascontiguousarray(f)), _d(x))
+        if rc != 0:
+            raise ZeroDivisionError("singular block")
+        return x
+
+    def block_solve_refined(self, A, lo, up, f, sweeps=4):
+        x = np.zeros((self.L, self.S))
+        rc = lib().ora_block_solve_refined(self.L, self.S, _d(np.ascontiguousarray(A, np.float64)),
+                                           _d(np.ascontiguousarray(lo)), _d(np.ascontiguousarray(up)),
+                                           _d(np.ascontiguousarray(f)), _d(x), int(sweeps))
         if rc != 0:
             raise ZeroDivisionError("singular block")
         return x

@@ -195,6 +195,15 @@ void build_indices(xk_ctx *c)
         }
 }
 
+// Krylov basis size: FGMRES(m) of the mixed path; in FP64 mode only the refinement around the
+// FP64 factorization runs, with at most refine_max_iter iterations.
+int basis_size(const xk_ctx *c)
+{
+    int m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
+    if (c->cfg.precision == XK_PREC_FP64) m = std::min(m, std::max(c->cfg.refine_max_iter, 1));
+    return m;
+}
+
 // Lay out the workspace; with base == nullptr only the size is computed.
 size_t layout(xk_ctx *c, char *base)
 {
@@ -237,28 +246,29 @@ size_t layout(xk_ctx *c, char *base)
     c->A64 = b.take<double>((size_t)L * S * ld);
     c->lo64 = b.take<double>(LS);
     c->up64 = b.take<double>(LS);
+    // FGMRES: around the FP32 inversion (mixed), around FP64 factorizations (both modes)
+    const int m = basis_size(c);
+    c->V = b.take<double>((size_t)(m + 1) * LS);
+    c->Z = b.take<double>((size_t)m * LS);
+    c->gw = b.take<double>(LS);
+    c->rowd = b.take<double>(LS);
+    c->bhat = b.take<double>(LS);
+    c->h1 = b.take<double>(kMaxBasis + 1);
+    c->h2 = b.take<double>(kMaxBasis + 1);
+    c->red = b.take<double>(8);
+    c->partials = b.take<double>((size_t)kGmPartialBlocks * (kMaxBasis + 1));
+    c->counter = b.take<unsigned>(8);
+    c->gm = b.take<GmState>(1);
     if (c->cfg.precision == XK_PREC_FP64) {
         c->A32 = nullptr; c->lo32 = nullptr; c->up32 = nullptr;
     } else {
         c->A32 = b.take<float>((size_t)L * S * ld);
         c->lo32 = b.take<float>(LS);
         c->up32 = b.take<float>(LS);
-        int m = std::min(std::max(c->cfg.gmres_restart, 1), kMaxBasis);
-        c->V = b.take<double>((size_t)(m + 1) * LS);
-        c->Z = b.take<double>((size_t)m * LS);
-        c->gw = b.take<double>(LS);
-        c->rowd = b.take<double>(LS);
-        c->bhat = b.take<double>(LS);
         c->gbuf = b.take<float>(4 * (size_t)S * 32);
         c->s64 = b.take<double>(LS);
         c->pin = b.take<double>(LS);
         c->pout = b.take<double>(LS);
-        c->h1 = b.take<double>(kMaxBasis + 1);
-        c->h2 = b.take<double>(kMaxBasis + 1);
-        c->red = b.take<double>(8);
-        c->partials = b.take<double>((size_t)kGmPartialBlocks * (kMaxBasis + 1));
-        c->counter = b.take<unsigned>(8);
-        c->gm = b.take<GmState>(1);
         c->ridx32 = b.take<int>(LS);    // the FP64 factorization's pivots stay intact for reuse
         c->sig32 = b.take<int>(LS);
     }
@@ -336,12 +346,57 @@ void set_preview(xk_ctx *c, FactorPlan *p)
     p->twisted = (c->cfg.twisted && !p->preview && c->use_cluster_solve64 && c->splan64.twisted) ? 1 : 0;
 }
 
+// A control block with nothing decided yet and the context's bound on device-side waits.
+Ctl fresh_ctl(const xk_ctx *c)
+{
+    Ctl init{};
+    init.wait_polls = c->cfg.wait_polls > 0 ? (unsigned long long)c->cfg.wait_polls : 0ull;
+    return init;
+}
+
+// A bounded wait gave up: the barrier words hold arrivals of the abandoned launch, so clear them
+// (and the flag) before the context is used again.
+int timed_out(xk_ctx *c)
+{
+    cudaMemsetAsync(c->bar, 0, 8 * sizeof(unsigned), c->st);
+    cudaMemsetAsync(&c->ctl->err_timeout, 0, sizeof(int), c->st);
+    cudaMemsetAsync(&c->ctl_aux->err_timeout, 0, sizeof(int), c->st);
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "clearing a timed-out wait: %s", cudaGetErrorString(e));
+    return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+}
+
 int need_ready(xk_ctx *c)
 {
     if (!c) return XK_EINVAL;
     if (!c->ready) return fail(c, XK_EINVAL, "workspace not set (load network, photolysis and atmosphere, then xk_set_workspace)");
     cudaSetDevice(c->cfg.device);
     return XK_OK;
+}
+
+// FGMRES in FP64 on the exact operator, preconditioned by a fresh FP64 factorization (the plain FP64
+// path, and the mixed path's FP64 route): the right-hand side and residuals are row-equilibrated by
+// c->rowd, which the preconditioner undoes before applying the stored inverses.
+void enqueue_refine64(xk_ctx *c, const Col &col, Ctl *ctl, const FactorPlan &plan, const int *skip, int max_iter)
+{
+    GmArgs a;
+    a.N = (long long)c->L * c->S;
+    a.m = std::min(basis_size(c), max_iter);
+    a.max_iter = max_iter;
+    a.tol = c->cfg.gmres_tol;
+    a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
+    a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
+    a.skip_solve = skip;
+    a.role = 2;
+    a.reuse_max_iters = 0;
+    const double *rowd = c->rowd;
+    a.matvec = [col, ctl, rowd](const double *x, double *y, const int *sk, cudaStream_t s) {
+        launch_jv(col, ctl, x, y, rowd, sk, s);
+    };
+    a.precond = [c, plan, ctl, rowd](const double *v, double *z, const int *sk, cudaStream_t s) {
+        solve64(c, plan, v, z, ctl, s, rowd, sk, nullptr);
+    };
+    enqueue_fgmres(a, c->st);
 }
 
 // Enqueue thermochemistry, rates, photolysis, residual, Jacobian and the linear solve for state col.n (or n_override),
@@ -361,17 +416,29 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
     { PhaseMark m(c, XK_PH_REACTION); launch_reaction_terms(col, n, st); }
     { PhaseMark m(c, XK_PH_RESIDUAL); launch_residual(col, n, col.F, ctl, c->cfg.f_floor, st); }
     cudaError_t e;
+    const long long N = (long long)c->L * c->S;
+    const int refine = std::max(c->cfg.refine_max_iter, 0);
     if (c->cfg.precision == XK_PREC_FP64) {
-        { PhaseMark m(c, XK_PH_JACOBIAN); launch_jacobian64(col, n, ctl, dt_override, 1, c->A64, c->lo64, c->up64, st); }
+        {
+            PhaseMark m(c, XK_PH_JACOBIAN);
+            launch_jacobian64(col, n, ctl, dt_override, 1, c->A64, c->lo64, c->up64, st);
+            if (refine > 0) {
+                launch_diag(col, ctl, c->rowd, st);
+                launch_rowdiv(N, col.b, c->rowd, c->bhat, st);
+            }
+        }
         { PhaseMark m(c, XK_PH_FACTOR); e = launch_factor<double>(sys64(c), c->plan, ctl, st); }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "factor launch: %s", cudaGetErrorString(e));
-        { PhaseMark m(c, XK_PH_SOLVE); e = solve64(c, c->plan, col.b, col.x, ctl, st, nullptr, nullptr, nullptr); }
+        PhaseMark m(c, XK_PH_SOLVE);
+        if (refine > 0)
+            enqueue_refine64(c, col, ctl, c->plan, nullptr, refine);
+        else
+            e = solve64(c, c->plan, col.b, col.x, ctl, st, nullptr, nullptr, nullptr);
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     } else {
         if (dt_override > 0.0) return fail(c, XK_EINVAL, "mixed path reads dt from the control block");
         launch_route(ctl, st);
         const int *skip32 = &ctl->skip32;
-        const long long N = (long long)c->L * c->S;
         {
             PhaseMark m(c, XK_PH_JACOBIAN);
             launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, nullptr, st, skip32);
@@ -414,7 +481,8 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
             };
             { PhaseMark m(c, XK_PH_SOLVE); enqueue_fgmres(a, st); }
         }
-        // FP64 factorization and direct solve, gated on the device by ctl->skip64
+        // FP64 factorization, then FGMRES refinement around it (or a direct solve), gated on the
+        // device by ctl->skip64
         const int *skip64 = &ctl->skip64;
         {
             PhaseMark m(c, XK_PH_FALLBACK);
@@ -422,7 +490,10 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
             e = launch_factor<double>(sys64(c), c->plan64, ctl, st, skip64);
             if (e == cudaSuccess) {
                 launch_after_refactor(N, col.s, c->s64, ctl, st);
-                e = solve64(c, c->plan64, col.b, col.x, ctl, st, nullptr, skip64, nullptr);
+                if (refine > 0)
+                    enqueue_refine64(c, col, ctl, c->plan64, skip64, refine);
+                else
+                    e = solve64(c, c->plan64, col.b, col.x, ctl, st, nullptr, skip64, nullptr);
             }
         }
         if (e != cudaSuccess) return fail(c, XK_ECUDA, "FP64 fallback launch: %s", cudaGetErrorString(e));
@@ -472,6 +543,8 @@ int xk_config_init(xk_config *cfg)
     cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
     cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-15;
     cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1; cfg->reuse_max_iters = 20;
+    cfg->refine_max_iter = 10;
+    cfg->wait_polls = 0;
     return XK_OK;
 }
 
@@ -678,7 +751,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     cudaMemsetAsync(c->bar, 0, 8 * sizeof(unsigned), c->st);
     if (c->counter) cudaMemsetAsync(c->counter, 0, 8 * sizeof(unsigned), c->st);
     cudaMemsetAsync(c->col.n, 0, sizeof(double) * (size_t)c->L * c->S, c->st);
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     init.dt = 1e-8;
     init.dt_fp64 = 1e300;
     init.reuse_enabled = c->cfg.reuse_factorization;
@@ -752,13 +825,14 @@ int xk_step(xk_ctx *c, double dt, xk_step_info *info)
     h.status = 0;
     h.err_timeout = 0;
     h.err_singular = 0;
+    h.wait_polls = fresh_ctl(c).wait_polls;
     if (dt > 0.0) h.dt = dt;
     *c->ctl_host = h;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     if ((rc = enqueue_step(c))) return rc;
     if ((rc = read_ctl(c, &h))) return rc;
     fill_step_info(h, info);
-    if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (h.err_timeout) return timed_out(c);
     if (h.status) return fail(c, h.status, "step failed with status %d", h.status);
     return XK_OK;
 }
@@ -770,7 +844,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
     if (max_steps <= 0) return fail(c, XK_EINVAL, "max_steps must be positive");
     Ctl h;
     if ((rc = read_ctl(c, &h))) return rc;
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     init.dt = dt0 > 0.0 ? dt0 : h.dt;
     init.t = 0.0;
     init.dt_fp64 = h.dt_fp64;
@@ -800,7 +874,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
         info->fp64_steps = h.fp64_steps;
         info->refactors = h.refactors;
     }
-    if (h.err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (h.err_timeout) return timed_out(c);
     if (h.status) return fail(c, h.status, "run stopped with status %d", h.status);
     if (!h.converged) return fail(c, XK_ENOCONV, "no steady state after %d steps", h.steps);
     return XK_OK;
@@ -917,7 +991,7 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
     cudaMemcpy2DAsync(c->A64, c->col.ld * 8, A, S * 8, S * 8, L * S, cudaMemcpyDeviceToDevice, c->st);
     d2d(c, c->lo64, lo, L * S * 8);
     d2d(c, c->up64, up, L * S * 8);
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     cudaError_t e = launch_factor<double>(sys64(c), c->plan64, c->ctl_aux, c->st);
@@ -926,7 +1000,7 @@ int xk_block_solve(xk_ctx *c, const double *A, const double *lo, const double *u
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve"))) return rc;
-    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_timeout) return timed_out(c);
     if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
     return XK_OK;
 }
@@ -941,7 +1015,7 @@ int xk_block_solve32(xk_ctx *c, const double *A, const double *lo, const double 
     launch_convert32(A, S, c->A32, ld, L * S, S, c->st);
     launch_convert32(lo, L * S, c->lo32, L * S, 1, L * S, c->st);
     launch_convert32(up, L * S, c->up32, L * S, 1, L * S, c->st);
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     *c->ctl_host = init;
     cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
     cudaError_t e = factor32(c, c->ctl_aux, nullptr);
@@ -950,7 +1024,7 @@ int xk_block_solve32(xk_ctx *c, const double *A, const double *lo, const double 
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "solve launch: %s", cudaGetErrorString(e));
     cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
     if ((rc = finish_eval(c, "block_solve32"))) return rc;
-    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_timeout) return timed_out(c);
     if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
     return XK_OK;
 }
@@ -960,7 +1034,7 @@ int xk_step_delta(xk_ctx *c, const double *n, double dt, double *delta, int *ite
     int rc = need_ready(c);
     if (rc) return rc;
     if (!n || !delta || !(dt > 0)) return fail(c, XK_EINVAL, "bad argument");
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     init.dt = dt;
     init.dt_fp64 = 1e300;
     *c->ctl_host = init;
@@ -971,9 +1045,20 @@ int xk_step_delta(xk_ctx *c, const double *n, double dt, double *delta, int *ite
     if ((rc = finish_eval(c, "step_delta"))) return rc;
     if (iters) *iters = c->ctl_host->used_fp64 ? -1 : c->ctl_host->solver_iters;
     if (resid) *resid = c->ctl_host->solver_resid;
-    if (c->ctl_host->err_timeout) return fail(c, XK_ETIMEOUT, "a device-side wait timed out");
+    if (c->ctl_host->err_timeout) return timed_out(c);
     if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "zero pivot in a diagonal block");
     return XK_OK;
+}
+
+int xk_hold_next_barrier(xk_ctx *c)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    // arrival counts that a grid of at most 2^30 CTAs never completes, for both counter pairs
+    // (the whole grid, and the second half of a two-chain elimination)
+    const unsigned held[4] = {1u << 30, 0u, 1u << 30, 0u};
+    cudaMemcpyAsync(c->bar, held, sizeof held, cudaMemcpyHostToDevice, c->st);
+    return finish_eval(c, "hold_next_barrier");
 }
 
 long long xk_launch_count(void) { return launches(); }
@@ -1096,7 +1181,7 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
     b->used += s.bytes;
     Ctl h;
     if ((rc = read_ctl(c, &h))) return rc;
-    Ctl init{};
+    Ctl init = fresh_ctl(c);
     init.dt = dt0;
     init.dt_fp64 = 1e300;
     init.reuse_enabled = c->cfg.reuse_factorization;

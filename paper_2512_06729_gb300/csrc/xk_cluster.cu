@@ -80,7 +80,7 @@ k_factor_cluster(BlockSys<float> a, float *gU, Ctl *ctl, const int *skip, int ns
 {
     // the flags are written by earlier kernels on the stream: every CTA of the
     // cluster takes the same branch
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int me = (int)cl.block_rank();
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kSolveClusterThreads, 1)
 k_solve_cluster(BlockSys<T> a, const int *perm, const double *b, double *x, double *g, Ctl *ctl,
                 const double *bscale, const int *skip, const double *xscale, int rpc, int lds, int nbuf)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     cg::cluster_group cl = cg::this_cluster();
     const int me = (int)cl.block_rank();
     const int S = a.S, ld = a.ld, L = a.L;
@@ -461,7 +461,7 @@ k_solve_twisted(BlockSys<T> a, const int *perm, const double *b, double *x, doub
                 const double *bscale, const int *skip, const double *xscale, int rpc, int lds, int nbuf, int phase,
                 int mid)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int me = (int)cl.block_rank();

@@ -24,33 +24,44 @@ constexpr int kSolveThreads = 512;
 constexpr unsigned long long kSpinLimit = 1ull << 24;   // ~1-2 s with the sleep below
 
 // Barrier over the nblk CTAs that share the counter pair bar[0..1] (the whole grid by default).
+// The wait is bounded: after ctl->wait_polls polls (default kSpinLimit) the CTA records
+// ctl->err_timeout and every CTA leaves at its next barrier.  The decision is taken by thread 0
+// and shared through shared memory, so all threads of a CTA return the same value.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl, unsigned nblk = 0)
 {
+    __shared__ int s_go;
     if (nblk == 0) nblk = gridDim.x;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        unsigned gen = *vgen;
-        __threadfence();
-        unsigned prev = atomicAdd(bar, 1u);
-        if (prev == nblk - 1) {
-            atomicExch(bar, 0u);
+        volatile int *vto = &ctl->err_timeout;
+        int go = *vto == 0;
+        if (go) {
+            const unsigned long long limit = ctl->wait_polls ? ctl->wait_polls : kSpinLimit;
+            volatile unsigned *vgen = bar + 1;
+            unsigned gen = *vgen;
             __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > kSpinLimit) {
-                    atomicExch(&ctl->err_timeout, 1);
-                    break;
+            unsigned prev = atomicAdd(bar, 1u);
+            if (prev == nblk - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                unsigned long long spins = 0;
+                while (*vgen == gen) {
+                    if (++spins > limit || *vto) {
+                        atomicExch(&ctl->err_timeout, 1);
+                        break;
+                    }
+                    __nanosleep(64);
                 }
-                __nanosleep(64);
             }
+            __threadfence();
+            go = *vto == 0;
         }
-        __threadfence();
+        s_go = go;
     }
     __syncthreads();
-    return *(volatile int *)&ctl->err_timeout == 0;
+    return s_go != 0;
 }
 
 // Pivot search key: the magnitude's bit pattern is monotonic for |x|, so the
@@ -222,7 +233,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(kFactorThreads, 1) k_factor(BlockSys<T> a, Ctl *ctl, const int *skip, int mode,
                                                                int mid)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int S = a.S, ld = a.ld, L = a.L;
     const int half = mode == 1 ? (int)(blockIdx.x >= gridDim.x / 2) : 0;
@@ -379,7 +390,7 @@ template <int NB>
 __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_pv(BlockSys<double> a, double *lu, Ctl *ctl,
                                                                   const int *skip)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double Ds[NB * NB];
     __shared__ double Dr_rcp[NB];
@@ -506,7 +517,7 @@ template <int NB>
 __global__ void __launch_bounds__(kFactorThreads, 1) k_factor_np(BlockSys<float> a, float *gbuf, Ctl *ctl,
                                                                   const int *skip)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     constexpr int MAXC = 8;
     __shared__ float Dinv[NB * (NB + 1)];
     __shared__ float U[NB * MAXC];
@@ -639,7 +650,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_solve(BlockSys<T> a, const
                                                                   const double *bscale, const int *skip,
                                                                   const double *xscale)
 {
-    if (ctl->finished || (skip && *skip)) return;
+    if (ctl->finished || ctl->err_timeout || (skip && *skip)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     T *vec = (T *)smem;
     const int S = a.S, ld = a.ld, L = a.L;

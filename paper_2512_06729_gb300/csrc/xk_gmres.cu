@@ -238,12 +238,14 @@ __global__ void k_gm_skip_if_finished(GmState *gm, const Ctl *ctl, const int *sk
 
 // Record the solve; a solve that did not reach the tolerance hands the step to
 // the FP64 factorization, and so does every later step at this dt or above.
+// Refinement around a fresh FP64 factorization (role 2) is only recorded.
 __global__ void k_gm_report(const GmState *gm, Ctl *ctl, const int *skip_solve, int role, int reuse_max_iters)
 {
     if (ctl->finished || (skip_solve && *skip_solve)) return;
     ctl->solver_iters = gm->iters;
     ctl->solver_resid = gm->resid;
     ctl->total_iters += gm->iters;
+    if (role == 2) return;             // refinement of a fresh FP64 factorization: the best FP64 can do
     if (gm->failed || !(gm->resid <= gm->tol)) {
         ctl->skip64 = 0;               // refactor in FP64 and solve directly
         ctl->used_fp64 = 1;

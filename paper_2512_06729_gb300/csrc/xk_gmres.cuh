@@ -37,7 +37,8 @@ struct GmArgs {
     GmState *gm;
     Ctl *ctl;
     const int *skip_solve;   // this solve is skipped when *skip_solve != 0
-    int role;                // 0: FP32-preconditioned attempt, 1: attempt with the reused FP64 factorization
+    int role;                // 0: FP32-preconditioned attempt, 1: attempt with the reused FP64 factorization,
+                             // 2: refinement around a fresh FP64 factorization (recorded, no routing)
     int reuse_max_iters;     // role 1: more iterations than this trigger a fresh factorization next step
     VecOp matvec;        // y = A x (FP64); must return at once while *skip != 0
     VecOp precond;       // z ~ A^-1 v (low precision); same skip rule

@@ -56,6 +56,7 @@ struct Ctl {
     double solver_resid;
     long long total_iters;
     int err_timeout;      // a bounded wait gave up
+    unsigned long long wait_polls;   // polls before a bounded wait gives up (0: the default, about a second)
     int err_singular;     // zero pivot met
     // mixed precision routing: skip32 = this step goes straight to FP64; skip64 = FP64 solve not needed
     int skip32, skip64;

@@ -27,16 +27,26 @@ unsigned char *g_dev_ptr[kMaxDevices] = {};
 
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Whether p is device (or managed) memory that the current device dev can address.
+bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in, not a device address).
-int scratch_on_current_device(unsigned char **out)
+// A cached address that no longer belongs to the current device's context (the
+// device was reset and the library's module loaded again) is looked up anew.
+int scratch_on_current_device(int dev, unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return XK_ECUDA;
-    }
+    if (dev < 0 || dev >= kMaxDevices) return XK_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
+    if (g_dev_ptr[dev] && !on_device(g_dev_ptr[dev], dev)) g_dev_ptr[dev] = nullptr;
     if (!g_dev_ptr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -74,8 +84,16 @@ extern "C" int xk_block_solve_noalloc(int L, int S, const double *A, const doubl
 
     FactorPlan plan;
     if (factor_plan(S, 8, 0, 0, &plan) != 0) return XK_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return XK_ECUDA;
+    }
+    // every array the kernels touch must be memory of this device (a host pointer would fault)
+    if (!on_device(A, dev) || !on_device(lo, dev) || !on_device(up, dev) || !on_device(f, dev) || !on_device(x, dev))
+        return XK_EINVAL;
     unsigned char *base = nullptr;
-    int rc = scratch_on_current_device(&base);
+    int rc = scratch_on_current_device(dev, &base);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -92,9 +110,13 @@ extern "C" int xk_block_solve_noalloc(int L, int S, const double *A, const doubl
     sys.S = S;
     sys.ld = (int)ld;
     // the array keeps the previous call's contents: flags and barrier words start at zero
-    cudaMemsetAsync(base, 0, o_pinfo, st);
-    cudaMemcpy2DAsync(sys.D, ld * sizeof(double), A, (size_t)S * sizeof(double), (size_t)S * sizeof(double), LS,
-                      cudaMemcpyDeviceToDevice, st);
+    // a refused clear or copy would leave the previous call's flags or blocks in place: no launch then
+    if (cudaMemsetAsync(base, 0, o_pinfo, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(sys.D, ld * sizeof(double), A, (size_t)S * sizeof(double), (size_t)S * sizeof(double), LS,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return XK_ECUDA;
+    }
     cudaError_t e = launch_factor<double>(sys, plan, ctl, st);
     if (e == cudaSuccess) e = launch_solve<double>(sys, plan, f, x, (double *)(base + o_g), ctl, st);
     if (e != cudaSuccess) {

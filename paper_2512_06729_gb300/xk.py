@@ -36,7 +36,7 @@ class Config(C.Structure):
         ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
         ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("reuse_max_iters", C.c_int),
         ("twisted", C.c_int),
-        ("fp64_panel", C.c_int),
+        ("fp64_panel", C.c_int), ("refine_max_iter", C.c_int), ("wait_polls", C.c_longlong),
     ]
 
 
@@ -98,6 +98,7 @@ SIGNATURES = {
     "xk_batch_query": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
+    "xk_hold_next_barrier": (C.c_int, [_vp]),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
 }
 
@@ -320,6 +321,10 @@ class Column:
         self._call("xk_block_solve32", self._ptr(A.contiguous()), self._ptr(lo.contiguous()),
                    self._ptr(up.contiguous()), self._ptr(f.contiguous()), self._ptr(x))
         return x
+
+    def hold_next_barrier(self):
+        """Testing aid: the next grid barrier of the FP64 factorization never completes."""
+        self._call("xk_hold_next_barrier")
 
     def step_delta(self, n, dt):
         d = self._dev(self.L, self.S)

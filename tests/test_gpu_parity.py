@@ -24,7 +24,7 @@ torch = pytest.importorskip("torch")
 
 from oracle.oracle import Oracle, default_policy
 from paper_2512_06729_gb300 import synth
-from tests.helpers import full_matrix
+from tests.helpers import full_matrix, independent_refined_solve, relative_to_state
 
 pytestmark = pytest.mark.gpu
 
@@ -189,15 +189,15 @@ def test_fp64_factor_variants(panel, nb, twisted):
     multipliers formed on all CTAs by triangular solves (panel = 1; widths 8,
     16, 32 with ragged last panels on 40 species) and column by column on one
     CTA (panel = 0; top-down, or from both ends on the two halves of the grid
-    meeting in the middle layer, with the matching two-cluster sweeps), against
-    the oracle's LU: at moderate dt to 1e-10, and near steady state at
-    dt = 1e8 s to the kappa * eps bound of the late-state test at width 8
-    (wider panels round more there: a numpy emulation of the same elimination
-    errs by 2.6e-4 at width 16 on the 20-species column)."""
+    meeting in the middle layer, with the matching two-cluster sweeps): the
+    direct solve against the oracle's LU at moderate dt to 1e-10; and near
+    steady state at dt = 1e8 s, where the system's condition number is near
+    1e16, the FP64 path's step (FGMRES refinement around each variant's
+    factorization) against the oracle's step, every width held to the bound
+    that an independent FP64 solve of the same system sets."""
     p = synth.small_column()
     o = Oracle(p)
     c = xk.Column(p, "fp64", fp64_panel=panel, panel_width=nb, twisted=twisted)
-    ng = o.grid()[0]
     n = o.initial_state()
     rng = np.random.default_rng(4)
     f = rng.normal(size=n.shape) * n
@@ -207,12 +207,9 @@ def test_fp64_factor_variants(panel, nb, twisted):
         ox = o.block_solve(oA, olo, oup, f)
         assert np.max(np.abs(x - ox)) / (np.abs(ox).max() + 1e-300) < 1e-10, (panel, nb, dt)
     nl, _ = o.run_to_steady(n, max_steps=400)
-    oA, olo, oup = o.jacobian(nl, 1e8)
-    fl = o.residual(nl)
-    x = cpu(c.block_solve(dev(oA), dev(olo), dev(oup), dev(fl)))
-    ox = o.block_solve(oA, olo, oup, fl)
-    s = np.maximum(nl, 1e-20 * ng[:, None])
-    assert np.max(np.abs(x - ox) / s) < (1e-4 if nb == 8 else 1e-1), (panel, nb, twisted)
+    d, iters, res = c.step_delta(dev(nl), 1e8)
+    bound, errs, spread = _step_parity(o, nl, 1e8, {"fp64": cpu(d)})
+    assert errs["fp64"] <= bound, (panel, nb, twisted, errs, bound, spread, iters, res)
 
 
 def test_fp64_factor_full_size():
@@ -390,22 +387,48 @@ def test_replayed_schedule_small_column(precision):
     assert err.max() <= 1e-6, err.max(axis=0)
 
 
+def _second_trajectory(p, dts):
+    """The oracle's replayed schedule taken a second time on the CPU with the
+    linear solves done by independent_refined_solve (the oracle's residual and
+    Jacobian, a solver that shares no code with it); per step, the worst
+    relative difference from the oracle's own trajectory over species above
+    1e-12 and between 1e-20 and 1e-12 mixing ratio: how far FP64 alone lets
+    two correct trajectories drift."""
+    o = Oracle(p)
+    ng = o.grid()[0]
+    pol = default_policy(rel_reject=1e300, neg_tol=1e300)
+    n = o.initial_state()
+    m = n.copy()
+    out = []
+    for dt in dts:
+        n, _ = o.step(n, dt, pol)
+        A, lo, up = o.jacobian(m, dt)
+        F = o.residual(m)
+        s = np.maximum(m, 1e-20 * ng[:, None])
+        m = np.maximum(m + independent_refined_solve(A, lo, up, F, s), 0.0)
+        rel = np.abs(m - n) / np.maximum(n, 1e-300)
+        major = n > 1e-12 * ng[:, None]
+        trace = (n > 1e-20 * ng[:, None]) & ~major
+        out.append((float(rel[major].max()), float(rel[trace].max()) if trace.any() else 0.0))
+    return np.array(out)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_replayed_schedule_tiny_column(precision):
-    """The same on the 20-species column.  Up to dt = 1e4 s: within 1e-6 above
-    1e-12 and 1e-3 between 1e-20 and 1e-12.  Beyond that this column has
-    species relaxing on 1e13 s time scales whose values FP64 no longer pins
-    down: two FP64 CPU solvers that pivot differently (the oracle's LU and a
-    scaled Gauss-Jordan) drift apart by 5e-6 at dt = 1e6 s and by up to 2e-4
-    at dt = 1e8 s, so the rest of the run is held to 1e-3."""
+    """The same on the 20-species column, whose late steps (up to dt = 1e8 s)
+    have species relaxing on 1e13 s time scales that FP64 no longer pins
+    down.  Every step is held to 1e-6 or, where FP64 itself cannot tell two
+    correct trajectories apart that closely, to 10x the drift between the
+    oracle's trajectory and a second CPU trajectory with an independent
+    solver (largest drift so far, per class of species)."""
     p = synth.tiny_column()
     dts = _oracle_schedule(Oracle(p), Oracle(p).initial_state(), 900)
     assert dts[-1] >= 1e8
     err = _replay(p, precision, dts)
-    early = np.array([d <= 1e4 for d in dts])
-    assert err[early, 0].max() <= 1e-6, err[early].max(axis=0)
-    assert err[early, 1].max() <= 1e-3, err[early].max(axis=0)
-    assert err.max() <= 1e-3, err.max(axis=0)
+    drift = np.maximum.accumulate(_second_trajectory(p, dts), axis=0)
+    bound = np.maximum(1e-6, 10.0 * drift)
+    worst = np.argmax((err / bound).max(axis=1))
+    assert (err <= bound).all(), (worst, dts[worst], err[worst], drift[worst])
 
 
 @pytest.mark.parametrize("precision,reuse", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
@@ -473,21 +496,36 @@ def test_rate_coefficients_evaluated_once():
     assert relerr(kf, okf, 1e-300) < 1e-11 and relerr(kr, okr, 1e-300) < 1e-11
 
 
+def _step_parity(o, n, dt, deltas):
+    """Each delta in `deltas` against the oracle's step, relative to n on the
+    species above 1e-20 mixing ratio, with the bound derived here from a
+    second FP64 solve of the same system that shares no code with the oracle
+    (LAPACK block Thomas in relative variables plus refinement): FP64 itself
+    determines the step only to within the disagreement of the two, so a
+    result within 10x that of the oracle (and never held to less than 1e-9)
+    is as close as FP64 can tell.  Returns (bound, errors, reference spread)."""
+    ng = o.grid()[0]
+    od = o.step_delta(n, dt)
+    A, lo, up = o.jacobian(n, dt)
+    F = o.residual(n)
+    s = np.maximum(n, 1e-20 * ng[:, None])
+    x2 = independent_refined_solve(A, lo, up, F, s)
+    spread = relative_to_state(x2, od, n, ng)
+    bound = max(10.0 * spread, 1e-9)
+    errs = {k: relative_to_state(d, od, n, ng) for k, d in deltas.items()}
+    return bound, errs, spread
+
+
 def test_full_size_column():
     """The 594-species, 7,720-reaction, 150-layer column at the bench's launch
     configuration (library defaults: twisted FP32 inversion on 16-CTA clusters,
-    twisted FP64 inversion): rate coefficients, photolysis and the residual at
-    the initial state element by element against the oracle; Jacobian blocks
-    of three layers; and the mixed and FP64 linear steps at dt = 1e-2 s checked
-    through the oracle's own block operator, (I/dt - J) delta = F, row by row
-    relative to the magnitudes in the row plus the residual's own cancellation
-    scale (its evaluation is accurate to 1e-10 of that scale): 1e-9 for the
-    mixed step (FGMRES on the FP64 operator), 1e-7 for the FP64 direct solve
-    with explicit block inverses.  The two steps are not compared with each
-    other here: at this size the direct solve's backward error (1.4e-8
-    measured) times the system's conditioning moves its solution by up to
-    3.6e-2 of max(n, 1e-20 n_gas) from the FGMRES one, whose residual is
-    converged on the exact operator."""
+    twisted FP64 inversion, FGMRES refinement in both paths): rate
+    coefficients, photolysis and the residual at the initial state element by
+    element against the oracle; Jacobian blocks of three layers; and the
+    mixed and FP64 linear steps at dt = 1e-6 s and 1e-2 s element by element
+    against the oracle's step, relative to n on every species above 1e-20
+    mixing ratio, within the bound that a second, independent FP64 solve of
+    the same system sets (see _step_parity)."""
     p = synth.full_column()
     o = Oracle(p)
     n = o.initial_state()
@@ -501,28 +539,24 @@ def test_full_size_column():
     oF = o.residual(n)
     gross = _gross(p, o, n) + np.abs(oF) + 1e-300
     assert np.max(np.abs(F - oF) / gross) < 1e-10
-    dt = 1e-2
-    oA, olo, oup = o.jacobian(n, dt)
-    A = c.eval_jacobian(dev(n), dt)[0]
+    oA = o.jacobian(n, 1e-2)[0]
+    A = c.eval_jacobian(dev(n), 1e-2)[0]
     for k in (0, 75, 149):
         Ak = cpu(A[k])
         scale = np.abs(oA[k]).max(axis=1, keepdims=True) + 1e-300
         assert np.max(np.abs(Ak - oA[k]) / scale) < 1e-12, k
-    del A
-    deltas = {}
-    for prec in ("mixed", "fp64"):
-        col = c if prec == "mixed" else xk.Column(p, "fp64")
-        d, iters, res = col.step_delta(dev(n), dt)
-        d = cpu(d)
-        r = np.einsum("kij,kj->ki", oA, d)
-        mag = np.einsum("kij,kj->ki", np.abs(oA), np.abs(d))
-        r[1:] += olo[1:] * d[:-1]
-        mag[1:] += np.abs(olo[1:] * d[:-1])
-        r[:-1] += oup[:-1] * d[1:]
-        mag[:-1] += np.abs(oup[:-1] * d[1:])
-        rel = np.max(np.abs(r - oF) / (mag + gross))
-        # mixed: FGMRES converged on the true FP64 residual; FP64: a direct solve with explicit
-        # block inverses, whose backward error grows with the blocks' condition (1.4e-8 measured)
-        assert rel < (1e-9 if prec == "mixed" else 1e-7), (prec, rel, iters, res)
-        assert np.isfinite(d).all(), prec
-        deltas[prec] = d
+    del A, oA
+    f64 = xk.Column(p, "fp64")
+    for dt in (1e-6, 1e-2):
+        deltas, info = {}, {}
+        for prec, col in (("mixed", c), ("fp64", f64)):
+            d, iters, res = col.step_delta(dev(n), dt)
+            deltas[prec] = cpu(d)
+            info[prec] = (iters, res)
+            assert np.isfinite(deltas[prec]).all(), prec
+        bound, errs, spread = _step_parity(o, n, dt, deltas)
+        print(f"full size dt={dt:g}: errors vs oracle {errs}, independent FP64 spread {spread:.3e}, solver {info}")
+        for prec, e in errs.items():
+            assert e <= bound, (dt, prec, e, bound, spread, info[prec])
+    f64.close()
+    c.close()
