@@ -112,6 +112,10 @@ typedef struct {
                              with stored block inverses carries their backward error times the
                              system's condition number; the iterations bring the residual down to
                              gmres_tol.  0 = direct solve only */
+    int fp32_bcr;         /* mixed mode: 1 factors the FP32 preconditioner by block cyclic reduction of
+                             the layers (odd layers eliminated first, level by level) with every dense
+                             product and block inversion on the tensor cores (TF32 head/tail split,
+                             FP32 accuracy); 0 by the chain of block inversions (cluster_size etc.) */
     long long wait_polls; /* every device-side wait on other CTAs (the grid barriers of the FP64
                              factorization) gives up after this many polls, about 0.1 us each, and
                              the call returns XK_ETIMEOUT with the context still usable (0: 2^24
@@ -320,6 +324,18 @@ XK_API int xk_batch_query(xk_batch *batch, int slot, int *done);
 #define XK_NOALLOC_SCRATCH_BYTES (32u << 20)
 XK_API int xk_block_solve_noalloc(int L, int S, const double *A, const double *lo, const double *up,
                                   const double *f, double *x, void *stream);
+
+/* ---- the tensor-core contraction, callable on its own ----
+ * C = alpha A B + beta C for row-major FP32 device matrices A [M x lda],
+ * B [K x ldb], C [M x ldc], computed on the 5th-generation tensor cores with
+ * TF32 inputs split into head and tail (three products per step, at most
+ * about 3 * 2^-22 of |a||b| per product) and FP32 accumulation; the product every dense
+ * step of the mixed path's block factorization is made of.  M, N, K, lda, ldb
+ * and ldc must be multiples of 32, A and B 256-byte aligned and C 16-byte
+ * aligned (XK_EINVAL otherwise).  Runs on stream and synchronizes it; calls
+ * are serialized (a single task slot in device memory). */
+XK_API int xk_tc_gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                      float alpha, float beta, void *stream);
 
 /* ---- tracing: CUDA events around each phase of every step ----
  * Phases: XK_PH_RATES (Gibbs energies + rate coefficients), XK_PH_PHOTO,

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "xk_bcr.cuh"
 #include "xk_gmres.cuh"
 #include "xk_internal.cuh"
 
@@ -59,6 +60,8 @@ struct xk_ctx {
     bool use_cluster_solve = false;
     SolvePlan splan64{};   // sweeps with the pivoted FP64 inverses on one cluster
     bool use_cluster_solve64 = false;
+    BcrPlan bcr;           // block cyclic reduction on the tensor cores (mixed path, fp32_bcr)
+    bool use_bcr = false;
     bool ready = false;
     // tracing
     bool prof = false;
@@ -261,6 +264,33 @@ size_t layout(xk_ctx *c, char *base)
     c->gm = b.take<GmState>(1);
     if (c->cfg.precision == XK_PREC_FP64) {
         c->A32 = nullptr; c->lo32 = nullptr; c->up32 = nullptr;
+    } else if (c->cfg.fp32_bcr) {
+        // FP32 blocks padded to Sp x Sp per layer (identity in the padding), and the reduction's arrays
+        const BcrSizes z = bcr_sizes(L, S);
+        BcrPlan &q = c->bcr;
+        c->A32 = b.take<float>(z.floats_D);
+        c->lo32 = b.take<float>(LS);
+        c->up32 = b.take<float>(LS);
+        q.D = c->A32; q.lo = c->lo32; q.up = c->up32;
+        q.INV = b.take<float>(z.floats_INV);
+        q.TMP = b.take<float>(z.floats_TMP);
+        q.CP = b.take<float>(z.floats_CP);
+        q.PQ = b.take<float>(z.floats_PQ);
+        q.bw = b.take<float>(z.floats_vec);
+        q.tw = b.take<float>(z.floats_vec);
+        q.xw = b.take<float>(z.floats_vec);
+        q.gemm_d = b.take<TcTask>(std::max(z.ngemm, 1));
+        q.leaf_d = b.take<BcrLeaf>(std::max(z.nleaf, 1));
+        q.mv_d = b.take<BcrMv>(std::max(z.nmv, 1));
+        q.maps_d = b.take<CUtensorMap>(10);
+        q.l0_d = b.take<int>(L);
+        q.sol_d = b.take<BcrStage>(std::max(z.nsol, 1));
+        c->gbuf = nullptr;
+        c->s64 = b.take<double>(LS);
+        c->pin = b.take<double>(LS);
+        c->pout = b.take<double>(LS);
+        c->ridx32 = b.take<int>(LS);
+        c->sig32 = b.take<int>(LS);
     } else {
         c->A32 = b.take<float>((size_t)L * S * ld);
         c->lo32 = b.take<float>(LS);
@@ -278,6 +308,7 @@ size_t layout(xk_ctx *c, char *base)
     c->dinv = b.take<double>(32 * 32);
     c->ymid = b.take<double>(2 * (size_t)S);
     c->bar = b.take<unsigned>(8);
+    c->bcr.bar = c->bar ? c->bar + 4 : nullptr;      // words 4-5: the reduction's solve
     c->ctl = b.take<Ctl>(1);
     c->ctl_aux = b.take<Ctl>(1);
     return b.off + 256;
@@ -308,6 +339,7 @@ BlockSys<float> sys32(xk_ctx *c)
 // FP32 block inversions of the mixed path
 cudaError_t factor32(xk_ctx *c, Ctl *ctl, const int *skip)
 {
+    if (c->use_bcr) return bcr_factor(c->bcr, skip, ctl, c->st);
     if (c->cfg.fp32_pivoting) return launch_factor<float>(sys32(c), c->plan, ctl, c->st, skip);
     if (c->use_cluster) return launch_factor_cluster(sys32(c), c->cplan, c->gbuf, ctl, c->st, skip);
     return launch_factor_nopivot(sys32(c), c->plan, c->gbuf, ctl, c->st, skip);
@@ -317,6 +349,7 @@ cudaError_t factor32(xk_ctx *c, Ctl *ctl, const int *skip)
 cudaError_t solve32(xk_ctx *c, const double *b, double *x, Ctl *ctl, cudaStream_t st, const double *bscale,
                     const int *skip)
 {
+    if (c->use_bcr) return bcr_solve(c->bcr, b, x, bscale, nullptr, skip, ctl, st);
     if (c->use_cluster_solve && c->use_cluster && cluster_twisted(c->cplan, c->L) && c->splan.twisted)
         return launch_solve_twisted<float>(sys32(c), c->splan, false, b, x, c->gsol, c->ymid, ctl, st, bscale, skip);
     if (c->use_cluster_solve && !(c->use_cluster && cluster_twisted(c->cplan, c->L)))
@@ -441,7 +474,8 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         const int *skip32 = &ctl->skip32;
         {
             PhaseMark m(c, XK_PH_JACOBIAN);
-            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, nullptr, st, skip32);
+            launch_jacobian32(col, n, ctl, c->A32, c->lo32, c->up32, nullptr, st, skip32,
+                              c->use_bcr ? (long long)c->bcr.Sp * c->bcr.Sp : 0);
             // equations divided by their diagonal: residuals in units of relative change per species
             launch_diag(col, ctl, c->rowd, st);
             launch_rowdiv(N, col.b, c->rowd, c->bhat, st);
@@ -723,10 +757,17 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
         return fail(c, XK_EINVAL, "no FP64 factorization plan for S=%d", c->S);
     c->use_cluster = false;
     c->use_cluster_solve = false;
+    c->use_bcr = sz == 4 && c->cfg.fp32_bcr;
     c->use_cluster_solve64 = c->cfg.cluster_size >= 0 && solve_cluster_plan(c->S, 8, &c->splan64) == 0;
     set_preview(c, &c->plan64);
     if (sz == 8) set_preview(c, &c->plan);
-    if (sz == 4 && !c->cfg.fp32_pivoting && c->cfg.cluster_size >= 0) {
+    if (c->use_bcr) {
+        if (bcr_build(c->bcr, c->L, c->S, c->st) != 0)
+            return fail(c, XK_ECUDA, "block cyclic reduction plan: %s", cudaGetErrorString(cudaGetLastError()));
+        // padded blocks: zero, then the identity in the padding rows (callers may fill only S x S)
+        cudaMemsetAsync(c->A32, 0, sizeof(float) * (size_t)c->L * c->bcr.Sp * c->bcr.Sp, c->st);
+        bcr_init_pad(c->bcr, c->st);
+    } else if (sz == 4 && !c->cfg.fp32_pivoting && c->cfg.cluster_size >= 0) {
         const int nbc = c->cfg.panel_width == 16 ? 16 : 8;
         // the panel rows go through gbuf (4 x S x 32 floats, enough for 4 x 16 x round_up(S, 4))
         if (cluster_plan(c->S, nbc, c->cfg.cluster_size, &c->cplan) == 0 &&
@@ -1012,7 +1053,12 @@ int xk_block_solve32(xk_ctx *c, const double *A, const double *lo, const double 
     if (c->cfg.precision != XK_PREC_MIXED) return fail(c, XK_EINVAL, "xk_block_solve32 needs a mixed-precision context");
     if (!A || !lo || !up || !f || !x) return fail(c, XK_EINVAL, "null pointer");
     const size_t S = c->S, L = c->L, ld = c->col.ld;
-    launch_convert32(A, S, c->A32, ld, L * S, S, c->st);
+    if (c->use_bcr) {
+        const size_t Sp = c->bcr.Sp;
+        for (size_t k = 0; k < L; ++k) launch_convert32(A + k * S * S, S, c->A32 + k * Sp * Sp, Sp, S, S, c->st);
+    } else {
+        launch_convert32(A, S, c->A32, ld, L * S, S, c->st);
+    }
     launch_convert32(lo, L * S, c->lo32, L * S, 1, L * S, c->st);
     launch_convert32(up, L * S, c->up32, L * S, 1, L * S, c->st);
     Ctl init = fresh_ctl(c);

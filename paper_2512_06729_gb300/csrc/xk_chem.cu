@@ -284,7 +284,7 @@ __global__ void k_residual(Col c, const double *n, double *F, const Ctl *ctl, do
 // diag(1/s) A diag(s) and the matching couplings.
 template <typename T>
 __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_override, int scaled,
-                           T *A, T *lo, T *up, double *dout, const int *skip)
+                           T *A, T *lo, T *up, double *dout, const int *skip, long long lstride)
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
     extern __shared__ double sh[];
@@ -336,7 +336,7 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
         up[row] = (T)upv;
     }
     __syncwarp();
-    T *Ar = A + ((long long)k * S + i) * c.ld;
+    T *Ar = A + (long long)k * (lstride > 0 ? lstride : (long long)S * c.ld) + (long long)i * c.ld;
     if (scaled) {
         double inv = 1.0 / sk[i];
         for (int j = lane; j < S; j += 32) Ar[j] = (T)(rowbuf[j] * sk[j] * inv);
@@ -631,16 +631,16 @@ void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr, skip); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr, skip, 0); }
 }
 
 void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
-                       cudaStream_t st, const int *skip)
+                       cudaStream_t st, const int *skip, long long lstride)
 {
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag, skip); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag, skip, lstride); }
 }
 
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,

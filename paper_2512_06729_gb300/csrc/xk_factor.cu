@@ -21,48 +21,6 @@ namespace {
 
 constexpr int kFactorThreads = 512;
 constexpr int kSolveThreads = 512;
-constexpr unsigned long long kSpinLimit = 1ull << 24;   // ~1-2 s with the sleep below
-
-// Barrier over the nblk CTAs that share the counter pair bar[0..1] (the whole grid by default).
-// The wait is bounded: after ctl->wait_polls polls (default kSpinLimit) the CTA records
-// ctl->err_timeout and every CTA leaves at its next barrier.  The decision is taken by thread 0
-// and shared through shared memory, so all threads of a CTA return the same value.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl, unsigned nblk = 0)
-{
-    __shared__ int s_go;
-    if (nblk == 0) nblk = gridDim.x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile int *vto = &ctl->err_timeout;
-        int go = *vto == 0;
-        if (go) {
-            const unsigned long long limit = ctl->wait_polls ? ctl->wait_polls : kSpinLimit;
-            volatile unsigned *vgen = bar + 1;
-            unsigned gen = *vgen;
-            __threadfence();
-            unsigned prev = atomicAdd(bar, 1u);
-            if (prev == nblk - 1) {
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            } else {
-                unsigned long long spins = 0;
-                while (*vgen == gen) {
-                    if (++spins > limit || *vto) {
-                        atomicExch(&ctl->err_timeout, 1);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __threadfence();
-            go = *vto == 0;
-        }
-        s_go = go;
-    }
-    __syncthreads();
-    return s_go != 0;
-}
 
 // Pivot search key: the magnitude's bit pattern is monotonic for |x|, so the
 // comparison runs on the integer pipes (FP64 compares are slow on this part).

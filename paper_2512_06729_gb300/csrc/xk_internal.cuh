@@ -73,6 +73,49 @@ struct Policy {
     double dt_max, rel_reject, rel_target, grow_max, shrink_min, neg_tol, f_floor, dt_min, ss_dt, ss_tol;
 };
 
+constexpr unsigned long long kSpinLimit = 1ull << 24;   // polls of a bounded wait: ~1-2 s with the sleep below
+
+// Barrier over the nblk CTAs that share the counter pair bar[0..1] (the whole grid by default).
+// The wait is bounded: after ctl->wait_polls polls (default kSpinLimit) the CTA records
+// ctl->err_timeout and every CTA leaves at its next barrier.  The decision is taken by thread 0
+// and shared through shared memory, so all threads of a CTA return the same value.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl, unsigned nblk = 0)
+{
+    __shared__ int s_go;
+    if (nblk == 0) nblk = gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int *vto = &ctl->err_timeout;
+        int go = *vto == 0;
+        if (go) {
+            const unsigned long long limit = ctl->wait_polls ? ctl->wait_polls : kSpinLimit;
+            volatile unsigned *vgen = bar + 1;
+            unsigned gen = *vgen;
+            __threadfence();
+            unsigned prev = atomicAdd(bar, 1u);
+            if (prev == nblk - 1) {
+                atomicExch(bar, 0u);
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                unsigned long long spins = 0;
+                while (*vgen == gen) {
+                    if (++spins > limit || *vto) {
+                        atomicExch(&ctl->err_timeout, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            go = *vto == 0;
+        }
+        s_go = go;
+    }
+    __syncthreads();
+    return s_go != 0;
+}
+
 // Launch helpers implemented in xk_chem.cu
 void launch_grid(const Col &c, cudaStream_t st);
 void launch_thermo(const Col &c, cudaStream_t st);
@@ -82,8 +125,9 @@ void launch_reaction_terms(const Col &c, const double *n, cudaStream_t st);
 void launch_residual(const Col &c, const double *n, double *F, const Ctl *ctl, double f_floor, cudaStream_t st);
 void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_override, int scaled,
                        double *A, double *lo, double *up, cudaStream_t st, const int *skip = nullptr);
+// lstride: elements between consecutive layers' blocks (0: S * ld)
 void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
-                       cudaStream_t st, const int *skip = nullptr);
+                       cudaStream_t st, const int *skip = nullptr, long long lstride = 0);
 void launch_route(Ctl *ctl, cudaStream_t st);
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
                cudaStream_t st);

@@ -36,7 +36,8 @@ class Config(C.Structure):
         ("panel_width", C.c_int), ("factor_ctas", C.c_int), ("fp32_pivoting", C.c_int),
         ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("reuse_max_iters", C.c_int),
         ("twisted", C.c_int),
-        ("fp64_panel", C.c_int), ("refine_max_iter", C.c_int), ("wait_polls", C.c_longlong),
+        ("fp64_panel", C.c_int), ("refine_max_iter", C.c_int), ("fp32_bcr", C.c_int),
+        ("wait_polls", C.c_longlong),
     ]
 
 
@@ -99,6 +100,8 @@ SIGNATURES = {
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_hold_next_barrier": (C.c_int, [_vp]),
+    "xk_tc_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_float, C.c_float,
+                             _vp]),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
 }
 
@@ -135,6 +138,21 @@ def default_config(**kw):
 
 def _np(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
+
+
+def tc_gemm(A, B, C=None, alpha=1.0, beta=0.0):
+    """C = alpha A B + beta C on the tensor cores (FP32 torch tensors on the device, sizes multiples of 32)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    stream = torch.cuda.current_stream(A.device).cuda_stream
+    rc = lib().xk_tc_gemm(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(),
+                          B.stride(0), C.data_ptr(), C.stride(0), float(alpha), float(beta), stream)
+    if rc != XK_OK:
+        raise XkError("xk_tc_gemm", rc, "bad sizes, alignment or a CUDA error")
+    return C
 
 
 class Column:
