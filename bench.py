@@ -52,12 +52,41 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def _alu_peaks(peaks):
-    """Peaks of the SIMT pipes the block inversion runs on, derived from the
-    measured bf16 tensor peak and NVIDIA's nominal ratios for GB300
-    (bf16 dense 2.25 PF; FP64 1.25 TF; FP32 SIMT 152 SMs x 128 lanes x 2 x 2.07 GHz)."""
+def _derived_peaks(peaks, kind):
+    """Peaks of the other pipes from the bf16 tensor peak and NVIDIA's nominal GB300 ratios
+    (dense bf16 2.25 PF, TF32 1.1 PF, FP64 1.25 TF; FP32 SIMT 152 SMs x 128 lanes x 2 x 2.07 GHz)."""
     scale = peaks["bf16_tflops"] / 2250.0
-    return {"f64": 1.25 * scale, "f32": 152 * 128 * 2 * 2.07e9 / 1e12 * scale}
+    return {"tf32": 1100.0 * scale, "f64": 1.25 * scale, "f32": 152 * 128 * 2 * 2.07e9 / 1e12 * scale,
+            "kind": f"{kind} bf16 x nominal ratio"}
+
+
+def live_peaks():
+    """Matrix-product throughput of this GPU measured now with torch.matmul (CUDA events, best of 5):
+    FP64, FP32 with TF32 tensor cores, FP32 without (SIMT).  Seconds of work in total."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, N, tf32 in (("f64", torch.float64, 4096, False), ("tf32", torch.float32, 8192, True),
+                              ("f32", torch.float32, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(N, N, device="cuda", dtype=dt)
+        b = torch.randn(N, N, device="cuda", dtype=dt)
+        c = torch.empty(N, N, device="cuda", dtype=dt)
+        best = None
+        for i in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                t = e0.elapsed_time(e1) / 1e3
+                best = t if best is None else min(best, t)
+        out[name] = 2.0 * N ** 3 / best / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
 
 
 class ClockSampler:
@@ -154,13 +183,16 @@ def replica_seed(rank):
     return 2 + rank
 
 
+def _sample_column(prob, layers):
+    return prob.replace(P_bar=prob.P_bar[:layers].copy(), T=prob.T[:layers].copy(),
+                        Kzz=prob.Kzz[:layers].copy(), f0=prob.f0[:layers].copy())
+
+
 def oracle_sample_step_time(prob, layers=SAMPLE_LAYERS, steps=1):
     """CPU oracle, single thread: seconds per implicit step on `layers` layers
     of the column (same network, same profile slice), steps repeated."""
     from oracle.oracle import Oracle
-    sub = prob.replace(P_bar=prob.P_bar[:layers].copy(), T=prob.T[:layers].copy(),
-                       Kzz=prob.Kzz[:layers].copy(), f0=prob.f0[:layers].copy())
-    o = Oracle(sub)
+    o = Oracle(_sample_column(prob, layers))
     n = o.initial_state()
     times = []
     for _ in range(steps):
@@ -168,6 +200,37 @@ def oracle_sample_step_time(prob, layers=SAMPLE_LAYERS, steps=1):
         o.step_delta(n, 1e-2)
         times.append(time.perf_counter() - t0)
     return times
+
+
+def _oracle_worker(args):
+    seed, layers, lo = args
+    from oracle.oracle import Oracle
+    from paper_2512_06729_gb300 import synth
+    prob = synth.full_column(seed=seed)
+    sub = prob.replace(P_bar=prob.P_bar[lo:lo + layers].copy(), T=prob.T[lo:lo + layers].copy(),
+                       Kzz=prob.Kzz[lo:lo + layers].copy(), f0=prob.f0[lo:lo + layers].copy())
+    o = Oracle(sub)
+    n = o.initial_state()
+    t0 = time.perf_counter()
+    o.step_delta(n, 1e-2)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(L, layers=SAMPLE_LAYERS, seed=2):
+    """The oracle on every host core at once (spawned processes, each one step on its own
+    `layers`-layer slice of the column): full-column steps/s of the whole host, and the cores."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [(seed, layers, (i * layers) % max(L - layers, 1)) for i in range(cores)]
+    # spawned (not forked) workers: the parent holds a CUDA context; a dead worker raises instead of hanging
+    with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as pool:
+        list(pool.map(_oracle_worker, jobs, timeout=600))       # interpreter and library start-up, untimed
+        t0 = time.perf_counter()
+        list(pool.map(_oracle_worker, jobs, timeout=600))
+        wall = time.perf_counter() - t0
+    # cores x layers layer-steps in `wall` seconds; a full step is L layer-steps
+    return cores * layers / L / wall, cores, wall
 
 
 def run_reference(args):
@@ -216,6 +279,72 @@ def time_steps(col, K, stream, prof=True):
     return ms, info, phases, launches
 
 
+def err_vs_oracle(prob, tuning, dt=1e-8):
+    """Element-wise error of the mixed and FP64 steps against the oracle's step on the bench's
+    first step (initial state, dt0), relative to n on every species above 1e-20 mixing ratio."""
+    import numpy as np
+    import torch
+    from oracle.oracle import Oracle
+    from paper_2512_06729_gb300 import xk
+    o = Oracle(prob)
+    n = o.initial_state()
+    ng = o.grid()[0]
+    keep = n > 1e-20 * ng[:, None]
+    t0 = time.perf_counter()
+    od = o.step_delta(n, dt)
+    oracle_s = time.perf_counter() - t0
+    out = {"dt": dt, "oracle_step_s": round(oracle_s, 2), "entries": int(keep.sum())}
+    for prec in ("mixed", "fp64"):
+        col = xk.Column(prob, prec, **tuning.get(prec, {}))
+        d, iters, _ = col.step_delta(torch.as_tensor(n, device="cuda"), dt)
+        rel = np.abs(d.cpu().numpy() - od)[keep] / n[keep]
+        out[prec] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
+                     "median": float(np.median(rel)), "within_1e-6": float((rel <= 1e-6).mean()),
+                     "solver_iters": int(iters)}
+        col.close()
+        del col
+        torch.cuda.empty_cache()
+    return out
+
+
+def steady_runs(prob, tuning, caps):
+    """Time to steady state from the initial state (dt0 1e-8 s) for each path, in chunks of 50
+    steps, each path stopped at its time cap (then reported as not converged, with how far it got)."""
+    import torch
+    from paper_2512_06729_gb300 import xk
+    out = {}
+    for prec, cap in caps.items():
+        kw = dict(tuning.get(prec, {}))
+        if prec == "mixed":
+            kw["reuse_factorization"] = 1
+        col = xk.Column(prob, prec, **kw)
+        col.set_mixing_ratios(prob.f0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps = fp64_steps = refactors = iters = 0
+        t_model = 0.0
+        info = None
+        while time.perf_counter() - t0 < cap:
+            info = col.run_to_steady(1e-8 if steps == 0 else 0.0, 50)
+            steps += int(info.steps)
+            fp64_steps += int(info.fp64_steps)
+            refactors += int(info.refactors)
+            iters += int(info.solver_iters)
+            t_model += float(info.t)
+            if info.converged or info.steps == 0:
+                break
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[prec] = {"s": round(wall, 2), "converged": bool(info and info.converged), "steps": steps,
+                     "steps_per_s": round(steps / wall, 2), "fp64_route_steps": fp64_steps,
+                     "fp64_refactors": refactors, "fgmres_iters": iters, "t_model_s": t_model,
+                     "dt_last": float(info.dt) if info else None, "time_cap_s": cap}
+        col.close()
+        del col
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -233,7 +362,8 @@ def run_ours(args):
     prob = synth.full_column(seed=replica_seed(rank))
     stream = torch.cuda.current_stream(dev)
     peaks, peak_kind = _peaks()
-    alu = _alu_peaks(peaks)
+    derived = _derived_peaks(peaks, peak_kind)
+    live = live_peaks()
 
     from paper_2512_06729_gb300 import autotune
     results = {}
@@ -247,6 +377,7 @@ def run_ours(args):
         if not tuning[prec]:
             tuning[prec], table = autotune.tune(prob, prec)
             tables[prec] = [[params, round(ms, 4)] for ms, params in table]
+    clocks = None
     for prec in ("mixed", "fp64"):
         col = xk.Column(prob, prec, device=local, **tuning[prec])
         col.set_mixing_ratios(prob.f0)
@@ -265,11 +396,12 @@ def run_ours(args):
         _barrier(ws)
         steps_done = max(int(info.steps), 1)
         t = tuning[prec]
-        col_cfg = {"cluster": t.get("cluster_size", 16), "nb": t.get("panel_width", 8) or 8,
-                   "twisted": t.get("twisted", 1), "ctas": t.get("factor_ctas", 152) or 152,
-                   "panel": t.get("fp64_panel", 0)}
+        col_cfg = {"bcr": t.get("fp32_bcr", 1) if prec == "mixed" else 0, "cluster": t.get("cluster_size", 16),
+                   "nb": t.get("panel_width", 8) or 8, "twisted": t.get("twisted", 1),
+                   "ctas": t.get("factor_ctas", 152) or 152, "panel": t.get("fp64_panel", 0)}
+        work = col.factor_work() if (prec == "mixed" and col_cfg["bcr"]) else None
         results[prec] = dict(ms=ms, steps=steps_done, phases=phases, launches=launches, info=info,
-                             col=col if prec == "mixed" else None, col_cfg=col_cfg)
+                             col=col if prec == "mixed" else None, col_cfg=col_cfg, work=work)
         if prec == "fp64":
             del col
             torch.cuda.empty_cache()
@@ -279,31 +411,64 @@ def run_ours(args):
     S, L = prob.S, prob.L
     value, ms_step = whole_job_rate(mixed["ms"] / mixed["steps"], ws, dev)
     fp64_value, fp64_ms_step = whole_job_rate(fp64["ms"] / fp64["steps"], ws, dev)
+    a7_flops = 8.0 / 3.0 * S ** 3 * L            # LU + Schur work of block Thomas per step (the survey's count)
 
-    def roofline(res, dtype):
+    def per_launch(ph, name):
+        ms_, calls = ph.get(name, (0.0, 0))
+        return ms_ / max(calls, 1), calls
+
+    def rooflines(res):
+        """Per-kernel rooflines of the mixed step's FP32 factorization and the FP64 one."""
         ph = res["phases"]
-        fac_ms, fac_calls = ph["factor"]          # mixed mode: the FP32 inversion only (FP64 is "fallback")
-        flops = 2.0 * S ** 3 * L + 3.0 * S * S * (L - 1)      # Gauss-Jordan inversions + Schur updates
-        avg_s = fac_ms / max(fac_calls, 1) * 1e-3
+        steps = res["steps"]
+        out = {}
+        if res["work"]:
+            mma, leaf = res["work"]
+            tc_ms, tc_calls = ph["tc"]
+            lf_ms, lf_calls = ph["leaf"]
+            nfac = max(ph["factor"][1], 1)            # factorizations timed
+            tc_s = tc_ms / nfac * 1e-3
+            lf_s = lf_ms / nfac * 1e-3
+            ach = 3.0 * mma / tc_s / 1e12            # the tensor pipe executes head x head, head x tail, tail x head
+            out["tc"] = {"kernel": "k_tc_gemm (tcgen05 kind::tf32, head/tail split)", "bound": "tensor",
+                         "achieved": ach, "peak": derived["tf32"], "unit": "TFLOP/s", "frac": ach / derived["tf32"],
+                         "peak_kind": derived["kind"] + " (tf32 1.1 / bf16 2.25)",
+                         "peak_live_tf32_matmul": live["tf32"], "frac_of_live": ach / live["tf32"],
+                         "useful_tflops": mma / tc_s / 1e12, "flops_per_factorization": mma,
+                         "ms_per_factorization": tc_s * 1e3, "launches_per_factorization": tc_calls / nfac,
+                         "ms_per_step": tc_ms / steps, "traffic": None}
+            ach = leaf / lf_s / 1e12
+            out["leaf"] = {"kernel": "k_leaf_inverse (FP32 Gauss-Jordan, partial pivoting, one CTA per block)",
+                           "bound": "alu", "achieved": ach, "peak": derived["f32"], "unit": "TFLOP/s",
+                           "frac": ach / derived["f32"], "peak_kind": derived["kind"],
+                           "peak_live_f32_matmul": live["f32"], "flops_per_factorization": leaf,
+                           "ms_per_factorization": lf_s * 1e3, "launches_per_factorization": lf_calls / nfac,
+                           "ms_per_step": lf_ms / steps, "traffic": None}
+        fac_ms, fac_calls = per_launch(ph, "factor")
+        out["a7"] = {"flops_per_factorization": a7_flops, "ms_per_factorization": fac_ms,
+                     "tflops": a7_flops / (fac_ms * 1e-3) / 1e12,
+                     "note": "8/3 S^3 L (block Thomas LU + Schur) over the whole FP32 factorization phase"}
+        return out
+
+    def roofline_fp64(res):
+        ph = res["phases"]
+        fac_ms, fac_calls = per_launch(ph, "factor")
+        avg_s = fac_ms * 1e-3
+        flops = 2.0 * S ** 3 * L + 3.0 * S * S * (L - 1)     # Gauss-Jordan inversions + Schur updates
         achieved = flops / avg_s / 1e12
-        peak = alu[dtype]
         cfg = res["col_cfg"]
-        if dtype == "f32":
-            twisted = int(cfg["twisted"] and cfg["cluster"] > 0 and L >= 3)
-            key = ("mixed", cfg["cluster"], cfg["nb"], twisted)
-            name = (f"k_factor_cluster<{cfg['nb']}> ({cfg['cluster']}-CTA clusters"
-                    + (", two-chain launch + middle-layer launch per factorization)" if twisted else ")"))
-        else:
-            twisted = int(cfg["twisted"] and not cfg["panel"] and L >= 3)
-            key = ("fp64", cfg["ctas"], cfg["nb"], cfg["panel"], twisted)
-            name = f"k_factor<double, {cfg['nb']}>" if not cfg["panel"] else f"k_factor_pv<{cfg['nb']}>"
-            if twisted:
-                name += " (two grid halves, then the middle layer on the whole grid)"
+        twisted = int(cfg["twisted"] and not cfg["panel"] and L >= 3)
+        key = ("fp64", cfg["ctas"], cfg["nb"], cfg["panel"], twisted)
         traffic, source = PROFILED_TRAFFIC.get(key, (None, None))
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": source,
-                "peak_kind": f"derived from {peak_kind} bf16 x nominal ratio",
-                "flops_per_factorization": flops, "ms_per_factorization": avg_s * 1e3}
+        return {"kernel": f"k_factor<double, {cfg['nb']}>" + (" (two grid halves, then the middle layer)" if twisted else ""),
+                "bound": "alu", "achieved": achieved, "peak": live["f64"], "unit": "TFLOP/s",
+                "frac": achieved / live["f64"], "peak_kind": "FP64 matmul measured live (torch.matmul float64)",
+                "peak_derived": derived["f64"], "flops_per_factorization": flops,
+                "a7_survey_tflops": a7_flops / avg_s / 1e12, "ms_per_factorization": avg_s * 1e3,
+                "traffic": traffic, "traffic_source": source}
+
+    roof = rooflines(mixed)
+    dom = max((k for k in ("tc", "leaf") if k in roof), key=lambda k: roof[k]["ms_per_step"], default=None)
 
     # end to end through the C-ABI with host buffers: the state from pinned host memory in, one step,
     # the state back into pinned host memory, every step
@@ -320,33 +485,50 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / Ke
     e2e_s = _max_over_ranks(e2e_s, ws, dev)
+    col.close()
+    del col
+    mixed["col"] = None
+    torch.cuda.empty_cache()
 
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        t = oracle_sample_step_time(prob, SAMPLE_LAYERS, 1)[0]
-        cpu = {"value": 1.0 / (t * L / SAMPLE_LAYERS), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one implicit step on {SAMPLE_LAYERS} of the {L} layers ({t:.1f} s), "
-                         f"scaled by {L}/{SAMPLE_LAYERS}"}
-
+    cpu = errs = steady = None
+    if rank == 0 and ws == 1:
+        if not args.no_cpu:
+            t = oracle_sample_step_time(prob, SAMPLE_LAYERS, 1)[0]
+            rate, cores, wall = oracle_all_cores(L)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"one implicit step on a {SAMPLE_LAYERS}-layer slice of the {L}-layer column per "
+                             f"process, {cores} processes at once ({wall:.1f} s), as full-column steps/s",
+                   "single_core": {"value": 1.0 / (t * L / SAMPLE_LAYERS), "cores": 1,
+                                   "sample": f"one step on {SAMPLE_LAYERS} of {L} layers ({t:.1f} s), "
+                                             f"scaled by {L}/{SAMPLE_LAYERS}"}}
+            errs = err_vs_oracle(prob, tuning)
+        if not args.no_steady:
+            steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
     if rank == 0:
-        ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items()}
-        ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items()}
+        ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items() if v[1]}
+        ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items() if v[1]}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": mixed["steps"],
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "species": S, "reactions": prob.R, "layers": L,
-                       "precision": "mixed: FP32 block inversions, FP64 FGMRES on the FP64 operator",
-                       "l2": "inputs larger than L2: FP32 blocks 217 MB per step (FP64 433 MB)",
+                       "precision": "mixed: FP32 factorization (tensor-core block cyclic reduction), "
+                                    "FP64 FGMRES on the FP64 operator",
+                       "l2": "inputs larger than L2: FP32 blocks 222 MB per step (FP64 433 MB)",
                        "start": "initial state, dt0 1e-8 s, adaptive dt", "parallelism": f"replicas x{ws}",
                        "factorization": tuning, "tuning_ms_per_layer": tables},
             "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms_step,
                      "steps": fp64["steps"], "speedup_mixed_over_fp64": fp64_ms_step / ms_step},
-            "roofline": roofline(mixed, "f32"),
-            "roofline_fp64": roofline(fp64, "f64"),
+            "roofline": roof.get(dom) if dom else roof["a7"],
+            "rooflines": roof,
+            "roofline_fp64": roofline_fp64(fp64),
+            "peaks": {"measured_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+                      "derived": derived, "live_matmul_tflops": live},
             "phases_ms": ph, "phases_ms_fp64": ph64,
             "solver_iters_per_step": mixed["info"].solver_iters / mixed["steps"],
             "fp64_fallback_steps": int(mixed["info"].fp64_steps),
+            "err_vs_oracle": errs,
+            "steady": steady,
             "cpu_baseline": cpu,
             "e2e": {"value": ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": L * S * 8,
                     "d2h_bytes_per_step": L * S * 8},
@@ -572,7 +754,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle legs (baseline, error vs oracle)")
+    ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady-state runs")
+    ap.add_argument("--steady-cap", type=float, default=300.0, help="seconds allowed to the mixed run to steady state")
+    ap.add_argument("--steady-cap-fp64", type=float, default=120.0,
+                    help="seconds allowed to the plain FP64 run to steady state")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels"],

@@ -115,7 +115,8 @@ typedef struct {
     int fp32_bcr;         /* mixed mode: 1 factors the FP32 preconditioner by block cyclic reduction of
                              the layers (odd layers eliminated first, level by level) with every dense
                              product and block inversion on the tensor cores (TF32 head/tail split,
-                             FP32 accuracy); 0 by the chain of block inversions (cluster_size etc.) */
+                             FP32 accuracy; the default); 0 by the chain of block inversions
+                             (cluster_size, panel_width, twisted, fp32_pivoting then apply) */
     long long wait_polls; /* every device-side wait on other CTAs (the grid barriers of the FP64
                              factorization) gives up after this many polls, about 0.1 us each, and
                              the call returns XK_ETIMEOUT with the context still usable (0: 2^24
@@ -146,7 +147,8 @@ XK_API int xk_version(void);
 /* Fill cfg with the default policy: FP64, dt_max 1e8 s, rel_reject 1.0,
  * rel_target 0.5, grow 3, shrink 0.5, neg_tol 1e-12, f_floor 1e-20,
  * dt_min 1e-20, ss_dt 1e8, ss_tol 1e-3, FGMRES(30), 40 iterations, tolerance
- * 1e-15, 10 refinement iterations around FP64 factorizations. */
+ * 1e-15, 10 refinement iterations around FP64 factorizations, the FP32
+ * factorization by block cyclic reduction on the tensor cores. */
 XK_API int xk_config_init(xk_config *cfg);
 
 /* Create a context for one atmospheric column on cfg->device.  *out is set
@@ -343,7 +345,9 @@ XK_API int xk_tc_gemm(int M, int N, int K, const float *A, int lda, const float 
  * XK_PH_FACTOR (block inversions), XK_PH_SOLVE (block sweeps, or FGMRES with
  * its sweeps in mixed mode), XK_PH_CONTROL (accept/reject/update),
  * XK_PH_FALLBACK (mixed mode only: the FP64 Jacobian, factorization and
- * solve, whose kernels exit at once on steps that FGMRES solved).
+ * solve, whose kernels exit at once on steps that FGMRES solved), and within
+ * the block cyclic reduction (fp32_bcr) XK_PH_TC and XK_PH_LEAF around every
+ * launch of its tensor-core products and of its leaf inversions.
  * xk_profile(ctx, 1) starts recording (and clears totals); 0 stops.
  * xk_profile_read fills ms[n] with the summed device time of each phase and
  * calls[n] with the number of timed occurrences, synchronizing the stream.
@@ -357,9 +361,16 @@ XK_API int xk_tc_gemm(int M, int N, int K, const float *A, int lda, const float 
 #define XK_PH_SOLVE 6
 #define XK_PH_CONTROL 7
 #define XK_PH_FALLBACK 8
-#define XK_PH_COUNT 9
+#define XK_PH_TC 9        /* inside XK_PH_FACTOR with fp32_bcr: each launch of the tensor-core products */
+#define XK_PH_LEAF 10     /* inside XK_PH_FACTOR with fp32_bcr: each launch of the leaf-block inversions */
+#define XK_PH_COUNT 11
 XK_API int xk_profile(xk_ctx *ctx, int enable);
 XK_API int xk_profile_read(xk_ctx *ctx, double *ms, long long *calls, int n);
+/* Work of the context's FP32 factorization (fp32_bcr): *mma_flops = 2 m n k summed over
+ * every tensor-core product of one factorization (the tensor pipe executes three times
+ * that: head x head, head x tail, tail x head); *leaf_flops = 2 n^3 summed over its leaf
+ * inversions.  XK_EINVAL for contexts without the reduction. */
+XK_API int xk_factor_work(xk_ctx *ctx, double *mma_flops, double *leaf_flops);
 /* Testing aid for the bounded waits: makes the next grid barrier of the
  * context's FP64 factorization unreachable (its arrival count is raised past
  * any grid), as if a CTA never arrived.  The waiting CTAs give up after

@@ -1,9 +1,10 @@
 """Autotuner for the block-inversion kernels: picks, per species count S and
-precision, the panel width and either the number of CTAs of the grid-wide
-persistent factorization or the size of the thread-block cluster that holds
-each block in distributed shared memory (mixed precision), by timing the
-library's own factorization phase (CUDA events around it, xk_profile) on a
-short slice of the column.
+precision, between the block cyclic reduction on the tensor cores and the
+chain of block inversions (mixed precision), and for the chain the panel
+width and either the number of CTAs of the grid-wide persistent
+factorization or the size of the thread-block cluster that holds each block
+in distributed shared memory, by timing the library's own factorization
+phase (CUDA events around it, xk_profile) on the column.
 
 Results are cached per (GPU name, S, precision) in a JSON file beside the
 built library, and applied through xk_config (panel_width, factor_ctas,
@@ -19,10 +20,11 @@ from . import build as _build
 CANDIDATES = {
     "fp64": [dict(panel_width=8, factor_ctas=152), dict(panel_width=16, factor_ctas=152),
              dict(panel_width=8, factor_ctas=76), dict(fp64_panel=1, panel_width=8, factor_ctas=152)],
-    "mixed": [dict(cluster_size=16, panel_width=8), dict(cluster_size=16, panel_width=16),
-              dict(cluster_size=12, panel_width=16), dict(cluster_size=8, panel_width=16),
-              dict(cluster_size=-1, panel_width=16, factor_ctas=152),
-              dict(cluster_size=-1, panel_width=32, factor_ctas=76)],
+    "mixed": [dict(fp32_bcr=1),
+              dict(fp32_bcr=0, cluster_size=16, panel_width=8), dict(fp32_bcr=0, cluster_size=16, panel_width=16),
+              dict(fp32_bcr=0, cluster_size=12, panel_width=16), dict(fp32_bcr=0, cluster_size=8, panel_width=16),
+              dict(fp32_bcr=0, cluster_size=-1, panel_width=16, factor_ctas=152),
+              dict(fp32_bcr=0, cluster_size=-1, panel_width=32, factor_ctas=76)],
 }
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 TIE = 1.03
@@ -42,13 +44,15 @@ def _load():
 
 
 def _key(S, precision):
-    return f"{_gpu_name()}|S={S}|{precision}|v2"
+    return f"{_gpu_name()}|S={S}|{precision}|v3"
 
 
-def measure(prob, precision, params, layers=6, reps=2):
-    """Factorization time per layer (ms) for one configuration."""
+def measure(prob, precision, params, layers=None, reps=2):
+    """Factorization time per layer (ms) for one configuration, on the first `layers` layers
+    (all of them by default: the reduction's cost per layer depends on the number of layers)."""
     import torch
     from . import xk
+    layers = prob.L if layers is None else layers
     sub = prob.replace(P_bar=prob.P_bar[:layers].copy(), T=prob.T[:layers].copy(),
                        Kzz=prob.Kzz[:layers].copy(), f0=prob.f0[:layers].copy())
     col = xk.Column(sub, precision, **params)
@@ -64,7 +68,7 @@ def measure(prob, precision, params, layers=6, reps=2):
     return ms / reps / layers
 
 
-def tune(prob, precision, layers=6, verbose=False):
+def tune(prob, precision, layers=None, verbose=False):
     """Time every candidate, cache and return (params, table)."""
     table = []
     for params in CANDIDATES[precision]:

@@ -239,7 +239,7 @@ size_t layout(xk_ctx *c, char *base)
     t.kf = b.take<double>(LR); t.kr = b.take<double>(LR);
     t.kph = b.take<double>((size_t)L * std::max(Rph, 1));
     t.alpha = b.take<double>((size_t)L * std::max(W, 1)); t.Jw = b.take<double>((size_t)L * std::max(W, 1));
-    t.w = b.take<double>(LR); t.d = b.take<double>(6 * LR);
+    t.w = b.take<double>(LR); t.d = b.take<double>(6 * LR); t.dw = b.take<double>(LR);
     t.n = b.take<double>(LS); t.F = b.take<double>(LS); t.s = b.take<double>(LS); t.b = b.take<double>(LS);
     t.x = b.take<double>(LS); t.delta = b.take<double>(LS); t.tmp = b.take<double>(LS);
     k = t;
@@ -336,10 +336,27 @@ BlockSys<float> sys32(xk_ctx *c)
     return s;
 }
 
+// Event marks around the reduction's product and leaf launches (tracing).
+struct StageMarks : BcrTimer {
+    xk_ctx *c;
+    PhaseMark *open = nullptr;
+    explicit StageMarks(xk_ctx *ctx) : c(ctx) {}
+    void begin(int kind) override { open = new PhaseMark(c, kind == kBcrGemm ? XK_PH_TC : XK_PH_LEAF); }
+    void end(int) override
+    {
+        delete open;
+        open = nullptr;
+    }
+};
+
 // FP32 block inversions of the mixed path
 cudaError_t factor32(xk_ctx *c, Ctl *ctl, const int *skip)
 {
-    if (c->use_bcr) return bcr_factor(c->bcr, skip, ctl, c->st);
+    if (c->use_bcr) {
+        if (!c->prof) return bcr_factor(c->bcr, skip, ctl, c->st);
+        StageMarks marks(c);
+        return bcr_factor(c->bcr, skip, ctl, c->st, &marks);
+    }
     if (c->cfg.fp32_pivoting) return launch_factor<float>(sys32(c), c->plan, ctl, c->st, skip);
     if (c->use_cluster) return launch_factor_cluster(sys32(c), c->cplan, c->gbuf, ctl, c->st, skip);
     return launch_factor_nopivot(sys32(c), c->plan, c->gbuf, ctl, c->st, skip);
@@ -578,6 +595,7 @@ int xk_config_init(xk_config *cfg)
     cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-15;
     cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1; cfg->reuse_max_iters = 20;
     cfg->refine_max_iter = 10;
+    cfg->fp32_bcr = 1;
     cfg->wait_polls = 0;
     return XK_OK;
 }
@@ -1107,6 +1125,13 @@ int xk_hold_next_barrier(xk_ctx *c)
     return finish_eval(c, "hold_next_barrier");
 }
 
+int xk_factor_work(xk_ctx *c, double *mma_flops, double *leaf_flops)
+{
+    if (!c || !c->ready || !c->use_bcr) return XK_EINVAL;
+    bcr_work(c->bcr, mma_flops, leaf_flops);
+    return XK_OK;
+}
+
 long long xk_launch_count(void) { return launches(); }
 
 // ---------------------------------------------------------------- batches
@@ -1118,6 +1143,7 @@ struct BatchSlot {
     bool inflight = false;
     cudaStream_t saved_st = nullptr;
     FactorPlan saved_plan{}, saved_plan64{};
+    int saved_solve_ctas = 0;
     size_t bytes = 0;
     bool finished = false;
 };
@@ -1161,6 +1187,7 @@ int xk_batch_remove(xk_batch *b, int slot)
     s.ctx->st = s.saved_st;
     s.ctx->plan = s.saved_plan;
     s.ctx->plan64 = s.saved_plan64;
+    s.ctx->bcr.solve_ctas = s.saved_solve_ctas;
     if (s.ev) cudaEventDestroy(s.ev);
     cudaStreamDestroy(s.st);
     b->used -= s.bytes;
@@ -1219,6 +1246,8 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
     s.saved_st = c->st;
     s.saved_plan = c->plan;
     s.saved_plan64 = c->plan64;
+    s.saved_solve_ctas = c->bcr.solve_ctas;
+    c->bcr.solve_ctas = share;          // the reduction's cooperative solve on this column's share of the SMs
     s.bytes = c->ws_bytes;
     s.finished = false;
     c->st = s.st;

@@ -45,95 +45,129 @@ __device__ __forceinline__ bool stop(const int *skip, const Ctl *ctl)
 int split_of(int n) { return 32 * ((n + 63) / 64); }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inversion with partial pivoting of one block per CTA, in shared
-// memory: W <- (P M)^-1 by the in-place elimination, then M^-1 = W P, i.e.
-// out[r][perm[i]] = W[r][i] with perm[i] the original row at position i.
-// Threads form a 16 x 32 grid: thread (ty, tx) owns rows ty + 16 a and columns
-// tx + 32 b, so a column step costs each thread one multiplier per row, one
-// pivot-row entry per column and one FMA per owned element.
+// Gauss-Jordan inversion with partial pivoting of one block per CTA, the block
+// held in registers: warp v owns columns v + 16 b (b < 10) and lane l owns rows
+// l + 32 a (a < 5), so column c belongs to one whole warp and, with the
+// column loop unrolled over b, to a fixed register.  Pivoting is implicit:
+// rows never move; the pivot of column c is the unused row p(c) of largest
+// |value| (a warp reduction in the owning warp), and the in-place elimination
+// leaves row p(k) holding row k of (P M)^-1, so M^-1[k][p(c)] = W[p(k)][c].
+// Per column: the owning warp publishes the pivot and the column's
+// multipliers (one barrier), the lanes holding the pivot row publish it (one
+// barrier), and every thread updates its 50 elements with one FMA each;
+// shared buffers alternate between columns.
 // ---------------------------------------------------------------------------
-constexpr int kLeafRowGroups = kLeafThreads / 32;                         // 16
-constexpr int kLeafRows = (kBcrLeafMax + kLeafRowGroups - 1) / kLeafRowGroups;   // 10
-constexpr int kLeafCols = (kBcrLeafMax + 31) / 32;                         // 5
+constexpr int kLeafWarps = kLeafThreads / 32;                       // 16
+constexpr int kLeafColGroups = (kBcrLeafMax + kLeafWarps - 1) / kLeafWarps;   // 10
+constexpr int kLeafRowGroups = (kBcrLeafMax + 31) / 32;             // 5
 
-__global__ void __launch_bounds__(kLeafThreads) k_leaf_inverse(const BcrLeaf *tasks, const int *skip, const Ctl *ctl)
+__global__ void __launch_bounds__(kLeafThreads, 1) k_leaf_inverse(const BcrLeaf *tasks, const int *skip, const Ctl *ctl)
 {
     if (stop(skip, ctl)) return;
     const BcrLeaf t = tasks[blockIdx.x];
-    extern __shared__ float sm[];
-    const int n = t.n, ld = n + 1;
-    float *W = sm;
-    float *fcol = W + n * ld;
-    int *perm = (int *)(fcol + n);
-    __shared__ int piv_row;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int r = ty; r < n; r += kLeafRowGroups)
-        for (int j = tx; j < n; j += 32) W[r * ld + j] = t.in[(long long)r * t.ldin + j];
-    for (int r = threadIdx.x; r < n; r += blockDim.x) perm[r] = r;
-    __syncthreads();
-    for (int c = 0; c < n; ++c) {
-        if (ty == 0) {
-            float best = -1.0f;
-            int br = c;
-            for (int r = c + tx; r < n; r += 32) {
-                const float v = fabsf(W[r * ld + c]);
-                if (v > best) { best = v; br = r; }
-            }
+    __shared__ float prow[2][kBcrLeafMax], fcol[2][kBcrLeafMax];
+    __shared__ int piv[2];
+    __shared__ int perm[kBcrLeafMax], iperm[kBcrLeafMax];
+    const int n = t.n;
+    const int ln = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    float w[kLeafRowGroups][kLeafColGroups];
+    unsigned used = 0;                      // bit a: row ln + 32 a is a pivot already (or beyond n)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orow = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ob > best || (ob == best && orow < br)) { best = ob; br = orow; }
-            }
-            if (tx == 0) piv_row = br;
+    for (int a = 0; a < kLeafRowGroups; ++a) {
+        const int r = ln + 32 * a;
+#pragma unroll
+        for (int b = 0; b < kLeafColGroups; ++b) {
+            const int j = wv + kLeafWarps * b;
+            w[a][b] = (r < n && j < n) ? t.in[(long long)r * t.ldin + j] : 0.0f;
         }
-        __syncthreads();
-        const int p = piv_row;
-        if (p != c) {
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                const float a = W[c * ld + j];
-                W[c * ld + j] = W[p * ld + j];
-                W[p * ld + j] = a;
-            }
-            if (threadIdx.x == 0) {
-                const int q = perm[c];
-                perm[c] = perm[p];
-                perm[p] = q;
+        if (r >= n) used |= 1u << a;
+    }
+    int col = 0;
+#pragma unroll
+    for (int bc = 0; bc < kLeafColGroups; ++bc) {
+        for (int cw = 0; cw < kLeafWarps; ++cw, ++col) {
+            const int c = kLeafWarps * bc + cw;
+            if (c >= n) break;
+            const int buf = col & 1;
+            if (wv == cw) {
+                // the owning warp: largest unused row of column c, lowest row on ties
+                float best = -1.0f;
+                int br = n;
+#pragma unroll
+                for (int a = 0; a < kLeafRowGroups; ++a) {
+                    const float v = fabsf(w[a][bc]);
+                    if (!((used >> a) & 1u) && v > best) { best = v; br = ln + 32 * a; }
+                    const int r = ln + 32 * a;
+                    if (r < n) fcol[buf][r] = w[a][bc];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int orow = __shfl_xor_sync(0xffffffffu, br, o);
+                    if (ob > best || (ob == best && orow < br)) { best = ob; br = orow; }
+                }
+                if (ln == 0) {
+                    const int p = br < n ? br : 0;
+                    piv[buf] = p;
+                    perm[c] = p;
+                    iperm[p] = c;
+                }
             }
             __syncthreads();
-        }
-        // multipliers of column c (row c's is not used), then row c scaled by the pivot's inverse
-        float pv = W[c * ld + c];
-        if (pv == 0.0f) pv = 1e-30f;           // singular block: the FP64 Krylov solve sees a poor preconditioner
-        const float inv = 1.0f / pv;
-        for (int r = threadIdx.x; r < n; r += blockDim.x)
-            if (r != c) fcol[r] = W[r * ld + c];
-        __syncthreads();
-        if (ty == 0)
-            for (int j = tx; j < n; j += 32) W[c * ld + j] = (j == c ? 1.0f : W[c * ld + j]) * inv;
-        __syncthreads();
-        float prow[kLeafCols];
+            const int p = piv[buf];
+            const int pa = p >> 5, pl = p & 31;
+            if (ln == pl) {
 #pragma unroll
-        for (int b = 0; b < kLeafCols; ++b) {
-            const int j = tx + 32 * b;
-            prow[b] = j < n ? W[c * ld + j] : 0.0f;
-        }
-#pragma unroll 2
-        for (int a = 0; a < kLeafRows; ++a) {
-            const int r = ty + kLeafRowGroups * a;
-            if (r >= n || r == c) continue;
-            const float f = fcol[r];
-            float *Wr = W + r * ld;
+                for (int a = 0; a < kLeafRowGroups; ++a)
+                    if (a == pa)
 #pragma unroll
-            for (int b = 0; b < kLeafCols; ++b) {
-                const int j = tx + 32 * b;
-                if (j < n) Wr[j] = (j == c) ? -f * prow[b] : Wr[j] - f * prow[b];
+                        for (int b = 0; b < kLeafColGroups; ++b) {
+                            const int j = wv + kLeafWarps * b;
+                            if (j < n) prow[buf][j] = w[a][b];
+                        }
+                used |= 1u << pa;
+            }
+            __syncthreads();
+            float pv = prow[buf][c];
+            if (pv == 0.0f) pv = 1e-30f;    // singular block: the FP64 Krylov solve sees a poor preconditioner
+            const float inv = 1.0f / pv;
+            float pr[kLeafColGroups];
+#pragma unroll
+            for (int b = 0; b < kLeafColGroups; ++b) {
+                const int j = wv + kLeafWarps * b;
+                pr[b] = (j < n) ? prow[buf][j] * inv : 0.0f;
+            }
+            if (wv == cw) pr[bc] = inv;
+#pragma unroll
+            for (int a = 0; a < kLeafRowGroups; ++a) {
+                const int r = ln + 32 * a;
+                const float f = (r < n) ? fcol[buf][r] : 0.0f;
+#pragma unroll
+                for (int b = 0; b < kLeafColGroups; ++b) w[a][b] = fmaf(-f, pr[b], w[a][b]);
+                if (wv == cw) w[a][bc] = -f * inv;     // column c of the other rows becomes -f / pivot
+            }
+            if (ln == pl) {                              // the pivot row is the scaled row
+#pragma unroll
+                for (int a = 0; a < kLeafRowGroups; ++a)
+                    if (a == pa)
+#pragma unroll
+                        for (int b = 0; b < kLeafColGroups; ++b) w[a][b] = pr[b];
             }
         }
-        __syncthreads();
     }
-    for (int r = ty; r < n; r += kLeafRowGroups)
-        for (int i = tx; i < n; i += 32) t.out[(long long)r * t.ldout + perm[i]] = W[r * ld + i];
+    __syncthreads();
+    // M^-1[k][p(c)] = W[p(k)][c]: row r = p(k) of W goes to row iperm[r] of the output
+#pragma unroll
+    for (int a = 0; a < kLeafRowGroups; ++a) {
+        const int r = ln + 32 * a;
+        if (r >= n) continue;
+        float *o = t.out + (long long)iperm[r] * t.ldout;
+#pragma unroll
+        for (int b = 0; b < kLeafColGroups; ++b) {
+            const int j = wv + kLeafWarps * b;
+            if (j < n) o[perm[j]] = w[a][b];
+        }
+    }
 }
 
 // Level 0 (diagonal couplings), for each kept even layer i with eliminated neighbours l = i-1, r = i+1:
@@ -711,23 +745,33 @@ void bcr_init_pad(const BcrPlan &p, cudaStream_t st)
     k_bcr_pad<<<nblk(n, 256), 256, 0, st>>>(p.D, p.L, p.S, p.Sp);
 }
 
-cudaError_t bcr_factor(const BcrPlan &p, const int *skip, Ctl *ctl, cudaStream_t st)
+void bcr_work(const BcrPlan &p, double *mma_flops, double *leaf_flops)
 {
-    static bool attr_done = false;
-    const size_t leaf_smem = (size_t)kBcrLeafMax * (kBcrLeafMax + 1) * 4 + kBcrLeafMax * 8 + 64;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_leaf_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)leaf_smem);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
+    double m = 0.0, l = 0.0;
+    for (const TcTask &t : p.gemm) {
+        long long k = 0;
+        for (int s = 0; s < t.nseg; ++s) k += t.seg[s].k;
+        m += 2.0 * t.m * (double)t.n * (double)k;
     }
+    for (const BcrLeaf &f : p.leaf) l += 2.0 * (double)f.n * f.n * f.n;
+    if (mma_flops) *mma_flops = m;
+    if (leaf_flops) *leaf_flops = l;
+}
+
+cudaError_t bcr_factor(const BcrPlan &p, const int *skip, Ctl *ctl, cudaStream_t st, BcrTimer *timer)
+{
     for (const BcrStage &s : p.fac) {
         switch (s.kind) {
         case kBcrLeafStage:
+            if (timer) timer->begin(s.kind);
             count_launches(1);
-            k_leaf_inverse<<<s.count, kLeafThreads, leaf_smem, st>>>(p.leaf_d + s.off, skip, ctl);
+            k_leaf_inverse<<<s.count, kLeafThreads, 0, st>>>(p.leaf_d + s.off, skip, ctl);
+            if (timer) timer->end(s.kind);
             break;
         case kBcrGemm: {
+            if (timer) timer->begin(s.kind);
             cudaError_t e = launch_tc_gemm(p.gemm_d + s.off, s.count, s.tiles, p.maps_d, skip, ctl, st);
+            if (timer) timer->end(s.kind);
             if (e != cudaSuccess) return e;
             break;
         }

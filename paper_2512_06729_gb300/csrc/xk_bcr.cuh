@@ -71,8 +71,16 @@ BcrSizes bcr_sizes(int L, int S);
 int bcr_build(BcrPlan &p, int L, int S, cudaStream_t st);
 // Pad rows of D to the identity (once per workspace).
 void bcr_init_pad(const BcrPlan &p, cudaStream_t st);
+// Optional marks around the factorization's launches (tracing).
+struct BcrTimer {
+    virtual void begin(int kind) = 0;
+    virtual void end(int kind) = 0;
+    virtual ~BcrTimer() = default;
+};
 // Factorization: every level's inversions and Schur updates (D is overwritten).
-cudaError_t bcr_factor(const BcrPlan &p, const int *skip, Ctl *ctl, cudaStream_t st);
+cudaError_t bcr_factor(const BcrPlan &p, const int *skip, Ctl *ctl, cudaStream_t st, BcrTimer *timer = nullptr);
+// Flops of one factorization: 2 m n k over the products, 2 n^3 over the leaves.
+void bcr_work(const BcrPlan &p, double *mma_flops, double *leaf_flops);
 // x = M^-1 (b * bscale) (* xscale) with the factorization, FP64 in and out.
 cudaError_t bcr_solve(const BcrPlan &p, const double *b, double *x, const double *bscale, const double *xscale,
                       const int *skip, Ctl *ctl, cudaStream_t st);

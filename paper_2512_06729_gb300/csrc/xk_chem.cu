@@ -346,7 +346,31 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
     for (int j = S + lane; j < c.ld; j += 32) Ar[j] = (T)0;
 }
 
-// y = diag(1/s) (I/dt - J) diag(s) x, matrix-free from the reaction derivatives (FP64).
+// y = diag(1/s) (I/dt - J) diag(s) x, matrix-free from the reaction derivatives (FP64), in two
+// passes.  First the directional derivative of every rate along v = s x:
+//   dw[k][r] = sum over the reaction's slots of d[k][r][slot] v[k][species(slot)]
+// (d holds d(k_f prod n_reac)/dn and -d(k_r prod n_prod)/dn, so dw is the change of w_r);
+// then per species (J v)_i = sum_r nu_ir dw_r through the species-major stoichiometry, a warp
+// per row, plus the transport terms.
+__global__ void k_jv_rates(Col c, const Ctl *ctl, const double *x, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)c.L * c.R) return;
+    const int k = (int)(idx / c.R), r = (int)(idx % c.R);
+    const double *d = c.d + idx * 6;
+    const double *sk = c.s + (long long)k * c.S, *xk = x + (long long)k * c.S;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int i = c.reac[3 * r + q];
+        if (i >= 0) acc += d[q] * sk[i] * xk[i];
+        const int j = c.prod[3 * r + q];
+        if (j >= 0) acc += d[3 + q] * sk[j] * xk[j];
+    }
+    c.dw[idx] = acc;
+}
+
 __global__ void k_jv(Col c, const Ctl *ctl, const double *x, double *y, const double *rowdiv, const int *skip)
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
@@ -355,17 +379,14 @@ __global__ void k_jv(Col c, const Ctl *ctl, const double *x, double *y, const do
     int lane = threadIdx.x & 31;
     if (warp >= L * S) return;
     int k = warp / S, i = warp % S;
-    const double *dk = c.d + (long long)k * c.R * 6;
+    const double *dwk = c.dw + (long long)k * c.R;
     const double *sk = c.s + (long long)k * S;
     const double *xk = x + (long long)k * S;
     double acc = 0.0;
-    for (int e = c.jp[i] + lane; e < c.jp[i + 1]; e += 32) {
-        int jc = c.jcol[e];
-        int rs = c.jrs[e];
-        double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
-        int j = jc & 0xffff;
-        double t = dv * sk[j] * xk[j];
-        acc += ((jc >> 16) > 0) ? t : -t;
+    for (int e = c.yp[i] + lane; e < c.yp[i + 1]; e += 32) {
+        const int code = c.yent[e];
+        const double v = dwk[code >> 4];
+        acc += ((code & 15) - 8 < 0) ? v : -v;       // -(nu) dw: reactant rows +, product rows -
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -646,6 +667,7 @@ void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, 
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
                cudaStream_t st)
 {
+    if (((long long)c.L * c.R) > 0) { count_launches(1); k_jv_rates<<<nblocks((long long)c.L * c.R), kThreads, 0, st>>>(c, ctl, xs, skip); }
     if (((long long)c.L * c.S * 32) > 0) { count_launches(1); k_jv<<<nblocks((long long)c.L * c.S * 32), kThreads, 0, st>>>(c, ctl, xs, ys, rowdiv, skip); }
 }
 

@@ -41,6 +41,7 @@ struct Col {
     double *ngas, *z, *dz, *dzi, *u, *v;
     // per step
     double *grt, *lnkc, *kf, *kr, *kph, *alpha, *Jw, *w, *d;
+    double *dw;           // [L][R] directional derivative of each rate along a vector (J v)
     double *n, *F, *s, *b, *x, *delta, *tmp;
 };
 

@@ -103,9 +103,11 @@ SIGNATURES = {
     "xk_tc_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_float, C.c_float,
                              _vp]),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
+    "xk_factor_work": (C.c_int, [_vp, _dp, _dp]),
 }
 
-PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control", "fallback"]
+PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control", "fallback",
+          "tc", "leaf"]
 
 
 def lib(build_if_missing=False):
@@ -333,6 +335,12 @@ class Column:
         calls = (C.c_longlong * len(PHASES))()
         self._call("xk_profile_read", ms, calls, len(PHASES))
         return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+
+    def factor_work(self):
+        """(tensor-core product flops 2mnk, leaf inversion flops 2n^3) of one FP32 factorization."""
+        m, l = C.c_double(), C.c_double()
+        self._call("xk_factor_work", C.byref(m), C.byref(l))
+        return m.value, l.value
 
     def block_solve32(self, A, lo, up, f):
         x = self._dev(self.L, self.S)

@@ -301,15 +301,16 @@ def test_fp32_cluster_full_size():
     assert all(e < (1.2e-3 if k[2] else 1e-4) for k, e in errs.items()), errs
 
 
-@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}), ("mixed", {"twisted": 0}),
-                                          ("mixed", {"cluster_size": -1}), ("mixed", {"fp32_pivoting": 1}),
-                                          ("mixed", {"fp32_bcr": 1})])
+@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}), ("mixed", {"fp32_bcr": 0, "twisted": 0}),
+                                          ("mixed", {"fp32_bcr": 0, "cluster_size": -1}),
+                                          ("mixed", {"fp32_bcr": 0, "fp32_pivoting": 1}), ("mixed", {"fp32_bcr": 0})])
 def test_step_delta(precision, kw):
     """One linear step at the initial state (small dt) and at a late state
     (the dt the controller reached there), against the oracle.  In mixed
-    precision (cluster-resident FP32 inversion, grid-wide without and with
-    pivoting) FGMRES must converge on the FP32 preconditioner at the initial
-    state (iters >= 0: no FP64 fallback)."""
+    precision (block cyclic reduction on the tensor cores, the default; the
+    cluster-resident FP32 inversion, top-down or twisted; grid-wide without
+    and with pivoting) FGMRES must converge on the FP32 preconditioner at the
+    initial state (iters >= 0: no FP64 fallback)."""
     p = synth.small_column()
     o = Oracle(p)
     c = xk.Column(p, precision, **kw)
@@ -383,7 +384,7 @@ def _replay(p, precision, dts, **kw):
     return np.array(out)
 
 
-@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}), ("mixed", {"fp32_bcr": 1})])
+@pytest.mark.parametrize("precision,kw", [("fp64", {}), ("mixed", {}), ("mixed", {"fp32_bcr": 0})])
 def test_replayed_schedule_small_column(precision, kw):
     """The oracle's own controlled dt sequence on the 40-species, 60-layer
     column (1e-8 s up to dt_max = 1e8 s), replayed by both sides with every
@@ -526,8 +527,8 @@ def _step_parity(o, n, dt, deltas):
 
 def test_full_size_column():
     """The 594-species, 7,720-reaction, 150-layer column at the bench's launch
-    configuration (library defaults: twisted FP32 inversion on 16-CTA clusters,
-    twisted FP64 inversion, FGMRES refinement in both paths): rate
+    configuration (library defaults: FP32 block cyclic reduction on the tensor
+    cores, twisted FP64 inversion, FGMRES refinement in both paths): rate
     coefficients, photolysis and the residual at the initial state element by
     element against the oracle; Jacobian blocks of three layers; and the
     mixed and FP64 linear steps at dt = 1e-6 s and 1e-2 s element by element
