@@ -235,6 +235,7 @@ size_t layout(xk_ctx *c, char *base)
     t.ngas = b.take<double>(L); t.z = b.take<double>(L); t.dz = b.take<double>(L); t.dzi = b.take<double>(L);
     t.u = b.take<double>(std::max<size_t>(1, (size_t)(L - 1) * S));
     t.v = b.take<double>(std::max<size_t>(1, (size_t)(L - 1) * S));
+    t.tdg = b.take<double>(LS); t.tlo = b.take<double>(LS); t.tup = b.take<double>(LS); t.rs = b.take<double>(LS);
     t.grt = b.take<double>(LS); t.lnkc = b.take<double>(LR);
     t.kf = b.take<double>(LR); t.kr = b.take<double>(LR);
     t.kph = b.take<double>((size_t)L * std::max(Rph, 1));

@@ -31,7 +31,7 @@ namespace xk {
 
 namespace {
 
-constexpr int kLeafThreads = 512;
+constexpr int kLeafWarpsUsed = 16;   // warps of the leaf inversion: 16 x 50 elements per thread
 constexpr int kMvThreads = 256;
 constexpr int kMvRows = 64;
 constexpr int kArrD = 0, kArrINV = 1, kArrTMP = 2, kArrCP = 3, kArrPQ = 4, kArrays = 5;
@@ -47,115 +47,186 @@ int split_of(int n) { return 32 * ((n + 63) / 64); }
 // ---------------------------------------------------------------------------
 // Gauss-Jordan inversion with partial pivoting of one block per CTA, the block
 // held in registers: warp v owns columns v + 16 b (b < 10) and lane l owns rows
-// l + 32 a (a < 5), so column c belongs to one whole warp and, with the
-// column loop unrolled over b, to a fixed register.  Pivoting is implicit:
-// rows never move; the pivot of column c is the unused row p(c) of largest
-// |value| (a warp reduction in the owning warp), and the in-place elimination
-// leaves row p(k) holding row k of (P M)^-1, so M^-1[k][p(c)] = W[p(k)][c].
-// Per column: the owning warp publishes the pivot and the column's
-// multipliers (one barrier), the lanes holding the pivot row publish it (one
-// barrier), and every thread updates its 50 elements with one FMA each;
-// shared buffers alternate between columns.
+// l + 32 a (a < 5), so column c belongs to one whole warp and, with the column
+// loop unrolled over b, to a fixed register.  Pivoting is implicit: rows never
+// move; the pivot of column c is the unused row p(c) of largest |value|, and
+// the in-place elimination leaves row p(k) holding row k of (P M)^-1, so
+// M^-1[k][p(c)] = W[p(k)][c].
+//
+// One barrier per column.  After it every warp reads the pivot row index, the
+// pivot and the column's multipliers from shared memory and takes the pivot
+// row's entries in its own columns from the lane that holds them (a warp
+// shuffle).  The warp owning the next column updates that column first, picks
+// its pivot (redux.sync maximum of |value| over the unused rows, the lowest
+// row on ties) and publishes it before updating its other columns
+// (look-ahead); shared buffers alternate between columns.
 // ---------------------------------------------------------------------------
-constexpr int kLeafWarps = kLeafThreads / 32;                       // 16
-constexpr int kLeafColGroups = (kBcrLeafMax + kLeafWarps - 1) / kLeafWarps;   // 10
-constexpr int kLeafRowGroups = (kBcrLeafMax + 31) / 32;             // 5
+constexpr int kLeafRowGroups = (kBcrLeafMax + 31) / 32;                         // 5
 
-__global__ void __launch_bounds__(kLeafThreads, 1) k_leaf_inverse(const BcrLeaf *tasks, const int *skip, const Ctl *ctl)
+// Row groups: element a of a lane's rows selected by a runtime index.
+__device__ __forceinline__ float leaf_pick(const float (&col)[kLeafRowGroups], int a)
 {
+    float v = col[0];
+#pragma unroll
+    for (int q = 1; q < kLeafRowGroups; ++q)
+        if (a == q) v = col[q];
+    return v;
+}
+
+struct LeafPivot {
+    int p;
+    float v;
+};
+
+// Pivot of one column (its values in this lane's rows: col[a]) over the unused rows of the warp.
+__device__ __forceinline__ LeafPivot leaf_argmax(const float (&col)[kLeafRowGroups], unsigned used, int ln, int n)
+{
+    unsigned key = 0u;
+    int br = 0x7fffffff;
+#pragma unroll
+    for (int a = 0; a < kLeafRowGroups; ++a) {
+        const float v = fabsf(col[a]);
+        const unsigned k = (((used >> a) & 1u) || !(v == v)) ? 0u : __float_as_uint(v) + 1u;
+        if (k > key) { key = k; br = ln + 32 * a; }
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, key);
+    int p = (int)__reduce_min_sync(0xffffffffu, (key == m && m != 0u) ? (unsigned)br : 0x7fffffffu);
+    if (m == 0u || p >= n) p = 0;       // no candidate left: a singular block
+    const float val = __shfl_sync(0xffffffffu, leaf_pick(col, p >> 5), p & 31);
+    return LeafPivot{p, val};
+}
+
+template <int kLeafWarps>
+__global__ void __launch_bounds__(kLeafWarps * 32, 1) k_leaf_inverse(const BcrLeaf *tasks, const int *skip, const Ctl *ctl)
+{
+    constexpr int kLeafColGroups = (kBcrLeafMax + kLeafWarps - 1) / kLeafWarps;
     if (stop(skip, ctl)) return;
     const BcrLeaf t = tasks[blockIdx.x];
-    __shared__ float prow[2][kBcrLeafMax], fcol[2][kBcrLeafMax];
+    __shared__ float fcol[2][kBcrLeafMax];
+    __shared__ float pval[2];
     __shared__ int piv[2];
     __shared__ int perm[kBcrLeafMax], iperm[kBcrLeafMax];
     const int n = t.n;
     const int ln = threadIdx.x & 31, wv = threadIdx.x >> 5;
-    float w[kLeafRowGroups][kLeafColGroups];
-    unsigned used = 0;                      // bit a: row ln + 32 a is a pivot already (or beyond n)
+    float w[kLeafColGroups][kLeafRowGroups];        // w[b][a] = W[ln + 32 a][wv + 16 b]
+    unsigned used = 0;
 #pragma unroll
     for (int a = 0; a < kLeafRowGroups; ++a) {
         const int r = ln + 32 * a;
 #pragma unroll
         for (int b = 0; b < kLeafColGroups; ++b) {
             const int j = wv + kLeafWarps * b;
-            w[a][b] = (r < n && j < n) ? t.in[(long long)r * t.ldin + j] : 0.0f;
+            w[b][a] = (r < n && j < n) ? t.in[(long long)r * t.ldin + j] : 0.0f;
         }
         if (r >= n) used |= 1u << a;
     }
-    int col = 0;
+    // column 0: its owner (warp 0) publishes the first pivot
+    if (wv == 0) {
+        const LeafPivot pv = leaf_argmax(w[0], used, ln, n);
+#pragma unroll
+        for (int a = 0; a < kLeafRowGroups; ++a) {
+            const int r = ln + 32 * a;
+            if (r < n) fcol[0][r] = w[0][a];
+        }
+        if (ln == 0) { piv[0] = pv.p; pval[0] = pv.v; perm[0] = pv.p; iperm[pv.p] = 0; }
+    }
+    __syncthreads();
 #pragma unroll
     for (int bc = 0; bc < kLeafColGroups; ++bc) {
-        for (int cw = 0; cw < kLeafWarps; ++cw, ++col) {
+        for (int cw = 0; cw < kLeafWarps; ++cw) {
             const int c = kLeafWarps * bc + cw;
             if (c >= n) break;
-            const int buf = col & 1;
-            if (wv == cw) {
-                // the owning warp: largest unused row of column c, lowest row on ties
-                float best = -1.0f;
-                int br = n;
-#pragma unroll
-                for (int a = 0; a < kLeafRowGroups; ++a) {
-                    const float v = fabsf(w[a][bc]);
-                    if (!((used >> a) & 1u) && v > best) { best = v; br = ln + 32 * a; }
-                    const int r = ln + 32 * a;
-                    if (r < n) fcol[buf][r] = w[a][bc];
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int orow = __shfl_xor_sync(0xffffffffu, br, o);
-                    if (ob > best || (ob == best && orow < br)) { best = ob; br = orow; }
-                }
-                if (ln == 0) {
-                    const int p = br < n ? br : 0;
-                    piv[buf] = p;
-                    perm[c] = p;
-                    iperm[p] = c;
-                }
-            }
-            __syncthreads();
+            const int buf = c & 1;
             const int p = piv[buf];
             const int pa = p >> 5, pl = p & 31;
-            if (ln == pl) {
-#pragma unroll
-                for (int a = 0; a < kLeafRowGroups; ++a)
-                    if (a == pa)
-#pragma unroll
-                        for (int b = 0; b < kLeafColGroups; ++b) {
-                            const int j = wv + kLeafWarps * b;
-                            if (j < n) prow[buf][j] = w[a][b];
-                        }
-                used |= 1u << pa;
-            }
-            __syncthreads();
-            float pv = prow[buf][c];
-            if (pv == 0.0f) pv = 1e-30f;    // singular block: the FP64 Krylov solve sees a poor preconditioner
-            const float inv = 1.0f / pv;
-            float pr[kLeafColGroups];
-#pragma unroll
-            for (int b = 0; b < kLeafColGroups; ++b) {
-                const int j = wv + kLeafWarps * b;
-                pr[b] = (j < n) ? prow[buf][j] * inv : 0.0f;
-            }
-            if (wv == cw) pr[bc] = inv;
+            float pivv = pval[buf];
+            if (pivv == 0.0f) pivv = 1e-30f;    // singular block: the FP64 Krylov solve sees a poor preconditioner
+            const float inv = 1.0f / pivv;
+            float f[kLeafRowGroups];
 #pragma unroll
             for (int a = 0; a < kLeafRowGroups; ++a) {
                 const int r = ln + 32 * a;
-                const float f = (r < n) ? fcol[buf][r] : 0.0f;
-#pragma unroll
-                for (int b = 0; b < kLeafColGroups; ++b) w[a][b] = fmaf(-f, pr[b], w[a][b]);
-                if (wv == cw) w[a][bc] = -f * inv;     // column c of the other rows becomes -f / pivot
+                f[a] = (r < n) ? fcol[buf][r] : 0.0f;
             }
-            if (ln == pl) {                              // the pivot row is the scaled row
-#pragma unroll
-                for (int a = 0; a < kLeafRowGroups; ++a)
-                    if (a == pa)
-#pragma unroll
-                        for (int b = 0; b < kLeafColGroups; ++b) w[a][b] = pr[b];
+            if (ln == pl) used |= 1u << pa;          // row p is a pivot from now on
+            const bool own = (wv == cw);             // this warp owns column c
+            // the pivot row in this warp's columns (lane pl, row group pa: uniform over the warp), scaled;
+            // the column-c entry becomes 1 / pivot
+            float pr[kLeafColGroups];
+            switch (pa) {
+#define XK_LEAF_ROW(A)                                                                            \
+    case A:                                                                                       \
+        _Pragma("unroll") for (int b = 0; b < kLeafColGroups; ++b) pr[b] =                     \
+            __shfl_sync(0xffffffffu, w[b][A], pl);                                                \
+        break;
+                XK_LEAF_ROW(0) XK_LEAF_ROW(1) XK_LEAF_ROW(2) XK_LEAF_ROW(3) XK_LEAF_ROW(4)
+#undef XK_LEAF_ROW
             }
+#pragma unroll
+            for (int b = 0; b < kLeafColGroups; ++b) pr[b] *= inv;
+            if (own) pr[bc] = inv;
+            // update of one column b: every row w - f pr (column c: -f / pivot); the pivot row is
+            // then overwritten by its scaled values (fix_pivot)
+            auto update = [&](float (&col)[kLeafRowGroups], float prb, bool is_c) {
+#pragma unroll
+                for (int a = 0; a < kLeafRowGroups; ++a) col[a] = is_c ? -f[a] * inv : fmaf(-f[a], prb, col[a]);
+            };
+            auto fix_pivot = [&](float (&col)[kLeafRowGroups], float prb) {
+                if (ln == pl) {
+                    switch (pa) {
+                    case 0: col[0] = prb; break;
+                    case 1: col[1] = prb; break;
+                    case 2: col[2] = prb; break;
+                    case 3: col[3] = prb; break;
+                    default: col[4] = prb; break;
+                    }
+                }
+            };
+            // look-ahead: the owner of column c + 1 updates it, picks its pivot and publishes it first
+            const int cn = c + 1;
+            const int nw = cn % kLeafWarps;
+            const bool next_here = cn < n && wv == nw;
+            if (next_here) {
+                if (cw + 1 < kLeafWarps) {
+                    update(w[bc], pr[bc], false);
+                    fix_pivot(w[bc], pr[bc]);
+                    const LeafPivot pv = leaf_argmax(w[bc], used, ln, n);
+#pragma unroll
+                    for (int a = 0; a < kLeafRowGroups; ++a) {
+                        const int r = ln + 32 * a;
+                        if (r < n) fcol[buf ^ 1][r] = w[bc][a];
+                    }
+                    if (ln == 0) { piv[buf ^ 1] = pv.p; pval[buf ^ 1] = pv.v; perm[cn] = pv.p; iperm[pv.p] = cn; }
+                } else if (bc + 1 < kLeafColGroups) {
+                    update(w[bc + 1], pr[bc + 1], false);
+                    fix_pivot(w[bc + 1], pr[bc + 1]);
+                    const LeafPivot pv = leaf_argmax(w[bc + 1], used, ln, n);
+#pragma unroll
+                    for (int a = 0; a < kLeafRowGroups; ++a) {
+                        const int r = ln + 32 * a;
+                        if (r < n) fcol[buf ^ 1][r] = w[bc + 1][a];
+                    }
+                    if (ln == 0) { piv[buf ^ 1] = pv.p; pval[buf ^ 1] = pv.v; perm[cn] = pv.p; iperm[pv.p] = cn; }
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < kLeafColGroups; ++b) {
+                const bool done_early = next_here && ((cw + 1 < kLeafWarps) ? (b == bc) : (b == bc + 1));
+                if (!done_early) update(w[b], pr[b], own && b == bc);
+            }
+            if (ln == pl) {
+                switch (pa) {
+#define XK_LEAF_FIX(A)                                                                           \
+    case A:                                                                                      \
+        _Pragma("unroll") for (int b = 0; b < kLeafColGroups; ++b) w[b][A] = pr[b];             \
+        break;
+                    XK_LEAF_FIX(0) XK_LEAF_FIX(1) XK_LEAF_FIX(2) XK_LEAF_FIX(3) XK_LEAF_FIX(4)
+#undef XK_LEAF_FIX
+                }
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
     // M^-1[k][p(c)] = W[p(k)][c]: row r = p(k) of W goes to row iperm[r] of the output
 #pragma unroll
     for (int a = 0; a < kLeafRowGroups; ++a) {
@@ -165,7 +236,7 @@ __global__ void __launch_bounds__(kLeafThreads, 1) k_leaf_inverse(const BcrLeaf 
 #pragma unroll
         for (int b = 0; b < kLeafColGroups; ++b) {
             const int j = wv + kLeafWarps * b;
-            if (j < n) o[perm[j]] = w[a][b];
+            if (j < n) o[perm[j]] = w[b][a];
         }
     }
 }
@@ -765,7 +836,7 @@ cudaError_t bcr_factor(const BcrPlan &p, const int *skip, Ctl *ctl, cudaStream_t
         case kBcrLeafStage:
             if (timer) timer->begin(s.kind);
             count_launches(1);
-            k_leaf_inverse<<<s.count, kLeafThreads, 0, st>>>(p.leaf_d + s.off, skip, ctl);
+            k_leaf_inverse<kLeafWarpsUsed><<<s.count, kLeafWarpsUsed * 32, 0, st>>>(p.leaf_d + s.off, skip, ctl);
             if (timer) timer->end(s.kind);
             break;
         case kBcrGemm: {

@@ -4,6 +4,8 @@
 // matrix-free Jacobian-vector product, and device-side step control.
 #include <math.h>
 
+#include <algorithm>
+
 #include <atomic>
 
 #include "xk_internal.cuh"
@@ -15,6 +17,11 @@ namespace {
 constexpr int kThreads = 256;
 
 inline int nblocks(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+// Grid of a kernel that a device flag may skip: a grid-stride loop over at most a few waves, so
+// that a skipped launch (an FGMRES slot past convergence, an FP64 route not taken) schedules a
+// few thousand threads, not one per element.
+constexpr int kGatedBlocks = 152 * 8;
+inline int gated_blocks(long long n, int t = kThreads) { return (int)std::min<long long>((n + t - 1) / t, kGatedBlocks); }
 
 // ---------------------------------------------------------------------------
 // grid (Sec. 2.1): n_gas = P / (k_B T); hydrostatic altitudes; layer widths
@@ -276,6 +283,7 @@ __global__ void k_residual(Col c, const double *n, double *F, const Ctl *ctl, do
         double sc = fmax(nk, f_floor * c.ngas[k]);
         c.s[idx] = sc;
         c.b[idx] = f / sc;
+        if (c.rs) c.rs[idx] = 1.0 / sc;
     }
 }
 
@@ -288,62 +296,62 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
     extern __shared__ double sh[];
-    int S = c.S, L = c.L;
-    int wpb = blockDim.x >> 5;
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long row = (long long)blockIdx.x * wpb + warp;     // (k, i)
-    bool active = row < (long long)L * S;
+    const int S = c.S, L = c.L;
+    const int wpb = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *rowbuf = sh + (long long)warp * (S + 64);
     double *vals = rowbuf + S;
     int *cols = (int *)(vals + 32);
-    int k = active ? (int)(row / S) : 0, i = active ? (int)(row % S) : 0;
-    if (!active) return;
-    for (int j = lane; j < S; j += 32) rowbuf[j] = 0.0;
-    __syncwarp();
-    const double *dk = c.d + (long long)k * c.R * 6;
-    int e0 = c.jp[i], e1 = c.jp[i + 1];
-    for (int base = e0; base < e1; base += 32) {
-        int e = base + lane;
-        if (e < e1) {
-            int jc = c.jcol[e];
-            int rs = c.jrs[e];
-            double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
-            cols[lane] = jc & 0xffff;
-            vals[lane] = ((jc >> 16) > 0) ? dv : -dv;      // +d for a reactant row, -d for a product row
-        }
+    const double dt = dt_override > 0.0 ? dt_override : ctl->dt;
+    for (long long row = (long long)blockIdx.x * wpb + warp; row < (long long)L * S; row += (long long)gridDim.x * wpb) {
+        const int k = (int)(row / S), i = (int)(row % S);
         __syncwarp();
+        for (int j = lane; j < S; j += 32) rowbuf[j] = 0.0;
+        __syncwarp();
+        const double *dk = c.d + (long long)k * c.R * 6;
+        int e0 = c.jp[i], e1 = c.jp[i + 1];
+        for (int base = e0; base < e1; base += 32) {
+            int e = base + lane;
+            if (e < e1) {
+                int jc = c.jcol[e];
+                int rs = c.jrs[e];
+                double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+                cols[lane] = jc & 0xffff;
+                vals[lane] = ((jc >> 16) > 0) ? dv : -dv;      // +d for a reactant row, -d for a product row
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int cnt = min(32, e1 - base);
+                for (int q = 0; q < cnt; ++q) rowbuf[cols[q]] += vals[q];
+            }
+            __syncwarp();
+        }
+        const double *sk = c.s + (long long)k * S;
         if (lane == 0) {
-            int cnt = min(32, e1 - base);
-            for (int q = 0; q < cnt; ++q) rowbuf[cols[q]] += vals[q];
+            double diag = 1.0 / dt;
+            if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
+            if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
+            rowbuf[i] += diag;
+            if (dout) dout[row] = fmax(fabs(rowbuf[i]), 1.0 / dt);
+            double lov = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
+            double upv = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+            if (scaled) {
+                if (k > 0) lov *= c.s[(long long)(k - 1) * S + i] / sk[i];
+                if (k + 1 < L) upv *= c.s[(long long)(k + 1) * S + i] / sk[i];
+            }
+            lo[row] = (T)lov;
+            up[row] = (T)upv;
         }
         __syncwarp();
-    }
-    double dt = dt_override > 0.0 ? dt_override : ctl->dt;
-    const double *sk = c.s + (long long)k * S;
-    if (lane == 0) {
-        double diag = 1.0 / dt;
-        if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
-        if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
-        rowbuf[i] += diag;
-        if (dout) dout[row] = fmax(fabs(rowbuf[i]), 1.0 / dt);
-        double lov = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
-        double upv = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+        T *Ar = A + (long long)k * (lstride > 0 ? lstride : (long long)S * c.ld) + (long long)i * c.ld;
         if (scaled) {
-            if (k > 0) lov *= c.s[(long long)(k - 1) * S + i] / sk[i];
-            if (k + 1 < L) upv *= c.s[(long long)(k + 1) * S + i] / sk[i];
+            double inv = 1.0 / sk[i];
+            for (int j = lane; j < S; j += 32) Ar[j] = (T)(rowbuf[j] * sk[j] * inv);
+        } else {
+            for (int j = lane; j < S; j += 32) Ar[j] = (T)rowbuf[j];
         }
-        lo[row] = (T)lov;
-        up[row] = (T)upv;
+        for (int j = S + lane; j < c.ld; j += 32) Ar[j] = (T)0;
     }
-    __syncwarp();
-    T *Ar = A + (long long)k * (lstride > 0 ? lstride : (long long)S * c.ld) + (long long)i * c.ld;
-    if (scaled) {
-        double inv = 1.0 / sk[i];
-        for (int j = lane; j < S; j += 32) Ar[j] = (T)(rowbuf[j] * sk[j] * inv);
-    } else {
-        for (int j = lane; j < S; j += 32) Ar[j] = (T)rowbuf[j];
-    }
-    for (int j = S + lane; j < c.ld; j += 32) Ar[j] = (T)0;
 }
 
 // y = diag(1/s) (I/dt - J) diag(s) x, matrix-free from the reaction derivatives (FP64), in two
@@ -355,29 +363,82 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
 __global__ void k_jv_rates(Col c, const Ctl *ctl, const double *x, const int *skip)
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)c.L * c.R) return;
-    const int k = (int)(idx / c.R), r = (int)(idx % c.R);
-    const double *d = c.d + idx * 6;
-    const double *sk = c.s + (long long)k * c.S, *xk = x + (long long)k * c.S;
-    double acc = 0.0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)c.L * c.R;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx / c.R), r = (int)(idx % c.R);
+        const double *d = c.d + idx * 6;
+        const double *sk = c.s + (long long)k * c.S, *xk = x + (long long)k * c.S;
+        double acc = 0.0;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int i = c.reac[3 * r + q];
-        if (i >= 0) acc += d[q] * sk[i] * xk[i];
-        const int j = c.prod[3 * r + q];
-        if (j >= 0) acc += d[3 + q] * sk[j] * xk[j];
+        for (int q = 0; q < 3; ++q) {
+            const int i = c.reac[3 * r + q];
+            if (i >= 0) acc += d[q] * sk[i] * xk[i];
+            const int j = c.prod[3 * r + q];
+            if (j >= 0) acc += d[3 + q] * sk[j] * xk[j];
+        }
+        c.dw[idx] = acc;
     }
-    c.dw[idx] = acc;
+}
+
+__device__ __forceinline__ void jv_row(const Col &c, const Ctl *ctl, const double *x, double *y, const double *rowdiv,
+                                       int warp, int lane);
+__device__ __forceinline__ void jv_finish(const Col &c, const Ctl *ctl, const double *x, double *y,
+                                          const double *rowdiv, int k, int i, double acc);
+
+// The same J v in one launch with one CTA per layer: the layer's R directional rate derivatives are
+// formed in shared memory, then each species sums its stoichiometric entries from there (the
+// gathers hit shared memory instead of L1).  For networks whose R doubles fit shared memory.
+__global__ void k_jv_layer(Col c, const Ctl *ctl, const double *x, double *y, const double *rowdiv, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    extern __shared__ double dws[];
+    const int S = c.S, R = c.R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = blockIdx.x; k < c.L; k += gridDim.x) {
+        const double *sk = c.s + (long long)k * S, *xk = x + (long long)k * S;
+        const double *dk = c.d + (long long)k * R * 6;
+        __syncthreads();
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+            const double *d = dk + (long long)r * 6;
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int a = c.reac[3 * r + q];
+                if (a >= 0) acc += d[q] * sk[a] * xk[a];
+                const int b = c.prod[3 * r + q];
+                if (b >= 0) acc += d[3 + q] * sk[b] * xk[b];
+            }
+            dws[r] = acc;
+        }
+        __syncthreads();
+        for (int i = warp; i < S; i += nw) {
+            double acc = 0.0;
+            for (int e = c.yp[i] + lane; e < c.yp[i + 1]; e += 32) {
+                const int code = c.yent[e];
+                const double v = dws[code >> 4];
+                acc += ((code & 15) - 8 < 0) ? v : -v;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) jv_finish(c, ctl, x, y, rowdiv, k, i, acc);
+        }
+    }
 }
 
 __global__ void k_jv(Col c, const Ctl *ctl, const double *x, double *y, const double *rowdiv, const int *skip)
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
-    int S = c.S, L = c.L;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= L * S) return;
+    const int S = c.S, L = c.L;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); warp < L * S; warp += nwarps)
+        jv_row(c, ctl, x, y, rowdiv, warp, lane);
+}
+
+__device__ __forceinline__ void jv_row(const Col &c, const Ctl *ctl, const double *x, double *y, const double *rowdiv,
+                                       int warp, int lane)
+{
+    const int S = c.S, L = c.L;
     int k = warp / S, i = warp % S;
     const double *dwk = c.dw + (long long)k * c.R;
     const double *sk = c.s + (long long)k * S;
@@ -390,17 +451,23 @@ __global__ void k_jv(Col c, const Ctl *ctl, const double *x, double *y, const do
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        double si = sk[i];
-        double diag = 1.0 / ctl->dt;
-        if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
-        if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
-        double r = acc / si + diag * xk[i];
-        if (k > 0) r += (-c.u[(long long)(k - 1) * S + i] / c.dz[k]) * c.s[(long long)(k - 1) * S + i] / si * x[(long long)(k - 1) * S + i];
-        if (k + 1 < L) r += (-c.v[(long long)k * S + i] / c.dz[k]) * c.s[(long long)(k + 1) * S + i] / si * x[(long long)(k + 1) * S + i];
-        if (rowdiv) r /= rowdiv[(long long)k * S + i];
-        y[(long long)k * S + i] = r;
-    }
+    if (lane == 0) jv_finish(c, ctl, x, y, rowdiv, k, i, acc);
+    (void)sk;
+    (void)xk;
+}
+
+// Row (k, i) of y from the chemistry sum acc = -(J diag(s) x)_i: scaling, I/dt and transport.
+__device__ __forceinline__ void jv_finish(const Col &c, const Ctl *ctl, const double *x, double *y,
+                                          const double *rowdiv, int k, int i, double acc)
+{
+    const int S = c.S, L = c.L;
+    const long long q = (long long)k * S + i;
+    const double ri = c.rs[q];
+    double r = acc * ri + (1.0 / ctl->dt + c.tdg[q]) * x[q];
+    if (k > 0) r += c.tlo[q] * c.s[q - S] * ri * x[q - S];
+    if (k + 1 < L) r += c.tup[q] * c.s[q + S] * ri * x[q + S];
+    if (rowdiv) r /= rowdiv[q];
+    y[q] = r;
 }
 
 // y = x / d (row equilibration of a right-hand side)
@@ -604,10 +671,26 @@ void launch_set_mixing(const Col &c, const double *f, double *n, cudaStream_t st
 }
 
 // ---------------------------------------------------------------------------
+// Transport terms of the rows of I/dt - dF/dn (the same quotients k_jacobian forms per row).
+__global__ void k_transport_rows(Col c)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = c.S, L = c.L;
+    if (idx >= (long long)L * S) return;
+    const int k = (int)(idx / S), i = (int)(idx % S);
+    double dg = 0.0;
+    if (k + 1 < L) dg += c.u[(long long)k * S + i] / c.dz[k];
+    if (k > 0) dg += c.v[(long long)(k - 1) * S + i] / c.dz[k];
+    c.tdg[idx] = dg;
+    c.tlo[idx] = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
+    c.tup[idx] = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+}
+
 void launch_grid(const Col &c, cudaStream_t st)
 {
     count_launches(1); k_grid<<<1, 256, 0, st>>>(c);
     if (c.L > 1) { count_launches(1); k_transport<<<nblocks((long long)(c.L - 1) * c.S), kThreads, 0, st>>>(c); }
+    if ((long long)c.L * c.S > 0) { count_launches(1); k_transport_rows<<<nblocks((long long)c.L * c.S), kThreads, 0, st>>>(c); }
 }
 
 void launch_thermo(const Col &c, cudaStream_t st)
@@ -652,7 +735,7 @@ void launch_jacobian64(const Col &c, const double *n, const Ctl *ctl, double dt_
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr, skip, 0); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<double><<<skip ? gated_blocks((long long)c.L * c.S, wpb) : nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, dt_override, scaled, A, lo, up, nullptr, skip, 0); }
 }
 
 void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, float *lo, float *up, double *diag,
@@ -661,14 +744,27 @@ void launch_jacobian32(const Col &c, const double *n, const Ctl *ctl, float *A, 
     const int wpb = 4;
     size_t sm = jac_smem(c, wpb);
     cudaFuncSetAttribute(k_jacobian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag, skip, lstride); }
+    if (((long long)c.L * c.S) > 0) { count_launches(1); k_jacobian<float><<<skip ? gated_blocks((long long)c.L * c.S, wpb) : nblocks((long long)c.L * c.S, wpb), wpb * 32, sm, st>>>(c, n, ctl, 0.0, 1, A, lo, up, diag, skip, lstride); }
 }
 
 void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const double *rowdiv, const int *skip,
                cudaStream_t st)
 {
-    if (((long long)c.L * c.R) > 0) { count_launches(1); k_jv_rates<<<nblocks((long long)c.L * c.R), kThreads, 0, st>>>(c, ctl, xs, skip); }
-    if (((long long)c.L * c.S * 32) > 0) { count_launches(1); k_jv<<<nblocks((long long)c.L * c.S * 32), kThreads, 0, st>>>(c, ctl, xs, ys, rowdiv, skip); }
+    if ((long long)c.L * c.S <= 0) return;
+    const size_t sm = (size_t)std::max(c.R, 1) * sizeof(double);
+    if (sm <= 160 * 1024) {
+        static size_t attr = 0;
+        if (sm > attr) {
+            cudaFuncSetAttribute(k_jv_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(160 * 1024));
+            attr = 160 * 1024;
+        }
+        count_launches(1);
+        k_jv_layer<<<std::min(c.L, kGatedBlocks), 512, sm, st>>>(c, ctl, xs, ys, rowdiv, skip);
+        return;
+    }
+    if (((long long)c.L * c.R) > 0) { count_launches(1); k_jv_rates<<<gated_blocks((long long)c.L * c.R), kThreads, 0, st>>>(c, ctl, xs, skip); }
+    count_launches(1);
+    k_jv<<<gated_blocks((long long)c.L * c.S * 32), kThreads, 0, st>>>(c, ctl, xs, ys, rowdiv, skip);
 }
 
 void launch_rowdiv(long long N, const double *x, const double *d, double *y, cudaStream_t st)

@@ -39,6 +39,10 @@ struct Col {
     double g, mbar, alpha_T;
     // derived on the device
     double *ngas, *z, *dz, *dzi, *u, *v;
+    // transport terms of row (k, y) of I/dt - dF/dn, per atmosphere: diagonal (u_k + v_{k-1}) / dz_k,
+    // couplings -u_{k-1} / dz_k (to layer k-1) and -v_k / dz_k (to layer k+1); [L][S]
+    double *tdg, *tlo, *tup;
+    double *rs;           // [L][S] 1 / s of the current step's scaling
     // per step
     double *grt, *lnkc, *kf, *kr, *kph, *alpha, *Jw, *w, *d;
     double *dw;           // [L][R] directional derivative of each rate along a vector (J v)
