@@ -29,7 +29,7 @@ struct xk_ctx {
     bool have_net = false, have_photo = false, have_atm = false;
     bool rates_valid = false;      // k_f, k_r of the loaded network and atmosphere are in the workspace
     // host index structures
-    std::vector<int> yp, yent, jp, jcol, jrs, abs_sp;
+    std::vector<int> yp, yent, jp, jcol, jtp, jrs, jdq, abs_sp;
     std::vector<double> sig_abs_c;
     // device
     char *ws = nullptr;
@@ -177,11 +177,30 @@ void build_indices(xk_ctx *c)
                     if (k >= 0) rows[k].push_back({j, rs});
                 }
             }
+    // grouped by column: row i's distinct columns jcol[jp[i] .. jp[i+1]) in increasing order, each
+    // with its terms jrs[jtp[q] .. jtp[q+1]) in reaction order, a term being (slot << 1) | (reactant
+    // row: +d, product row: -d); jdq[i] is the entry of column i in row i (-1 if none)
     c->jp.assign(S + 1, 0);
     c->jcol.clear();
+    c->jtp.assign(1, 0);
     c->jrs.clear();
+    c->jdq.assign(S, -1);
     for (int i = 0; i < S; ++i) {
-        for (auto &e : rows[i]) { c->jcol.push_back(e.first); c->jrs.push_back(e.second); }
+        std::vector<std::pair<int, int>> ent = rows[i];
+        std::stable_sort(ent.begin(), ent.end(),
+                         [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+                             return (a.first & 0xffff) < (b.first & 0xffff);
+                         });
+        for (size_t e = 0; e < ent.size(); ++e) {
+            const int j = ent[e].first & 0xffff;
+            if (e == 0 || j != (ent[e - 1].first & 0xffff)) {
+                if (e > 0) c->jtp.push_back((int)c->jrs.size());
+                if (j == i) c->jdq[i] = (int)c->jcol.size();
+                c->jcol.push_back(j);
+            }
+            c->jrs.push_back((ent[e].second << 1) | ((ent[e].first >> 16) > 0 ? 1 : 0));
+        }
+        if (!ent.empty()) c->jtp.push_back((int)c->jrs.size());
         c->jp[i + 1] = (int)c->jcol.size();
     }
     // absorbers with a non-zero cross section somewhere
@@ -224,7 +243,9 @@ size_t layout(xk_ctx *c, char *base)
     t.form = b.take<int>(R); t.prow = b.take<int>(R);
     t.yp = b.take<int>(S + 1); t.yent = b.take<int>(std::max<size_t>(1, c->yent.size()));
     t.jp = b.take<int>(S + 1); t.jcol = b.take<int>(std::max<size_t>(1, c->jcol.size()));
+    t.jtp = b.take<int>(std::max<size_t>(1, c->jtp.size()));
     t.jrs = b.take<int>(std::max<size_t>(1, c->jrs.size()));
+    t.jdq = b.take<int>(S);
     t.J0 = b.take<double>(std::max(W, 1)); t.dlam = b.take<double>(std::max(W, 1));
     t.sigma = b.take<double>(std::max<size_t>(1, (size_t)Rph * W));
     t.sig_abs = b.take<double>(std::max<size_t>(1, (size_t)Sabs * W));
@@ -804,7 +825,8 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
     up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
     up(c, k.prod, c->prod); up(c, k.form, c->form); up(c, k.prow, c->prow);
-    up(c, k.yp, c->yp); up(c, k.yent, c->yent); up(c, k.jp, c->jp); up(c, k.jcol, c->jcol); up(c, k.jrs, c->jrs);
+    up(c, k.yp, c->yp); up(c, k.yent, c->yent); up(c, k.jp, c->jp); up(c, k.jcol, c->jcol); up(c, k.jtp, c->jtp); up(c, k.jrs, c->jrs);
+    up(c, k.jdq, c->jdq);
     up(c, k.J0, c->J0); up(c, k.dlam, c->dlam); up(c, k.sigma, c->sigma); up(c, k.sig_abs, c->sig_abs_c);
     up(c, k.abs_sp, c->abs_sp);
     up(c, k.P, c->P); up(c, k.T, c->T); up(c, k.Kzz, c->Kzz);

@@ -300,8 +300,6 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
     const int wpb = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *rowbuf = sh + (long long)warp * (S + 64);
-    double *vals = rowbuf + S;
-    int *cols = (int *)(vals + 32);
     const double dt = dt_override > 0.0 ? dt_override : ctl->dt;
     for (long long row = (long long)blockIdx.x * wpb + warp; row < (long long)L * S; row += (long long)gridDim.x * wpb) {
         const int k = (int)(row / S), i = (int)(row % S);
@@ -309,32 +307,24 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
         for (int j = lane; j < S; j += 32) rowbuf[j] = 0.0;
         __syncwarp();
         const double *dk = c.d + (long long)k * c.R * 6;
-        int e0 = c.jp[i], e1 = c.jp[i + 1];
-        for (int base = e0; base < e1; base += 32) {
-            int e = base + lane;
-            if (e < e1) {
-                int jc = c.jcol[e];
-                int rs = c.jrs[e];
-                double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
-                cols[lane] = jc & 0xffff;
-                vals[lane] = ((jc >> 16) > 0) ? dv : -dv;      // +d for a reactant row, -d for a product row
+        // each lane owns whole column entries and sums their terms in a fixed order (deterministic)
+        for (int q = c.jp[i] + lane; q < c.jp[i + 1]; q += 32) {
+            double acc = 0.0;
+            for (int t = c.jtp[q]; t < c.jtp[q + 1]; ++t) {
+                const int code = c.jrs[t];
+                const int rs = code >> 1;
+                const double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+                acc += (code & 1) ? dv : -dv;
             }
-            __syncwarp();
-            if (lane == 0) {
-                int cnt = min(32, e1 - base);
-                for (int q = 0; q < cnt; ++q) rowbuf[cols[q]] += vals[q];
-            }
-            __syncwarp();
+            rowbuf[c.jcol[q]] = acc;
         }
+        __syncwarp();
         const double *sk = c.s + (long long)k * S;
         if (lane == 0) {
-            double diag = 1.0 / dt;
-            if (k + 1 < L) diag += c.u[(long long)k * S + i] / c.dz[k];
-            if (k > 0) diag += c.v[(long long)(k - 1) * S + i] / c.dz[k];
-            rowbuf[i] += diag;
+            rowbuf[i] += 1.0 / dt + c.tdg[row];
             if (dout) dout[row] = fmax(fabs(rowbuf[i]), 1.0 / dt);
-            double lov = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
-            double upv = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+            double lov = c.tlo[row];
+            double upv = c.tup[row];
             if (scaled) {
                 if (k > 0) lov *= c.s[(long long)(k - 1) * S + i] / sk[i];
                 if (k + 1 < L) upv *= c.s[(long long)(k + 1) * S + i] / sk[i];
@@ -541,13 +531,14 @@ __global__ void k_diag(Col c, const Ctl *ctl, double *diag)
     int k = (int)(idx / S), i = (int)(idx % S);
     const double *dk = c.d + (long long)k * c.R * 6;
     double acc = 0.0;
-    for (int e = c.jp[i]; e < c.jp[i + 1]; ++e) {
-        int jc = c.jcol[e];
-        if ((jc & 0xffff) != i) continue;
-        int rs = c.jrs[e];
-        double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
-        acc += ((jc >> 16) > 0) ? dv : -dv;
-    }
+    const int q = c.jdq[i];
+    if (q >= 0)
+        for (int t = c.jtp[q]; t < c.jtp[q + 1]; ++t) {
+            const int code = c.jrs[t];
+            const int rs = code >> 1;
+            const double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+            acc += (code & 1) ? dv : -dv;
+        }
     double dg = 1.0 / ctl->dt + acc;
     if (k + 1 < L) dg += c.u[(long long)k * S + i] / c.dz[k];
     if (k > 0) dg += c.v[(long long)(k - 1) * S + i] / c.dz[k];

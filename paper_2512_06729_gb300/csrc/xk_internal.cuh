@@ -28,8 +28,10 @@ struct Col {
     const int *rtype, *reac, *prod, *form, *prow;
     // species-major stoichiometry (residual gather): entries r * 16 + (nu + 8)
     const int *yp, *yent;
-    // row-major Jacobian pattern: per row i, entries (j, coeff) and (r, slot)
-    const int *jp, *jcol, *jrs;
+    // Jacobian pattern by row and column: row i's distinct columns jcol[jp[i] .. jp[i+1]), the terms of
+    // column entry q in jrs[jtp[q] .. jtp[q+1]) as (reaction * 8 + slot) << 1 | (1: +d, 0: -d); jdq[i]
+    // the diagonal entry of row i (-1: none)
+    const int *jp, *jcol, *jtp, *jrs, *jdq;
     // photolysis
     const double *J0, *dlam, *sigma, *sig_abs;   // sig_abs: Sabs x W
     const int *abs_sp;

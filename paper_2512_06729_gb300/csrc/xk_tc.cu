@@ -1,10 +1,11 @@
 // Batched products C = A B on the tcgen05 tensor cores with FP32 accuracy.
 //
 // Each CTA computes one 128 x 128 tile of one task's output.  Warp 0 streams
-// the operands into shared memory with TMA, two stages deep: A (row-major,
+// the operands into shared memory with TMA, three stages deep: A (row-major,
 // i.e. K-major) straight into the 128-byte swizzled layout the tensor core
 // reads; B (row-major, i.e. N-major) as a plain [32 k][128 n] tile, because the
-// TF32 kind reads K-major operands only.  Warps 2-5 split every staged FP32
+// TF32 kind reads K-major operands only (a ring of two such tiles).  Warps 2-9
+// split every staged FP32
 // element x into a TF32 head h (x rounded to nearest at 10 explicit mantissa
 // bits, exact in TF32) and tail l = x - h (exact in FP32, at most 2^-11 |x|),
 // itself rounded to TF32: A in place, B while transposing
@@ -13,7 +14,7 @@
 // the three products A_h B_h + A_h B_l + A_l B_h into one FP32 accumulator in
 // tensor memory (the 3xTF32 scheme: the rounding of the tails and the dropped
 // A_l B_l term leave at most about 3 * 2^-22 of |a||b| per product, a dozen FP32
-// units, far below TF32's 2^-11).  Warps 2-5 then read the accumulator back
+// units, far below TF32's 2^-11).  Warps 2-9 then read the accumulator back
 // (tcgen05.ld) and apply alpha, beta and the column routing of the task.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up records
@@ -31,12 +32,15 @@ namespace xk {
 
 namespace {
 
-constexpr int kStages = 2;
-constexpr int kThreads = 192;                            // warp 0 TMA, warp 1 MMA, warps 2-5 split + epilogue
+constexpr int kStages = 3;
+constexpr int kSplitWarps = 8;                           // warps 2-9: head/tail split, then the epilogue
+constexpr int kSplitThreads = 32 * kSplitWarps;
+constexpr int kThreads = 64 + kSplitThreads;             // warp 0 TMA, warp 1 MMA
 constexpr uint32_t kTileBytes = kTcTileM * kTcStageK * 4; // 16 KB: A tile (128 x 32) or B tile (32 x 128)
-constexpr uint32_t kStageBytes = 5 * kTileBytes;          // A head (TMA lands here), A tail, B as loaded, B head, B tail
+constexpr uint32_t kStageBytes = 4 * kTileBytes;          // A head (TMA lands here), A tail, B head, B tail
+constexpr int kRawB = 2;                                  // B as loaded: a ring of two tiles
 constexpr uint32_t kTmemCols = 128;
-constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr size_t kSmemBytes = kStages * kStageBytes + kRawB * kTileBytes + 1024 + 256;
 constexpr unsigned long long kWaitPolls = 1ull << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -157,7 +161,8 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
     const uint32_t raw_u = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + (((raw_u + 1023u) & ~1023u) - raw_u);     // 1024-byte aligned stages
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bars = sbase + kStages * kStageBytes;
+    const uint32_t rawb = sbase + kStages * kStageBytes;               // B as loaded, ring slot it % kRawB
+    const uint32_t bars = rawb + kRawB * kTileBytes;
     auto full = [&](int s) { return bars + 8u * s; };
     auto split = [&](int s) { return bars + 8u * (kStages + s); };
     auto empty = [&](int s) { return bars + 8u * (2 * kStages + s); };
@@ -183,7 +188,7 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
         abort_sh = 0;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full(s), 1);
-            mbar_init(split(s), 128);
+            mbar_init(split(s), kSplitThreads);
             mbar_init(empty(s), 1);
         }
         mbar_init(accf, 1);
@@ -208,12 +213,18 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
                 const int s = it % kStages;
                 const uint32_t round = (uint32_t)(it / kStages);
                 if (it >= kStages && !mbar_wait(empty(s), (round & 1u) ^ 1u, abort, ctl)) break;
+                // the raw-B slot of this iteration was last read by the split of iteration it - kRawB
+                if (it >= kRawB) {
+                    const int q = it - kRawB;
+                    if (!mbar_wait(split(q % kStages), (uint32_t)(q / kStages) & 1u, abort, ctl)) break;
+                }
                 const TcSeg &g = it < nk0 ? t.seg[0] : t.seg[1];
                 const int kk = (it < nk0 ? it : it - nk0) * kTcStageK;
                 const uint32_t st = sbase + s * kStageBytes;
                 mbar_expect_tx(full(s), 2 * kTileBytes);
                 tma_load_3d(st, maps + 2 * g.amap, g.ax + kk, g.ay + tm * kTcTileM, g.az, full(s));
-                tma_load_3d(st + 2 * kTileBytes, maps + 2 * g.bmap + 1, g.bx + tn * kTcTileN, g.by + kk, g.bz, full(s));
+                tma_load_3d(rawb + (it % kRawB) * kTileBytes, maps + 2 * g.bmap + 1, g.bx + tn * kTcTileN, g.by + kk,
+                            g.bz, full(s));
             }
         }
     } else if (warp == 1) {
@@ -230,8 +241,8 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
                     // K-major: rows of 32 FP32 (128 B), 8-row groups 1024 B apart, K step of 8 = 32 B
                     const uint64_t ah = sw128_desc(st + ks * 32u, 16u, 1024u);
                     const uint64_t al = sw128_desc(st + kTileBytes + ks * 32u, 16u, 1024u);
-                    const uint64_t bh = sw128_desc(st + 3 * kTileBytes + ks * 32u, 16u, 1024u);
-                    const uint64_t bl = sw128_desc(st + 4 * kTileBytes + ks * 32u, 16u, 1024u);
+                    const uint64_t bh = sw128_desc(st + 2 * kTileBytes + ks * 32u, 16u, 1024u);
+                    const uint64_t bl = sw128_desc(st + 3 * kTileBytes + ks * 32u, 16u, 1024u);
                     mma_tf32(tmem, ah, bh, idesc, (it | ks) ? 1u : 0u);
                     mma_tf32(tmem, ah, bl, idesc, 1u);
                     mma_tf32(tmem, al, bh, idesc, 1u);
@@ -253,7 +264,7 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
                 float4 *h = (float4 *)st;
                 float4 *l = (float4 *)(st + kTileBytes);
 #pragma unroll 4
-                for (int i = ct; i < (int)(kTileBytes / 16); i += 128) {
+                for (int i = ct; i < (int)(kTileBytes / 16); i += kSplitThreads) {
                     float4 v = h[i];
                     float4 a = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
                     h[i] = a;
@@ -261,13 +272,14 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
                                        tf32_round(v.w - a.w));
                 }
             }
-            {   // B: thread ct takes column n = ct of the [32 k][128 n] tile and writes row n of the
-                // K-major tiles, 16-byte chunk c (k = 4c .. 4c+3) at chunk c ^ (n mod 8)
-                const float *b = (const float *)(st + 2 * kTileBytes);
-                uint8_t *bh = st + 3 * kTileBytes, *bl = st + 4 * kTileBytes;
-                const int n = ct;
+            {   // B: thread ct takes column n = ct mod 128 of the [32 k][128 n] tile, half of its chunks, and
+                // writes row n of the K-major tiles, 16-byte chunk c (k = 4c .. 4c+3) at chunk c ^ (n mod 8)
+                const float *b = (const float *)(smem + kStages * kStageBytes + (it % kRawB) * kTileBytes);
+                uint8_t *bh = st + 2 * kTileBytes, *bl = st + 3 * kTileBytes;
+                const int n = ct & (kTcTileN - 1);
+                const int c0 = (ct / kTcTileN) * (8 * kTcTileN / kSplitThreads);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = c0; c < c0 + 8 * kTcTileN / kSplitThreads; ++c) {
                     float4 v = make_float4(b[(4 * c) * kTcTileN + n], b[(4 * c + 1) * kTcTileN + n],
                                            b[(4 * c + 2) * kTcTileN + n], b[(4 * c + 3) * kTcTileN + n]);
                     float4 a = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
@@ -280,13 +292,16 @@ k_tc_gemm(const TcTask *__restrict__ tasks, int ntasks, const CUtensorMap *__res
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(split(s));
         }
-        // epilogue: TMEM lanes 32 (warp % 4) .. +31 hold this warp's rows
+        // epilogue: TMEM lanes 32 (warp % 4) .. +31 hold this warp's rows; the warps sharing those lanes
+        // take different column ranges
         const bool ok = mbar_wait(accf, 0u, abort, ctl);
         tc_fence_after();
         const int ew = warp & 3;
+        const int cpart = (warp - 2) / 4;
+        constexpr int kColsPerWarp = kTcTileN * 4 / kSplitWarps;
         const int row = tm * kTcTileM + ew * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTcTileN; c0 += 32) {
+        for (int c0 = cpart * kColsPerWarp; c0 < (cpart + 1) * kColsPerWarp; c0 += 32) {
             uint32_t r[32];
             tmem_ld32(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0, r);
             const int n = tn * kTcTileN + c0;
