@@ -296,6 +296,10 @@ XK_API int xk_batch_step(xk_batch *batch, int nsteps);
 XK_API int xk_batch_poll(xk_batch *batch, int slot, xk_run_info *info, int *finished, int *status);
 XK_API const char *xk_batch_last_error(xk_batch *batch);
 XK_API int xk_batch_submit(xk_batch *batch, int slot, int nsteps);
+/* Admission check before any allocation: *fits = 1 when a column whose
+ * workspace needs `bytes` (xk_workspace_bytes) would be admitted now (a slot is
+ * free and the bytes fit the remaining budget), 0 otherwise.  Host only. */
+XK_API int xk_batch_fits(xk_batch *batch, size_t bytes, int *fits);
 XK_API int xk_batch_query(xk_batch *batch, int slot, int *done);
 
 /* ---- block solve without any device allocation ----

@@ -1327,6 +1327,15 @@ int xk_batch_step(xk_batch *b, int nsteps)
 
 const char *xk_batch_last_error(xk_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
+int xk_batch_fits(xk_batch *b, size_t bytes, int *fits)
+{
+    if (!b || !fits) return XK_EINVAL;
+    bool slot = false;
+    for (const auto &s : b->slots) slot |= s.ctx == nullptr;
+    *fits = (slot && b->used + bytes <= b->budget) ? 1 : 0;
+    return XK_OK;
+}
+
 int xk_batch_submit(xk_batch *b, int slot, int nsteps)
 {
     if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot].ctx || nsteps <= 0) return XK_EINVAL;

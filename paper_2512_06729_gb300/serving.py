@@ -112,10 +112,16 @@ class Server:
                 break
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.pop(0))
-            # admit in arrival order while slots and budget allow
+            # admit in arrival order while slots and budget allow: the footprint is checked against
+            # the batch before the column's workspace is allocated
             while waiting:
                 req = waiting[0]
-                col = xk.Column(req.problem, self.precision, device=self.device, **self.column_kw)
+                col = xk.Column(req.problem, self.precision, device=self.device, allocate=False, **self.column_kw)
+                if not self.batch.fits(col.workspace_bytes):
+                    col.close()
+                    del col
+                    break
+                col.allocate()
                 col.set_mixing_ratios(req.problem.f0)
                 slot = self.batch.add(col, req.dt0)
                 if slot is None:

@@ -97,6 +97,7 @@ SIGNATURES = {
     "xk_batch_last_error": (C.c_char_p, [_vp]),
     "xk_batch_submit": (C.c_int, [_vp, C.c_int, C.c_int]),
     "xk_batch_query": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
+    "xk_batch_fits": (C.c_int, [_vp, C.c_size_t, C.POINTER(C.c_int)]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
     "xk_hold_next_barrier": (C.c_int, [_vp]),
@@ -160,7 +161,9 @@ def tc_gemm(A, B, C=None, alpha=1.0, beta=0.0):
 class Column:
     """One atmospheric column on one GPU: owns an xk context and its workspace."""
 
-    def __init__(self, prob, precision="fp64", device=0, stream=None, **cfg_kw):
+    def __init__(self, prob, precision="fp64", device=0, stream=None, allocate=True, **cfg_kw):
+        """With allocate=False only the context and its inputs are set up (workspace_bytes is then the
+        device footprint); allocate() creates the workspace."""
         import torch
         self._torch = torch
         self.prob = prob
@@ -194,7 +197,15 @@ class Column:
         nbytes = C.c_size_t()
         self._call("xk_workspace_bytes", C.byref(nbytes))
         self.workspace_bytes = int(nbytes.value)
-        self.ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws = None
+        if allocate:
+            self.allocate()
+
+    def allocate(self):
+        """Create the device workspace (workspace_bytes) and upload the inputs."""
+        if self.ws is not None:
+            return
+        self.ws = self._torch.empty(self.workspace_bytes + 256, dtype=self._torch.uint8, device=self.device)
         base = self.ws.data_ptr()
         aligned = (base + 255) & ~255
         self._call("xk_set_workspace", _vp(aligned), C.c_size_t(self.workspace_bytes))
@@ -370,6 +381,14 @@ class Batch:
             raise XkError("xk_batch_create", rc, "")
         self.h = h
         self.cols = {}
+
+    def fits(self, nbytes):
+        """Whether a column of this device footprint would be admitted now (no allocation)."""
+        ok = C.c_int(0)
+        rc = lib().xk_batch_fits(self.h, C.c_size_t(int(nbytes)), C.byref(ok))
+        if rc != XK_OK:
+            raise XkError("xk_batch_fits", rc, "")
+        return bool(ok.value)
 
     def add(self, col, dt0=1e-8):
         """Admit a column; returns the slot, or None when it does not fit (footprint or slots)."""

@@ -70,12 +70,17 @@ def test_batch_results_equal_alone(precision, largest_first):
 def test_batch_admission_by_footprint():
     p = synth.small_column()
     c1 = xk.Column(p, "fp64")
-    c2 = xk.Column(p, "fp64")
+    c2 = xk.Column(p, "fp64", allocate=False)
+    assert c2.ws is None and c2.workspace_bytes == c1.workspace_bytes   # footprint known, nothing allocated
     b = xk.Batch(int(c1.workspace_bytes * 1.5), 4)
+    assert b.fits(c2.workspace_bytes)
     s1 = b.add(c1)
     assert s1 is not None
-    assert b.add(c2) is None              # the second footprint does not fit
+    assert not b.fits(c2.workspace_bytes)  # the second footprint does not fit: checked before allocating
+    c2.allocate()
+    assert b.add(c2) is None
     b.remove(s1)
+    assert b.fits(c2.workspace_bytes)
     assert b.add(c2) is not None          # admitted once the first one left
     b.close()
 

@@ -8,11 +8,22 @@ import numpy as np
 from paper_2512_06729_gb300 import serving
 
 
+ALLOCATED = []
+
+
 class FakeColumn:
-    def __init__(self, prob, precision, device=0, **kw):
+    def __init__(self, prob, precision, device=0, allocate=True, **kw):
         self.prob = prob
-        self.bytes = prob.S * 100
+        self.workspace_bytes = prob.S * 100
+        self.bytes = self.workspace_bytes
         self.closed = False
+        self.allocated = False
+        if allocate:
+            self.allocate()
+
+    def allocate(self):
+        self.allocated = True
+        ALLOCATED.append(self.prob.name)
 
     def set_mixing_ratios(self, f):
         pass
@@ -30,8 +41,12 @@ class FakeBatch:
         self.active = {}
         self.admissions = []
 
+    def fits(self, nbytes):
+        return len(self.active) < self.slots and self.used + nbytes <= self.budget
+
     def add(self, col, dt0=1e-8):
-        if len(self.active) >= self.slots or self.used + col.bytes > self.budget:
+        assert col.allocated
+        if not self.fits(col.bytes):
             return None
         slot = min(set(range(self.slots)) - set(self.active))
         self.active[slot] = [col, 0]
@@ -76,9 +91,12 @@ def test_admission_order_budget_and_latency(monkeypatch):
         return t[0]
 
     srv = serving.Server(budget_bytes=16000, max_slots=2, chunk=2)
+    ALLOCATED.clear()
     res = srv.run(reqs, clock=clock)
     # arrival order is kept; never more than 2 slots or 16000 bytes at once
     assert srv.batch.admissions == ["r0", "r1", "r2", "r3", "r4"]
+    # a workspace is allocated only for a column the batch admits: once per request
+    assert ALLOCATED == ["r0", "r1", "r2", "r3", "r4"]
     assert all(r.converged for r in res)
     assert all(r.finished > r.admitted >= r.arrival for r in res)
     s = serving.summarize(res, t[0])
