@@ -114,13 +114,19 @@ typedef struct {
                              gmres_tol.  0 = direct solve only */
     int fp32_bcr;         /* mixed mode: 1 factors the FP32 preconditioner by block cyclic reduction of
                              the layers (odd layers eliminated first, level by level) with every dense
-                             product and block inversion on the tensor cores (TF32 head/tail split,
-                             FP32 accuracy; the default); 0 by the chain of block inversions
+                             product on the tensor cores (TF32 head/tail split, FP32 accuracy) and the
+                             leaf block inversions in FP32 on the CUDA cores (the default); 0 by the
+                             chain of block inversions
                              (cluster_size, panel_width, twisted, fp32_pivoting then apply) */
     long long wait_polls; /* every device-side wait on other CTAs (the grid barriers of the FP64
                              factorization) gives up after this many polls, about 0.1 us each, and
                              the call returns XK_ETIMEOUT with the context still usable (0: 2^24
                              polls, one to two seconds) */
+    int use_graphs;       /* 1 (default): xk_run_to_steady and the batch calls capture a chunk of
+                             controlled steps (every kernel of every step, with the device-side
+                             gating of FGMRES iterations and of the FP64 route) in a CUDA graph once
+                             and replay it, one graph launch per chunk; 0 launches every kernel from
+                             the host.  Tracing (xk_profile) launches from the host either way. */
 } xk_config;
 
 typedef struct {
@@ -388,6 +394,11 @@ XK_API int xk_hold_next_barrier(xk_ctx *ctx);
  * contexts of the process; kernels that exit at once because their solve or
  * step has finished are counted too). */
 XK_API long long xk_launch_count(void);
+
+/* Number of CUDA graph launches (captured chunks of steps, see cfg.use_graphs)
+ * since the library was loaded; each replay also adds its kernel nodes to
+ * xk_launch_count. */
+XK_API long long xk_graph_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -16,6 +17,14 @@
 #include "xk_internal.cuh"
 
 using namespace xk;
+
+// A chunk of controlled steps captured once and replayed with one graph launch.
+struct StepGraph {
+    int steps = 0;
+    bool ctl_copy = false;           // ends with the copy of the control block to its host mirror
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;           // kernel nodes of one replay
+};
 
 struct xk_ctx {
     xk_config cfg;
@@ -63,6 +72,10 @@ struct xk_ctx {
     BcrPlan bcr;           // block cyclic reduction on the tensor cores (mixed path, fp32_bcr)
     bool use_bcr = false;
     bool ready = false;
+    // captured chunks of controlled steps (cfg.use_graphs), dropped whenever a plan, the workspace
+    // or the batch slot changes
+    std::vector<StepGraph> graphs;
+    cudaStream_t cap_st = nullptr;   // capture stream (the legacy default stream cannot be captured)
     // tracing
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[XK_PH_COUNT];
@@ -599,6 +612,120 @@ int read_ctl(xk_ctx *c, Ctl *out)
     return XK_OK;
 }
 
+// ---------------------------------------------------------------- CUDA graphs of steps
+
+std::atomic<long long> g_graph_launches{0};
+
+void drop_graphs(xk_ctx *c)
+{
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// Replay captured steps (tracing times each phase from the host instead).
+bool graphs_on(const xk_ctx *c) { return c->cfg.use_graphs != 0 && !c->prof; }
+
+// Rate coefficients depend on the atmosphere only: evaluated outside any graph, once.
+void ensure_rates(xk_ctx *c)
+{
+    if (c->rates_valid) return;
+    launch_rates(c->col, c->st);
+    c->rates_valid = true;
+}
+
+// Enqueue `steps` controlled steps of c, and with ctl_copy the copy of its control block to the
+// host mirror, into a graph being captured on the stream c->st.
+int enqueue_chunk(xk_ctx *c, int steps, bool ctl_copy)
+{
+    for (int i = 0; i < steps; ++i) {
+        int rc = enqueue_step(c);
+        if (rc) return rc;
+    }
+    if (ctl_copy) cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+    return XK_OK;
+}
+
+// End a capture begun on st and instantiate it; the kernels enqueued since n0 are nodes, not
+// launches, until the graph is replayed.
+int finish_capture(xk_ctx *c, cudaStream_t st, int rc, long long n0, cudaGraphExec_t *exec, long long *kernels)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    *kernels = launches() - n0;
+    count_launches(-*kernels);
+    *exec = nullptr;
+    if (rc != XK_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != XK_OK ? rc : fail(c, XK_ECUDA, "step capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        cudaGetLastError();
+        return fail(c, XK_ECUDA, "step graph instantiation: %s", cudaGetErrorString(e));
+    }
+    return XK_OK;
+}
+
+// The context's graph of `steps` steps (captured on first use), or null with *rc set.
+StepGraph *step_graph(xk_ctx *c, int steps, bool ctl_copy, int *rc)
+{
+    *rc = XK_OK;
+    for (auto &g : c->graphs)
+        if (g.steps == steps && g.ctl_copy == ctl_copy) return &g;
+    ensure_rates(c);
+    if (!c->cap_st && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess) {
+        *rc = cuda_check(c, "capture stream");
+        return nullptr;
+    }
+    // captured on a stream of its own, replayed on the context's
+    cudaStream_t own = c->st;
+    c->st = c->cap_st;
+    const long long n0 = launches();
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        c->st = own;
+        *rc = fail(c, XK_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+        return nullptr;
+    }
+    int erc = enqueue_chunk(c, steps, ctl_copy);
+    StepGraph g;
+    g.steps = steps;
+    g.ctl_copy = ctl_copy;
+    *rc = finish_capture(c, c->st, erc, n0, &g.exec, &g.kernels);
+    c->st = own;
+    if (*rc) return nullptr;
+    c->graphs.push_back(g);
+    return &c->graphs.back();
+}
+
+int replay(xk_ctx *c, const StepGraph &g, cudaStream_t st)
+{
+    cudaError_t e = cudaGraphLaunch(g.exec, st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    count_launches(g.kernels);
+    g_graph_launches.fetch_add(1, std::memory_order_relaxed);
+    return XK_OK;
+}
+
+// `steps` controlled steps on c->st: one graph launch when graphs are on, else launched one by one.
+int run_steps(xk_ctx *c, int steps, bool ctl_copy)
+{
+    if (!graphs_on(c)) {
+        int rc = enqueue_chunk(c, steps, false);
+        if (!rc && ctl_copy) cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+        return rc;
+    }
+    ensure_rates(c);
+    int rc;
+    StepGraph *g = step_graph(c, steps, ctl_copy, &rc);
+    if (!g) return rc;
+    return replay(c, *g, c->st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -619,6 +746,7 @@ int xk_config_init(xk_config *cfg)
     cfg->refine_max_iter = 10;
     cfg->fp32_bcr = 1;
     cfg->wait_polls = 0;
+    cfg->use_graphs = 1;
     return XK_OK;
 }
 
@@ -653,6 +781,8 @@ int xk_create(xk_ctx **out, const xk_config *cfg)
 int xk_destroy(xk_ctx *ctx)
 {
     if (!ctx) return XK_EINVAL;
+    drop_graphs(ctx);
+    if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
     for (auto &v : ctx->ev)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
@@ -781,6 +911,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     if (!dptr || bytes < need) return fail(c, XK_ENOMEM, "workspace of %zu bytes, need %zu", bytes, need);
     if (((uintptr_t)dptr) & 255) return fail(c, XK_EINVAL, "workspace must be 256-byte aligned");
     cudaSetDevice(c->cfg.device);
+    drop_graphs(c);
     c->ws = (char *)dptr;
     c->ws_bytes = bytes;
     layout(c, c->ws);
@@ -911,7 +1042,7 @@ int xk_step(xk_ctx *c, double dt, xk_step_info *info)
     if (dt > 0.0) h.dt = dt;
     *c->ctl_host = h;
     cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
-    if ((rc = enqueue_step(c))) return rc;
+    if ((rc = run_steps(c, 1, false))) return rc;
     if ((rc = read_ctl(c, &h))) return rc;
     fill_step_info(h, info);
     if (h.err_timeout) return timed_out(c);
@@ -938,8 +1069,7 @@ int xk_run_to_steady(xk_ctx *c, double dt0, int max_steps, xk_run_info *info)
     const int chunk = 16;
     while (enq < max_steps) {
         int nrun = std::min(chunk, max_steps - enq);
-        for (int i = 0; i < nrun; ++i)
-            if ((rc = enqueue_step(c))) return rc;
+        if ((rc = run_steps(c, nrun, false))) return rc;
         enq += nrun;
         if ((rc = read_ctl(c, &h))) return rc;
         if (h.finished) break;
@@ -1157,6 +1287,8 @@ int xk_factor_work(xk_ctx *c, double *mma_flops, double *leaf_flops)
 
 long long xk_launch_count(void) { return launches(); }
 
+long long xk_graph_launch_count(void) { return g_graph_launches.load(std::memory_order_relaxed); }
+
 // ---------------------------------------------------------------- batches
 
 struct BatchSlot {
@@ -1179,7 +1311,75 @@ struct xk_batch {
     int max_slots = 1;
     std::vector<BatchSlot> slots;
     std::string err;
+    // one round of xk_batch_step for every unfinished column, captured as one graph: a branch per
+    // column from a fork on `origin`, joined back there
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t round = nullptr;
+    std::vector<int> round_slots;
+    int round_steps = 0;
+    long long round_kernels = 0;
 };
+
+namespace {
+
+void drop_round(xk_batch *b)
+{
+    if (b->round) cudaGraphExecDestroy(b->round);
+    b->round = nullptr;
+    b->round_slots.clear();
+    b->round_steps = 0;
+    b->round_kernels = 0;
+}
+
+// Capture nsteps steps of every listed slot's column, each on its slot's stream, into b->round.
+int capture_round(xk_batch *b, const std::vector<int> &live, int nsteps)
+{
+    drop_round(b);
+    cudaError_t e = cudaSuccess;
+    if (!b->origin) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && b->joins.size() < b->slots.size()) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->joins.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        b->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return XK_ECUDA;
+    }
+    for (int i : live) ensure_rates(b->slots[i].ctx);
+    const long long n0 = launches();
+    e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch capture: ") + cudaGetErrorString(e);
+        return XK_ECUDA;
+    }
+    cudaEventRecord(b->fork, b->origin);
+    int rc = XK_OK;
+    xk_ctx *bad = nullptr;
+    for (int i : live) {
+        BatchSlot &s = b->slots[i];
+        cudaStreamWaitEvent(s.st, b->fork, 0);
+        if (rc == XK_OK && (rc = enqueue_chunk(s.ctx, nsteps, true)) != XK_OK) bad = s.ctx;
+        cudaEventRecord(b->joins[i], s.st);
+        cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+    }
+    xk_ctx *owner = bad ? bad : b->slots[live[0]].ctx;
+    rc = finish_capture(owner, b->origin, rc, n0, &b->round, &b->round_kernels);
+    if (rc) {
+        b->err = owner->err;
+        drop_round(b);
+        return rc;
+    }
+    b->round_slots = live;
+    b->round_steps = nsteps;
+    return XK_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1207,6 +1407,8 @@ int xk_batch_remove(xk_batch *b, int slot)
     BatchSlot &s = b->slots[slot];
     cudaSetDevice(b->device);
     cudaStreamSynchronize(s.st);
+    drop_graphs(s.ctx);
+    drop_round(b);
     s.ctx->st = s.saved_st;
     s.ctx->plan = s.saved_plan;
     s.ctx->plan64 = s.saved_plan64;
@@ -1223,6 +1425,10 @@ int xk_batch_destroy(xk_batch *b)
     if (!b) return XK_EINVAL;
     for (int i = 0; i < (int)b->slots.size(); ++i)
         if (b->slots[i].ctx) xk_batch_remove(b, i);
+    drop_round(b);
+    for (auto ev : b->joins) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
     delete b;
     return XK_OK;
 }
@@ -1265,6 +1471,8 @@ int xk_batch_add(xk_batch *b, xk_ctx *c, double dt0, int *slot)
     }
     set_preview(c, &p64);
     if (sz == 8) set_preview(c, &p);
+    drop_graphs(c);
+    drop_round(b);
     s.ctx = c;
     s.saved_st = c->st;
     s.saved_plan = c->plan;
@@ -1300,28 +1508,55 @@ int xk_batch_step(xk_batch *b, int nsteps)
             b->err = "a slot has submitted steps in flight (query it first)";
             return XK_EINVAL;
         }
+    std::vector<int> live;
+    bool graphs = true;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i].ctx && !b->slots[i].finished) {
+            live.push_back(i);
+            graphs = graphs && graphs_on(b->slots[i].ctx);
+        }
+    if (live.empty()) return XK_OK;
+    if (graphs) {
+        // one graph launch for the whole round, captured again when the set of columns changes
+        if (!b->round || b->round_slots != live || b->round_steps != nsteps) {
+            int rc = capture_round(b, live, nsteps);
+            if (rc) return rc;
+        }
+        for (int i : live) ensure_rates(b->slots[i].ctx);
+        cudaError_t e = cudaGraphLaunch(b->round, b->origin);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->origin);
+        if (e != cudaSuccess) {
+            b->err = std::string("batch round: ") + cudaGetErrorString(e);
+            return XK_ECUDA;
+        }
+        count_launches(b->round_kernels);
+        g_graph_launches.fetch_add(1, std::memory_order_relaxed);
+        for (int i : live) b->slots[i].finished = b->slots[i].ctx->ctl_host->finished != 0;
+        return cuda_check(nullptr, "batch_step");
+    }
     for (int k = 0; k < nsteps; ++k)
-        for (auto &s : b->slots)
-            if (s.ctx && !s.finished) {
-                int rc = enqueue_step(s.ctx);
-                if (rc) {
-                    b->err = s.ctx->err;
-                    return rc;
-                }
-            }
-    for (auto &s : b->slots)
-        if (s.ctx && !s.finished)
-            cudaMemcpyAsync(s.ctx->ctl_host, s.ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s.st);
-    for (auto &s : b->slots)
-        if (s.ctx && !s.finished) {
-            cudaError_t e = cudaStreamSynchronize(s.st);
-            if (e != cudaSuccess) {
-                int rc = fail(s.ctx, XK_ECUDA, "batch step: %s", cudaGetErrorString(e));
+        for (int i : live) {
+            BatchSlot &s = b->slots[i];
+            int rc = enqueue_step(s.ctx);
+            if (rc) {
                 b->err = s.ctx->err;
                 return rc;
             }
-            s.finished = s.ctx->ctl_host->finished != 0;
         }
+    for (int i : live) {
+        BatchSlot &s = b->slots[i];
+        cudaMemcpyAsync(s.ctx->ctl_host, s.ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s.st);
+    }
+    for (int i : live) {
+        BatchSlot &s = b->slots[i];
+        cudaError_t e = cudaStreamSynchronize(s.st);
+        if (e != cudaSuccess) {
+            int rc = fail(s.ctx, XK_ECUDA, "batch step: %s", cudaGetErrorString(e));
+            b->err = s.ctx->err;
+            return rc;
+        }
+        s.finished = s.ctx->ctl_host->finished != 0;
+    }
     return cuda_check(nullptr, "batch_step");
 }
 
@@ -1347,16 +1582,13 @@ int xk_batch_submit(xk_batch *b, int slot, int nsteps)
     if (s.finished) return XK_OK;
     cudaSetDevice(b->device);
     b->err.clear();
-    for (int k = 0; k < nsteps; ++k) {
-        int rc = enqueue_step(s.ctx);
-        if (rc) {
-            b->err = s.ctx->err;
-            return rc;
-        }
+    int rc = run_steps(s.ctx, nsteps, true);
+    if (rc) {
+        b->err = s.ctx->err;
+        return rc;
     }
-    cudaMemcpyAsync(s.ctx->ctl_host, s.ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s.st);
     if (cudaEventRecord(s.ev, s.st) != cudaSuccess) {
-        int rc = fail(s.ctx, XK_ECUDA, "batch submit: %s", cudaGetErrorString(cudaGetLastError()));
+        rc = fail(s.ctx, XK_ECUDA, "batch submit: %s", cudaGetErrorString(cudaGetLastError()));
         b->err = s.ctx->err;
         return rc;
     }

@@ -37,7 +37,7 @@ class Config(C.Structure):
         ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("reuse_max_iters", C.c_int),
         ("twisted", C.c_int),
         ("fp64_panel", C.c_int), ("refine_max_iter", C.c_int), ("fp32_bcr", C.c_int),
-        ("wait_polls", C.c_longlong),
+        ("wait_polls", C.c_longlong), ("use_graphs", C.c_int),
     ]
 
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "xk_batch_fits": (C.c_int, [_vp, C.c_size_t, C.POINTER(C.c_int)]),
     "xk_profile": (C.c_int, [_vp, C.c_int]),
     "xk_launch_count": (C.c_longlong, []),
+    "xk_graph_launch_count": (C.c_longlong, []),
     "xk_hold_next_barrier": (C.c_int, [_vp]),
     "xk_tc_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_float, C.c_float,
                              _vp]),
@@ -337,6 +338,10 @@ class Column:
     @staticmethod
     def lib_launches():
         return int(lib().xk_launch_count())
+
+    @staticmethod
+    def graph_launches():
+        return int(lib().xk_graph_launch_count())
 
     def profile(self, enable=True):
         self._call("xk_profile", 1 if enable else 0)
