@@ -512,6 +512,14 @@ def run_ours(args):
             errs = err_vs_oracle(prob, tuning)
         if not args.no_steady:
             steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
+    batch = serving_obj = parcel = None
+    if rank == 0 and ws == 1:
+        if not args.no_batch:
+            batch = batch_object(args.columns, steps=5, warmup=3, tune=not args.no_tune)
+        if not args.no_serving:
+            serving_obj = serving_object(args.requests, args.rate, args.slots, args.serving_deadline)
+        if not args.no_parcel:
+            parcel = parcel_object(live, cpu=not args.no_cpu)
     if rank == 0:
         ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items() if v[1]}
         ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items() if v[1]}
@@ -542,6 +550,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": L * S * 8},
             "gpu_launches": int(mixed["launches"]),
             "graph_launches": int(mixed["graphs"]),
+            "batch": batch,
+            "serving": serving_obj,
+            "parcel": parcel,
             "traced": {"ms_per_step": mixed["ms_traced"] / mixed["steps_traced"],
                        "note": "the next steps with every kernel launched from the host between CUDA event "
                                "pairs (phases_ms comes from this run)"},
@@ -568,90 +579,202 @@ def batch_problems(n=64, seed=0):
     return out
 
 
-def run_batch(args):
-    """Batched uneven columns: column-steps/s of the whole batch (mixed precision)."""
+def batch_object(columns=64, steps=5, warmup=3, tune=True, budget=200 << 30):
+    """Config-3 batch: `columns` uneven columns advanced together, every round (one controlled step
+    of every unfinished column) replayed as one CUDA graph with a branch per column.  Returns the
+    bench's `batch` object: column-steps/s of the whole batch over `steps` timed rounds."""
     import torch
     from paper_2512_06729_gb300 import autotune
-    from paper_2512_06729_gb300 import build as xkbuild
     from paper_2512_06729_gb300 import xk
-    xkbuild.build()
-    probs = batch_problems(args.columns)
-    tuning = {}
+    probs = batch_problems(columns)
+    tuning, tables = {}, {}
+    t_tune = time.perf_counter()
     for p in probs:
-        if p.S not in tuning:
-            tuning[p.S] = {} if args.no_tune else (autotune.tuned(p.S, "mixed") or autotune.tune(p, "mixed")[0])
-    b = xk.Batch(200 << 30, len(probs))
+        if p.S in tuning:
+            continue
+        if not tune:
+            tuning[p.S] = {}
+            continue
+        got = autotune.tuned(p.S, "mixed")
+        if not got:
+            got, table = autotune.tune(p, "mixed")
+            tables[str(p.S)] = [[params, round(ms, 4)] for ms, params in table]
+        tuning[p.S] = got
+    t_tune = time.perf_counter() - t_tune
+    b = xk.Batch(budget, len(probs))
     cols = []
+    footprint = 0
     for p in probs:
         kw = {k: v for k, v in tuning[p.S].items() if k != "factor_ctas"}   # the batch shares the SMs
-        c = xk.Column(p, "mixed", gmres_restart=10, gmres_max_iter=10, reuse_factorization=1, **kw)
+        c = xk.Column(p, "mixed", reuse_factorization=1, allocate=False, **kw)
+        if not b.fits(c.workspace_bytes):
+            raise RuntimeError(f"batch budget exhausted at column {len(cols)}")
+        c.allocate()
         c.set_mixing_ratios(p.f0)
         assert b.add(c, 1e-8) is not None
+        footprint += c.workspace_bytes
         cols.append(c)
-    for _ in range(args.warmup):
+    t_cap = time.perf_counter()
+    b.step(1)                       # the first round captures the round's graph
+    torch.cuda.synchronize()
+    t_cap = time.perf_counter() - t_cap
+    for _ in range(max(warmup - 1, 0)):
         b.step(1)
     torch.cuda.synchronize()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n0 = xk.Column.lib_launches()
+    n0, g0 = xk.Column.lib_launches(), xk.Column.graph_launches()
     with ClockSampler(0) as cs:
-        start.record()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.step(1)
-        t1 = time.perf_counter()
-        end.record()
-        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
     launches = xk.Column.lib_launches() - n0
-    wall = t1 - t0
-    col_steps = len(probs) * args.steps
+    graphs = xk.Column.graph_launches() - g0
+    done = sum(1 for i in range(len(cols)) if b.poll(i)[1])
     sizes = {}
     for p in probs:
-        sizes[p.S] = sizes.get(p.S, 0) + 1
-    line = {
-        "metric": "column-steps/s, 64 uneven columns (S in {96, 250, 594}, L 80..200) batched on one GPU",
-        "value": col_steps / wall, "unit": "column-steps/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "batch-64-uneven", "columns": len(probs), "species_counts": sizes,
-                   "layers_total": int(sum(p.L for p in probs)), "precision": "mixed, FP64 reuse",
-                   "streams": "one per column", "factor_ctas_per_column": max(1, 152 // len(probs)),
-                   "factorization": {str(k): v for k, v in tuning.items()}},
-        "gpu_launches": int(launches), "clocks": cs.summary(),
-    }
-    print(json.dumps(line), flush=True)
+        sizes[str(p.S)] = sizes.get(str(p.S), 0) + 1
     b.close()
+    for c in cols:
+        c.close()
+    del cols
+    torch.cuda.empty_cache()
+    col_steps = len(probs) * steps
+    return {
+        "metric": f"column-steps/s, {len(probs)} uneven columns (S in {{96, 250, 594}}, L 80..200) on one GPU",
+        "value": col_steps / wall, "unit": "column-steps/s", "rounds": steps, "warmup": warmup,
+        "ms_per_round": wall * 1e3 / steps, "columns": len(probs), "species_counts": sizes,
+        "layers_total": int(sum(p.L for p in probs)), "footprint_gb": footprint / 1e9,
+        "precision": "mixed (FP32 factorization, FP64 FGMRES, FP64 reuse)",
+        "graph_launches_per_round": graphs / steps, "kernel_nodes_per_round": launches / steps,
+        "first_round_s_with_capture": t_cap, "tune_s": t_tune, "finished_columns": done,
+        "factorization": {str(k): v for k, v in tuning.items()}, "tuning_ms_per_layer": tables or None,
+        "clocks": cs.summary(),
+    }
+
+
+def run_batch(args):
+    """Batched uneven columns: column-steps/s of the whole batch (mixed precision)."""
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    obj = batch_object(args.columns, args.steps, args.warmup, tune=not args.no_tune)
+    line = {"metric": obj["metric"], "value": obj["value"], "unit": obj["unit"], "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": obj["ms_per_round"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "batch-64-uneven"}, "batch": obj,
+            "gpu_launches": int(obj["kernel_nodes_per_round"] * args.steps), "clocks": obj["clocks"]}
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_object(requests=16, rate=0.25, slots=16, deadline=120.0, precisions=("mixed", "fp64"), seed=0):
+    """Config-4 serving: Poisson-arriving steady-state requests from the planet-parameter sweep
+    (60/30/10 % of 96/250/594 species on 150 layers), admitted by HBM footprint and kept on the
+    device, served once by the mixed path and once by the plain FP64 path on the same requests.
+    Returns the bench's `serving` object (p50/p99 time to steady state of the finished requests,
+    solves/s, and how many did not finish before the deadline)."""
+    import torch
+    from paper_2512_06729_gb300 import serving
+    reqs = serving.sweep_requests(requests, rate, seed=seed)
+    out = {"requests": requests, "rate_per_s": rate, "slots": slots, "deadline_s": deadline, "layers": 150,
+           "species": [r.problem.S for r in reqs]}
+    for prec in precisions:
+        kw = dict(reuse_factorization=1) if prec == "mixed" else {}
+        srv = serving.Server(200 << 30, slots, precision=prec, chunk=8, column_kw=kw)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, deadline=deadline)
+        wall = time.perf_counter() - t0
+        srv.close()
+        torch.cuda.empty_cache()
+        summ = serving.summarize(res, wall)
+        summ["wall_s"] = wall
+        summ["unfinished"] = summ["requests"] - summ["finished"]
+        summ["per_request"] = [{"S": q.problem.S, "arrival_s": round(x.arrival, 3),
+                                "latency_s": None if x.finished is None else round(x.latency, 3),
+                                "steps": x.steps, "fp64_steps": x.fp64_steps} for q, x in zip(reqs, res)]
+        out[prec] = summ
+    if "mixed" in out and "fp64" in out:
+        fm, ff = out["mixed"]["solves_per_s"], out["fp64"]["solves_per_s"]
+        out["solves_per_s_mixed_over_fp64"] = fm / ff if ff > 0 else None
+    return out
 
 
 def run_serving(args):
     """Continuous batching of steady-state requests from a planet-parameter sweep."""
-    import torch
     from paper_2512_06729_gb300 import build as xkbuild
-    from paper_2512_06729_gb300 import serving
     xkbuild.build()
-    reqs = serving.sweep_requests(args.requests, args.rate, seed=0)
-    srv = serving.Server(200 << 30, args.slots, precision="mixed", chunk=8,
-                         column_kw=dict(reuse_factorization=1, gmres_restart=10, gmres_max_iter=10))
-    t0 = time.perf_counter()
-    res = srv.run(reqs, deadline=args.time_limit)
-    wall = time.perf_counter() - t0
-    srv.close()
-    summ = serving.summarize(res, wall)
+    obj = serving_object(args.requests, args.rate, args.slots, args.time_limit,
+                         precisions=tuple(args.variants.split(",")))
+    first = obj[args.variants.split(",")[0]]
     line = {
         "metric": "serving: time to steady state p50/p99 (s) and solves/s, sweep requests 60/30/10 % of 96/250/594 sp",
-        "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": summ["steps_total"],
+        "value": first["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": first["steps_total"],
         "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "serving-sweep", "requests": args.requests, "rate_per_s": args.rate,
-                   "slots": args.slots, "layers": 150, "deadline_s": args.time_limit,
-                   "species": [r.problem.S for r in reqs]},
-        "per_request": [{"S": r.problem.S, "arrival_s": round(x.arrival, 3),
-                         "latency_s": None if x.finished is None else round(x.latency, 3),
-                         "steps": x.steps, "fp64_steps": x.fp64_steps} for r, x in zip(reqs, res)],
-        "serving": summ,
+        "dtype": "f64+f32", "data": "synthetic", "config": {"workload": "serving-sweep"}, "serving": obj,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def parcel_object(live, iterations=3, cpu=True):
+    """The paper's Lagrangian parcel scheme (Sec. 2, Fig. 2) on the 96-species, 150-layer column:
+    device time of a global iteration (one CTA sweeps the parcel bottom to top and back, an FP64
+    partial-pivot LU per implicit step), after one untimed iteration from the initial state; the
+    oracle's time for the same first iteration on one host core, and the element-wise error of
+    that iteration against it."""
+    import numpy as np
+    import torch
+    from paper_2512_06729_gb300 import synth, xk
+    prob = synth.chons_column()
+    S, L = prob.S, prob.L
+    col = xk.Column(prob, "fp64")
+    col.set_mixing_ratios(prob.f0)
+    n0 = col.get_state()
+    first = col.parcel_iteration(h=1e-8)
+    n1 = col.get_state()
+    h = first.h
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 0
+    ms = 0.0
+    for _ in range(iterations):
+        torch.cuda.synchronize()
+        start.record(stream)
+        info = col.parcel_iteration(h=h)
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms += start.elapsed_time(end)
+        h = info.h
+        steps += int(info.steps + info.rejected)
+    ms_it = ms / iterations
+    steps_it = steps / iterations
+    # FP64 work of one implicit step: elimination 2/3 S^3 plus the two triangular solves 2 S^2
+    flops_step = 2.0 / 3.0 * S ** 3 + 2.0 * S ** 2
+    achieved = flops_step * steps_it / (ms_it * 1e-3) / 1e12
+    peak_sm = live["f64"] / 152.0
+    out = {
+        "workload": f"{S} species x {L} layers, {2 * L - 1} visits per global iteration",
+        "iterations_per_s": 1e3 / ms_it, "ms_per_iteration": ms_it, "implicit_steps_per_iteration": steps_it,
+        "first_iteration": {"steps": int(first.steps), "rejected": int(first.rejected),
+                            "max_change": float(first.max_change)},
+        "roofline": {"kernel": "k_parcel_iteration (one CTA, FP64 Gaussian elimination per implicit step)",
+                     "bound": "alu", "achieved": achieved, "peak": peak_sm, "unit": "TFLOP/s",
+                     "frac": achieved / peak_sm,
+                     "peak_kind": "FP64 matmul measured live / 152 SMs (the sweep is sequential: one SM)"},
+    }
+    col.close()
+    if cpu:
+        from oracle.oracle import Oracle
+        o = Oracle(prob)
+        t0 = time.perf_counter()
+        N, oi = o.parcel_iteration(n0, h=1e-8)
+        dt = time.perf_counter() - t0
+        ngas = o.grid()[0]
+        keep = N > 1e-20 * ngas[:, None]
+        out["cpu_oracle_first_iteration_s"] = dt
+        out["gpu_vs_oracle_first_iteration"] = {
+            "max_rel": float(np.max(np.abs(n1[keep] - N[keep]) / N[keep])),
+            "steps_equal": bool(oi.steps == first.steps and oi.rejected == first.rejected)}
+    return out
 
 
 def run_steady(args):
@@ -666,7 +789,8 @@ def run_steady(args):
     prob = synth.full_column()
     stream = torch.cuda.current_stream()
     runs = {}
-    variants = {"mixed": ("mixed", dict(reuse_factorization=1)), "fp64": ("fp64", {})}
+    extra = json.loads(args.column_kw) if args.column_kw else {}
+    variants = {"mixed": ("mixed", dict(reuse_factorization=1, **extra)), "fp64": ("fp64", {})}
     for name in args.variants.split(","):
         prec, kw = variants[name]
         col = xk.Column(prob, prec, **kw)
@@ -769,23 +893,29 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle legs (baseline, error vs oracle)")
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady-state runs")
     ap.add_argument("--steady-cap", type=float, default=300.0, help="seconds allowed to the mixed run to steady state")
-    ap.add_argument("--steady-cap-fp64", type=float, default=120.0,
+    ap.add_argument("--steady-cap-fp64", type=float, default=60.0,
                     help="seconds allowed to the plain FP64 run to steady state")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the default line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving object of the default line")
+    ap.add_argument("--no-parcel", action="store_true", help="skip the parcel-scheme object of the default line")
+    ap.add_argument("--serving-deadline", type=float, default=75.0,
+                    help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
-    ap.add_argument("--variants", default="mixed,fp64", help="--mode steady: paths to run, in order")
+    ap.add_argument("--variants", default="mixed,fp64", help="--mode steady / serving: paths to run, in order")
     ap.add_argument("--time-limit", type=float, default=600.0,
                     help="--mode steady: seconds per path; --mode serving: deadline of the serving loop")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="--mode kernels")
     ap.add_argument("--dt", type=float, default=1e-2, help="--mode kernels: step size of the linear steps")
     ap.add_argument("--columns", type=int, default=64)
-    ap.add_argument("--requests", type=int, default=12)
-    ap.add_argument("--rate", type=float, default=1.0)
-    ap.add_argument("--slots", type=int, default=12)
+    ap.add_argument("--column-kw", default="", help="--mode steady: JSON of extra config fields of the mixed path")
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=0.25)
+    ap.add_argument("--slots", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

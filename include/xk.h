@@ -94,7 +94,7 @@ typedef struct {
                              inverted (1..16; 0 = the largest that fits; -1 = grid-wide kernel with
                              the block in global memory).  panel_width 8 or 16 applies (default 8). */
     int reuse_max_iters;  /* with reuse_factorization: a solve on the reused FP64 factorization that
-                             needs more FGMRES iterations than this (default 20; an iteration costs
+                             needs more FGMRES iterations than this (default 40; an iteration costs
                              about one FP64 sweep pair, a fresh factorization a few hundred) makes
                              the next FP64 step refactor */
     int twisted;          /* mixed mode, cluster-resident inversion: 1 (default) eliminates from both
@@ -260,6 +260,42 @@ XK_API int xk_block_solve32(xk_ctx *ctx, const double *A, const double *lo, cons
  * mode *iters = -1 when the FP64 route solved the step; in FP64 mode the
  * refinement iterations around the FP64 factorization). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
+
+/* ---- Lagrangian parcel scheme (Sec. 2, Fig. 1 and Fig. 2) ----
+ * The paper's own driver.  One global iteration carries an air parcel from the
+ * bottom layer to the top and back (layers 0 .. L-1, then L-2 .. 0).  In layer
+ * k the parcel spends the eddy mixing time tau_k = dz_k^2 / K_zz,k: eddy
+ * diffusion is the parcel's motion.  There the parcel evolves under the layer's
+ * chemistry (rate coefficients of Sec. 2.3, photolysis rates from the stored
+ * profile at the start of the iteration).  Molecular diffusion is a
+ * pseudo-reaction pair (Sec. 2.1, after Eq. 4: the molecular part of Eq. 2's
+ * flux) with the stored densities of layers k -+ 1.
+ * Time integration: linearly implicit Euler steps under the context's step
+ * policy (dt_max, rel_reject, rel_target, grow_max, shrink_min, neg_tol, f_floor,
+ * dt_min), each solved by Gaussian elimination with partial pivoting in FP64.
+ * No step crosses the end of a visit, and the trial step is carried from
+ * visit to visit.  The parcel keeps its mixing ratios from layer to layer;
+ * each visit leaves its densities as the layer's.  The stored profile is the
+ * context's state (xk_set_state / xk_get_state); every K_zz must be positive.
+ *
+ * xk_parcel_iteration: one global iteration.  info->h must hold the first
+ *   trial step (> 0) and receives the next one.  steps / rejected count this
+ *   iteration.  max_change is the largest |N_new - N_old| / N_new over entries
+ *   above f_floor mixing ratio.  The whole iteration runs on one CTA, with no
+ *   grid-wide waits.  Returns XK_ESINGULAR (zero pivot), XK_ENEG (a step below
+ *   dt_min), XK_ENOCONV (more than max_visit_steps steps in one visit) or
+ *   XK_OK; the profile is then partly swept.
+ * xk_parcel_run: iterations until max_change < tol (Sec. 2: 0.1 %), or
+ *   XK_ENOCONV after max_iter; steps and rejected count the whole run. */
+typedef struct {
+    double h;
+    long long steps;
+    long long rejected;
+    double max_change;
+} xk_parcel_info;
+XK_API int xk_parcel_iteration(xk_ctx *ctx, int max_visit_steps, xk_parcel_info *info);
+XK_API int xk_parcel_run(xk_ctx *ctx, int max_visit_steps, int max_iter, double tol, xk_parcel_info *info,
+                         int *iterations);
 
 /* ---- batches of columns: continuous batching on one GPU ----
  * A batch advances many columns together, each on its own stream, with the

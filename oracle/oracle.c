@@ -599,3 +599,297 @@ int ora_run_to_steady(const ora_problem *p, const ora_policy *pol, double *n, do
     info->max_rel = si.max_rel;
     return conv ? 0 : -1;
 }
+
+/* ------------------------------------------------ Lagrangian parcel */
+
+/* The paper's own driver (Sec. 2, Fig. 1 and Fig. 2): an air parcel is carried
+ * from the bottom of the atmosphere to the top and back; in each layer it evolves
+ * under that layer's chemistry, and molecular diffusion acts on it as a pair of
+ * pseudo-reactions (Sec. 2.1, after Eq. 4): the parcel loses a species to the
+ * neighbouring layers and gains it back from their stored densities.  Eddy
+ * diffusion has no term of its own: it is the parcel's motion.  A global
+ * iteration is one such round trip; the run has converged when two successive
+ * iterations change no mixing ratio by 0.1 % or more (Sec. 2).
+ *
+ * Readings where the paper is silent:
+ *  - visits: layers 0, 1, ..., L-1, then L-2, ..., 0 (2L - 1 visits; the top
+ *    layer once); each visit stores the parcel's densities as that layer's;
+ *  - the parcel keeps its mixing ratios as it moves: entering layer k its
+ *    densities are f * n_gas,k;
+ *  - residence time in layer k: the eddy mixing time tau_k = dz_k^2 / K_zz,k;
+ *  - time integration within a visit, in place of the paper's DLSODES:
+ *    linearly implicit Euler steps over [0, tau_k] under the step controller
+ *    of the Eulerian path (ora_step): a step is rejected and halved when a
+ *    density would fall below -neg_tol n_gas or change by more than rel_reject
+ *    (relative, over species above f_floor); an accepted step clips negatives
+ *    to 0 and scales the next one by rel_target / max change, within
+ *    [shrink_min, grow_max]; a step never crosses the end of the visit, and
+ *    the trial step is carried from visit to visit (a step cut short by the
+ *    end of a visit does not shrink it);
+ *  - molecular diffusion: the molecular part of Eq. 2's flux (eddy K = 0)
+ *    between the parcel and the stored densities of layers k - 1 and k + 1
+ *    as they stand at the visit (zero flux at both ends);
+ *  - photolysis rates from the stored profile at the start of the iteration;
+ *  - the convergence measure: the largest |N_new - N_old| / N_new over
+ *    entries above f_floor mixing ratio (same layer, so mixing ratios and
+ *    densities give the same ratio). */
+
+#define ORA_PARCEL_REFINE 2
+
+/* Chemistry of one layer at composition nk: Fk = sum_r nu_r w_r and the dense Jacobian
+ * Jk = dFk/dnk (S x S, row-major), mass action as in ora_residual / ora_jacobian. */
+static void layer_chemistry(const ora_problem *p, const double *kf_k, const double *kr_k, const double *nk,
+                            double *Fk, double *Jk)
+{
+    int S = p->S, R = p->R;
+    memset(Fk, 0, sizeof(double) * S);
+    memset(Jk, 0, sizeof(double) * S * S);
+    for (int r = 0; r < R; ++r) {
+        const int *ra = p->reac + 3 * r, *pa = p->prod + 3 * r;
+        double wf = kf_k[r], wb = kr_k[r];
+        for (int s = 0; s < 3; ++s) {
+            if (ra[s] >= 0) wf *= nk[ra[s]];
+            if (pa[s] >= 0) wb *= nk[pa[s]];
+        }
+        double w = wf - wb;
+        for (int s = 0; s < 3; ++s) {
+            if (ra[s] >= 0) Fk[ra[s]] -= w;
+            if (pa[s] >= 0) Fk[pa[s]] += w;
+        }
+        /* dw/dn_j, then dF_i/dn_j = nu_i dw/dn_j */
+        for (int side = 0; side < 2; ++side) {
+            const int *sp = side == 0 ? ra : pa;
+            double kk = side == 0 ? kf_k[r] : -kr_k[r];
+            for (int s = 0; s < 3; ++s) {
+                int j = sp[s];
+                if (j < 0)
+                    continue;
+                double d = kk;
+                for (int t = 0; t < 3; ++t)
+                    if (t != s && sp[t] >= 0)
+                        d *= nk[sp[t]];
+                for (int q = 0; q < 3; ++q) {
+                    if (ra[q] >= 0) Jk[(size_t)ra[q] * S + j] -= d;
+                    if (pa[q] >= 0) Jk[(size_t)pa[q] * S + j] += d;
+                }
+            }
+        }
+    }
+}
+
+/* Everything a visit needs that does not change within an iteration. */
+typedef struct {
+    double *ngas, *z, *dz, *dzi;
+    double *kf, *kr, *kph;
+    double *um, *vm;          /* molecular part of Eq. 2's u, v per interface */
+} parcel_fields;
+
+static void parcel_fields_make(const ora_problem *p, const double *N, parcel_fields *f)
+{
+    int L = p->L, S = p->S, R = p->R;
+    size_t m = (size_t)(L > 1 ? L - 1 : 1) * S;
+    f->ngas = malloc(sizeof(double) * L * 4);
+    f->z = f->ngas + L; f->dz = f->z + L; f->dzi = f->dz + L;
+    ora_grid(p, f->ngas, f->z, f->dz, f->dzi);
+    f->kf = malloc(sizeof(double) * (size_t)L * R * 2);
+    f->kr = f->kf + (size_t)L * R;
+    ora_rate_coefficients(p, f->kf, f->kr);
+    f->kph = malloc(sizeof(double) * (size_t)L * (p->Rph > 0 ? p->Rph : 1));
+    ora_photolysis(p, N, f->kph);
+    f->um = malloc(sizeof(double) * m * 2);
+    f->vm = f->um + m;
+    double *zero = calloc((size_t)L, sizeof(double));
+    ora_problem q = *p;
+    q.Kzz = zero;
+    ora_transport(&q, f->um, f->vm);
+    free(zero);
+}
+
+static void parcel_fields_free(parcel_fields *f)
+{
+    free(f->ngas); free(f->kf); free(f->kph); free(f->um);
+}
+
+/* F and A = I/h - dF/dpk of the parcel with densities pk in layer k. */
+static void parcel_system(const ora_problem *p, const parcel_fields *f, const double *N, int k,
+                          const double *pk, double h, double *F, double *A)
+{
+    int L = p->L, S = p->S, R = p->R;
+    double *kf_k = malloc(sizeof(double) * R * 2 + sizeof(double)), *kr_k = kf_k + R;
+    layer_rates(p, k, f->kf, f->kr, f->kph, kf_k, kr_k);
+    layer_chemistry(p, kf_k, kr_k, pk, F, A);
+    /* A = -J so far: negate, then add I/h */
+    for (size_t i = 0; i < (size_t)S * S; ++i)
+        A[i] = -A[i];
+    for (int y = 0; y < S; ++y) {
+        /* molecular diffusion: loss of the parcel's own density, gain from the neighbours' */
+        double loss = 0.0, gain = 0.0;
+        if (k + 1 < L) {
+            loss += f->um[(size_t)k * S + y];
+            gain += f->vm[(size_t)k * S + y] * N[(size_t)(k + 1) * S + y];
+        }
+        if (k > 0) {
+            loss += f->vm[(size_t)(k - 1) * S + y];
+            gain += f->um[(size_t)(k - 1) * S + y] * N[(size_t)(k - 1) * S + y];
+        }
+        F[y] += (gain - loss * pk[y]) / f->dz[k];
+        A[(size_t)y * S + y] += 1.0 / h + loss / f->dz[k];
+    }
+    free(kf_k);
+}
+
+int ora_parcel_system(const ora_problem *p, const double *N, int k, const double *pk, double h,
+                      double *F, double *A)
+{
+    if (k < 0 || k >= p->L || !(h > 0.0))
+        return -1;
+    parcel_fields f;
+    parcel_fields_make(p, N, &f);
+    parcel_system(p, &f, N, k, pk, h, F, A);
+    parcel_fields_free(&f);
+    return 0;
+}
+
+/* delta solves A delta = F: partial-pivot LU plus ORA_PARCEL_REFINE refinement sweeps. */
+static int dense_solve(int S, const double *A, const double *F, double *delta)
+{
+    double *LU = malloc(sizeof(double) * ((size_t)S * S + 2 * S));
+    double *r = LU + (size_t)S * S, *c = r + S;
+    int *piv = malloc(sizeof(int) * S);
+    memcpy(LU, A, sizeof(double) * S * S);
+    int rc = lu_factor(S, LU, piv);
+    if (rc == 0) {
+        lu_solve(S, LU, piv, F, delta, 1);
+        for (int sweep = 0; sweep < ORA_PARCEL_REFINE; ++sweep) {
+            for (int i = 0; i < S; ++i) {
+                double acc = F[i];
+                for (int j = 0; j < S; ++j)
+                    acc -= A[(size_t)i * S + j] * delta[j];
+                r[i] = acc;
+            }
+            lu_solve(S, LU, piv, r, c, 1);
+            for (int i = 0; i < S; ++i)
+                delta[i] += c[i];
+        }
+    }
+    free(piv);
+    free(LU);
+    return rc;
+}
+
+/* Integrate the parcel x over one visit of layer k (tau_k); *h is the trial step, carried. */
+static int parcel_visit(const ora_problem *p, const ora_policy *pol, const parcel_fields *f, const double *N, int k,
+                        int max_steps, double *x, double *h, double *A, double *F, double *delta, ora_parcel_info *info)
+{
+    int S = p->S;
+    double tau = f->dz[k] * f->dz[k] / p->Kzz[k];
+    double t = 0.0;
+    int steps = 0;
+    while (t < tau) {
+        double rest = tau - t;
+        double hs = *h < rest ? *h : rest;
+        if (hs > pol->dt_max) hs = pol->dt_max;
+        int last = hs >= rest;
+        parcel_system(p, f, N, k, x, hs, F, A);
+        if (dense_solve(S, A, F, delta) != 0)
+            return -1;
+        int ok = 1;
+        double maxrel = 0.0;
+        for (int y = 0; y < S; ++y) {
+            double nn = x[y] + delta[y];
+            if (!isfinite(nn) || nn < -pol->neg_tol * f->ngas[k]) { ok = 0; break; }
+            if (x[y] > pol->f_floor * f->ngas[k]) {
+                double rel = fabs(delta[y]) / x[y];
+                if (rel > maxrel) maxrel = rel;
+            }
+        }
+        if (ok && maxrel > pol->rel_reject)
+            ok = 0;
+        if (ok) {
+            for (int y = 0; y < S; ++y) {
+                double nn = x[y] + delta[y];
+                x[y] = nn < 0.0 ? 0.0 : nn;
+            }
+            t = last ? tau : t + hs;
+            double fac = maxrel > 0.0 ? pol->rel_target / maxrel : pol->grow_max;
+            if (fac > pol->grow_max) fac = pol->grow_max;
+            if (fac < pol->shrink_min) fac = pol->shrink_min;
+            double next = hs * fac;
+            if (hs < *h && fac >= 1.0 && next < *h)
+                next = *h;                 /* cut short by the end of the visit: keep the trial step */
+            *h = next;
+            ++info->steps;
+        } else {
+            *h = 0.5 * hs;
+            ++info->rejected;
+            if (*h < pol->dt_min)
+                return -2;
+        }
+        if (++steps > max_steps)
+            return -3;
+    }
+    return 0;
+}
+
+int ora_parcel_iteration(const ora_problem *p, const ora_policy *pol, int max_visit_steps, double *N,
+                         ora_parcel_info *info)
+{
+    int L = p->L, S = p->S;
+    size_t LS = (size_t)L * S;
+    parcel_fields f;
+    parcel_fields_make(p, N, &f);
+    double *old = malloc(sizeof(double) * LS);
+    double *x = malloc(sizeof(double) * ((size_t)S * S + 4 * S));
+    double *A = x + S, *F = A + (size_t)S * S, *delta = F + S, *vmr = delta + S;
+    memcpy(old, N, sizeof(double) * LS);
+    for (int y = 0; y < S; ++y)
+        vmr[y] = N[y] / f.ngas[0];
+    info->steps = 0;
+    info->rejected = 0;
+    int rc = 0;
+    for (int v = 0; v < 2 * L - 1 && rc == 0; ++v) {
+        int k = v < L ? v : 2 * L - 2 - v;
+        for (int y = 0; y < S; ++y)
+            x[y] = vmr[y] * f.ngas[k];
+        rc = parcel_visit(p, pol, &f, N, k, max_visit_steps, x, &info->h, A, F, delta, info);
+        for (int y = 0; y < S; ++y) {
+            N[(size_t)k * S + y] = x[y];
+            vmr[y] = x[y] / f.ngas[k];
+        }
+    }
+    double change = 0.0;
+    for (int k = 0; k < L; ++k)
+        for (int y = 0; y < S; ++y) {
+            double nv = N[(size_t)k * S + y];
+            if (nv > pol->f_floor * f.ngas[k]) {
+                double c = fabs(nv - old[(size_t)k * S + y]) / nv;
+                if (c > change) change = c;
+            }
+        }
+    info->max_change = change;
+    free(x);
+    free(old);
+    parcel_fields_free(&f);
+    return rc;
+}
+
+int ora_parcel_run(const ora_problem *p, const ora_policy *pol, int max_visit_steps, int max_iter, double tol,
+                   double *N, ora_parcel_info *info, int *iterations)
+{
+    int it = 0, rc = 0;
+    int steps = 0, rejected = 0;
+    while (it < max_iter) {
+        rc = ora_parcel_iteration(p, pol, max_visit_steps, N, info);
+        ++it;
+        steps += info->steps;
+        rejected += info->rejected;
+        if (rc != 0 || info->max_change < tol)
+            break;
+    }
+    info->steps = steps;
+    info->rejected = rejected;
+    *iterations = it;
+    if (rc != 0)
+        return rc;
+    return info->max_change < tol ? 0 : 1;
+}

@@ -97,6 +97,27 @@ int ora_step(const ora_problem *p, const ora_policy *pol, double *n, double dt, 
 int ora_run_to_steady(const ora_problem *p, const ora_policy *pol, double *n, double dt0,
                       int max_steps, ora_run_info *info);
 
+/* Lagrangian parcel scheme (Sec. 2, Fig. 2).  The parcel's system in layer k with densities
+ * pk: F = chemistry of layer k at pk plus the molecular-diffusion exchange with the stored
+ * densities N of layers k -+ 1, and A = I/h - dF/dpk (S x S row-major).  0 or -1. */
+int ora_parcel_system(const ora_problem *p, const double *N, int k, const double *pk, double h,
+                      double *F, double *A);
+typedef struct {
+    double h;           /* in: the first trial step (s); out: the trial step after the last visit */
+    int steps;          /* accepted implicit steps (of the iteration; of the run for ora_parcel_run) */
+    int rejected;       /* rejected trial steps */
+    double max_change;  /* largest |N_new - N_old| / N_new over entries above f_floor mixing ratio */
+} ora_parcel_info;
+/* One global iteration (bottom to top and back) on the stored profile N [L][S], updated in
+ * place; each visit integrated under the step controller of pol.  0; -1 singular visit
+ * system; -2 step below dt_min; -3 more than max_visit_steps steps in one visit. */
+int ora_parcel_iteration(const ora_problem *p, const ora_policy *pol, int max_visit_steps, double *N,
+                         ora_parcel_info *info);
+/* Global iterations until info->max_change < tol (returns 0) or max_iter (returns 1); a
+ * negative return as ora_parcel_iteration.  info->h is the first trial step. */
+int ora_parcel_run(const ora_problem *p, const ora_policy *pol, int max_visit_steps, int max_iter, double tol,
+                   double *N, ora_parcel_info *info, int *iterations);
+
 #ifdef __cplusplus
 }
 #endif

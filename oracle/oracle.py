@@ -47,6 +47,10 @@ class RunInfo(C.Structure):
                 ("rejected", C.c_int), ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double)]
 
 
+class ParcelInfo(C.Structure):
+    _fields_ = [("h", C.c_double), ("steps", C.c_int), ("rejected", C.c_int), ("max_change", C.c_double)]
+
+
 def default_policy(**kw):
     """The step-control policy shared (by value, not by code) with the CUDA path."""
     vals = dict(dt_max=1e8, rel_reject=1.0, rel_target=0.5, grow_max=3.0, shrink_min=0.5,
@@ -93,6 +97,13 @@ def lib():
         l.ora_step.argtypes = [P, C.POINTER(Policy), _dp, C.c_double, C.POINTER(StepInfo)]
         l.ora_run_to_steady.argtypes = [P, C.POINTER(Policy), _dp, C.c_double, C.c_int, C.POINTER(RunInfo)]
         l.ora_run_to_steady.restype = C.c_int
+        l.ora_parcel_system.argtypes = [P, _dp, C.c_int, _dp, C.c_double, _dp, _dp]
+        l.ora_parcel_system.restype = C.c_int
+        l.ora_parcel_iteration.argtypes = [P, C.POINTER(Policy), C.c_int, _dp, C.POINTER(ParcelInfo)]
+        l.ora_parcel_iteration.restype = C.c_int
+        l.ora_parcel_run.argtypes = [P, C.POINTER(Policy), C.c_int, C.c_int, C.c_double, _dp,
+                                     C.POINTER(ParcelInfo), _ip]
+        l.ora_parcel_run.restype = C.c_int
         _lib = l
     return _lib
 
@@ -227,3 +238,36 @@ class Oracle:
         info = RunInfo()
         lib().ora_run_to_steady(C.byref(self.st), C.byref(pol), _d(m), float(dt0), int(max_steps), C.byref(info))
         return m, info
+
+    # -- Lagrangian parcel scheme (Sec. 2, Fig. 2) ------------------------------
+    def parcel_system(self, N, k, pk, h):
+        """F and A = I/h - dF/dpk of the parcel with densities pk visiting layer k."""
+        F = np.zeros(self.S)
+        A = np.zeros((self.S, self.S))
+        rc = lib().ora_parcel_system(C.byref(self.st), _d(np.ascontiguousarray(N, np.float64)), int(k),
+                                     _d(np.ascontiguousarray(pk, np.float64)), float(h), _d(F), _d(A))
+        if rc != 0:
+            raise ValueError("bad layer or step")
+        return F, A
+
+    def parcel_iteration(self, N, h=1e-8, policy=None, max_visit_steps=100000):
+        """One global iteration; returns (new profile, ParcelInfo).  N is not modified."""
+        pol = policy or default_policy()
+        m = np.array(N, np.float64, order="C", copy=True)
+        info = ParcelInfo(h=float(h))
+        rc = lib().ora_parcel_iteration(C.byref(self.st), C.byref(pol), int(max_visit_steps), _d(m), C.byref(info))
+        if rc != 0:
+            raise ArithmeticError(f"parcel iteration failed ({rc})")
+        return m, info
+
+    def parcel_run(self, N, h=1e-8, policy=None, max_iter=200, tol=1e-3, max_visit_steps=100000):
+        """Global iterations to convergence; returns (profile, iterations, ParcelInfo, converged)."""
+        pol = policy or default_policy()
+        m = np.array(N, np.float64, order="C", copy=True)
+        info = ParcelInfo(h=float(h))
+        it = C.c_int(0)
+        rc = lib().ora_parcel_run(C.byref(self.st), C.byref(pol), int(max_visit_steps), int(max_iter), float(tol),
+                                  _d(m), C.byref(info), C.byref(it))
+        if rc < 0:
+            raise ArithmeticError(f"parcel run failed ({rc})")
+        return m, it.value, info, rc == 0

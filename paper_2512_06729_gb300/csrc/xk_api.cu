@@ -72,6 +72,10 @@ struct xk_ctx {
     BcrPlan bcr;           // block cyclic reduction on the tensor cores (mixed path, fp32_bcr)
     bool use_bcr = false;
     bool ready = false;
+    // Lagrangian parcel scheme: its buffers in the workspace (ParcelArgs without the policy)
+    ParcelArgs parcel{};
+    double *parcel_kzz0 = nullptr;   // [L] zero eddy profile: the molecular part of u, v
+    ParcelState *parcel_host = nullptr;   // pinned
     // captured chunks of controlled steps (cfg.use_graphs), dropped whenever a plan, the workspace
     // or the batch slot changes
     std::vector<StepGraph> graphs;
@@ -346,6 +350,21 @@ size_t layout(xk_ctx *c, char *base)
     c->bcr.bar = c->bar ? c->bar + 4 : nullptr;      // words 4-5: the reduction's solve
     c->ctl = b.take<Ctl>(1);
     c->ctl_aux = b.take<Ctl>(1);
+    // Lagrangian parcel scheme
+    ParcelArgs &q = c->parcel;
+    q.N = k.n;
+    q.Nold = b.take<double>(LS);
+    const size_t ifc = std::max<size_t>(1, (size_t)(L - 1) * S);
+    q.um = b.take<double>(ifc);
+    q.vm = b.take<double>(ifc);
+    q.A = b.take<double>((size_t)S * S);
+    q.x = b.take<double>(S);
+    q.F = b.take<double>(S);
+    q.vmr = b.take<double>(S);
+    q.w = b.take<double>(std::max(R, 1));
+    q.dd = b.take<double>(6 * (size_t)std::max(R, 1));
+    q.st = b.take<ParcelState>(1);
+    c->parcel_kzz0 = b.take<double>(L);
     return b.off + 256;
 }
 
@@ -544,7 +563,7 @@ int enqueue_linear_step(xk_ctx *c, const double *n, double dt_override, double *
         a.tol = c->cfg.gmres_tol;
         a.b = c->bhat; a.x = col.x; a.V = c->V; a.Z = c->Z; a.w = c->gw; a.h1 = c->h1; a.h2 = c->h2;
         a.red = c->red; a.partials = c->partials; a.counter = c->counter; a.gm = c->gm; a.ctl = ctl;
-        a.reuse_max_iters = c->cfg.reuse_max_iters > 0 ? c->cfg.reuse_max_iters : 20;
+        a.reuse_max_iters = c->cfg.reuse_max_iters > 0 ? c->cfg.reuse_max_iters : 40;
         FactorPlan plan64 = c->plan64;
         const double *rowd = c->rowd, *pin = c->pin, *pout = c->pout;
         a.matvec = [col, ctl, rowd](const double *x, double *y, const int *skip, cudaStream_t s) {
@@ -742,7 +761,7 @@ int xk_config_init(xk_config *cfg)
     cfg->dt_max = 1e8; cfg->rel_reject = 1.0; cfg->rel_target = 0.5; cfg->grow_max = 3.0; cfg->shrink_min = 0.5;
     cfg->neg_tol = 1e-12; cfg->f_floor = 1e-20; cfg->dt_min = 1e-20; cfg->ss_dt = 1e8; cfg->ss_tol = 1e-3;
     cfg->gmres_restart = 30; cfg->gmres_max_iter = 40; cfg->gmres_tol = 1e-15;
-    cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1; cfg->reuse_max_iters = 20;
+    cfg->panel_width = 0; cfg->factor_ctas = 0; cfg->twisted = 1; cfg->reuse_max_iters = 40;
     cfg->refine_max_iter = 10;
     cfg->fp32_bcr = 1;
     cfg->wait_polls = 0;
@@ -769,8 +788,10 @@ int xk_create(xk_ctx **out, const xk_config *cfg)
     x->cfg = c;
     x->st = (cudaStream_t)c.stream;
     cudaSetDevice(c.device);
-    if (cudaMallocHost((void **)&x->ctl_host, sizeof(Ctl)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&x->ctl_host, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void **)&x->parcel_host, sizeof(ParcelState)) != cudaSuccess) {
         cudaGetLastError();
+        if (x->ctl_host) cudaFreeHost(x->ctl_host);
         delete x;
         return XK_ECUDA;
     }
@@ -786,6 +807,7 @@ int xk_destroy(xk_ctx *ctx)
     for (auto &v : ctx->ev)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+    if (ctx->parcel_host) cudaFreeHost(ctx->parcel_host);
     delete ctx;
     return XK_OK;
 }
@@ -1636,6 +1658,66 @@ int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *
     }
     if (finished) *finished = b->slots[slot].finished ? 1 : 0;
     if (status) *status = h.err_timeout ? XK_ETIMEOUT : h.status;
+    return XK_OK;
+}
+
+// ---------------------------------------------------------------- Lagrangian parcel scheme
+
+int xk_parcel_iteration(xk_ctx *c, int max_visit_steps, xk_parcel_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!info || max_visit_steps <= 0 || !(info->h > 0.0)) return fail(c, XK_EINVAL, "parcel: bad arguments");
+    if (!(c->L >= 1)) return fail(c, XK_EINVAL, "parcel: no layers");
+    for (int k = 0; k < c->L; ++k)
+        if (!(c->Kzz[k] > 0.0)) return fail(c, XK_EINVAL, "parcel: K_zz must be positive (residence time dz^2 / K_zz)");
+    ensure_rates(c);
+    // photolysis from the stored profile at the start of the iteration; molecular-only u, v
+    launch_photolysis(c->col, c->col.n, c->st);
+    cudaMemsetAsync(c->parcel_kzz0, 0, sizeof(double) * c->L, c->st);
+    launch_transport_coeffs(c->col, c->parcel_kzz0, const_cast<double *>(c->parcel.um),
+                            const_cast<double *>(c->parcel.vm), c->st);
+    ParcelState init{};
+    init.h = info->h;
+    init.status = -1;
+    *c->parcel_host = init;
+    cudaMemcpyAsync(c->parcel.st, c->parcel_host, sizeof(ParcelState), cudaMemcpyHostToDevice, c->st);
+    ParcelArgs a = c->parcel;
+    a.pol = policy_of(c->cfg);
+    a.max_visit_steps = max_visit_steps;
+    launch_parcel_iteration(c->col, a, c->st);
+    cudaMemcpyAsync(c->parcel_host, c->parcel.st, sizeof(ParcelState), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(c, XK_ECUDA, "parcel iteration: %s", cudaGetErrorString(e));
+    const ParcelState &h = *c->parcel_host;
+    info->h = h.h;
+    info->steps = h.steps;
+    info->rejected = h.rejected;
+    info->max_change = h.max_change;
+    if (h.status == XK_ESINGULAR) return fail(c, XK_ESINGULAR, "parcel: singular system at visit %d", h.visit);
+    if (h.status == XK_ENEG) return fail(c, XK_ENEG, "parcel: step below dt_min at visit %d", h.visit);
+    if (h.status == XK_ENOCONV) return fail(c, XK_ENOCONV, "parcel: more than %d steps in visit %d", max_visit_steps, h.visit);
+    if (h.status != 0) return fail(c, XK_ECUDA, "parcel: iteration did not complete (status %d)", h.status);
+    return cuda_check(c, "parcel iteration");
+}
+
+int xk_parcel_run(xk_ctx *c, int max_visit_steps, int max_iter, double tol, xk_parcel_info *info, int *iterations)
+{
+    if (!c || !info || !iterations || max_iter <= 0 || !(tol > 0.0)) return c ? fail(c, XK_EINVAL, "parcel run: bad arguments") : XK_EINVAL;
+    long long steps = 0, rejected = 0;
+    int it = 0, rc = XK_OK;
+    while (it < max_iter) {
+        rc = xk_parcel_iteration(c, max_visit_steps, info);
+        ++it;
+        steps += info->steps;
+        rejected += info->rejected;
+        if (rc != XK_OK || info->max_change < tol) break;
+    }
+    info->steps = steps;
+    info->rejected = rejected;
+    *iterations = it;
+    if (rc != XK_OK) return rc;
+    if (!(info->max_change < tol)) return fail(c, XK_ENOCONV, "parcel: change %.3g after %d iterations", info->max_change, it);
     return XK_OK;
 }
 

@@ -209,50 +209,7 @@ __global__ void k_reaction_terms(Col c, const double *n)
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)c.L * c.R) return;
     int k = (int)(idx / c.R), r = (int)(idx % c.R);
-    const double *nk = n + (long long)k * c.S;
-    double kfv, krv;
-    if (c.rtype[r] == XK_RX_PHOTO) {
-        kfv = c.kph[(long long)k * c.Rph + c.prow[r]];
-        krv = 0.0;
-    } else {
-        kfv = c.kf[idx];
-        krv = c.kr[idx];
-    }
-    int ra[3], pa[3];
-    double na[3], pb[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        ra[s] = c.reac[3 * r + s];
-        pa[s] = c.prod[3 * r + s];
-        na[s] = ra[s] >= 0 ? nk[ra[s]] : 0.0;
-        pb[s] = pa[s] >= 0 ? nk[pa[s]] : 0.0;
-    }
-    double wf = kfv, wb = krv;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        if (ra[s] >= 0) wf *= na[s];
-        if (pa[s] >= 0) wb *= pb[s];
-    }
-    c.w[idx] = wf - wb;
-    double *d = c.d + idx * 6;
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        double df = 0.0, db = 0.0;
-        if (ra[s] >= 0) {
-            df = kfv;
-#pragma unroll
-            for (int t = 0; t < 3; ++t)
-                if (t != s && ra[t] >= 0) df *= na[t];
-        }
-        if (pa[s] >= 0) {
-            db = -krv;
-#pragma unroll
-            for (int t = 0; t < 3; ++t)
-                if (t != s && pa[t] >= 0) db *= pb[t];
-        }
-        d[s] = df;
-        d[3 + s] = db;
-    }
+    reaction_terms_at(c, k, r, n + (long long)k * c.S, c.w + idx, c.d + idx * 6);
 }
 
 // F = sum_r nu w_r - (phi_{k+1/2} - phi_{k-1/2}) / dz_k; also the solve scaling
@@ -675,6 +632,17 @@ __global__ void k_transport_rows(Col c)
     c.tdg[idx] = dg;
     c.tlo[idx] = (k > 0) ? -c.u[(long long)(k - 1) * S + i] / c.dz[k] : 0.0;
     c.tup[idx] = (k + 1 < L) ? -c.v[(long long)k * S + i] / c.dz[k] : 0.0;
+}
+
+void launch_transport_coeffs(const Col &c, const double *Kzz, double *u, double *v, cudaStream_t st)
+{
+    if (c.L < 2) return;
+    Col t = c;
+    t.Kzz = Kzz;
+    t.u = u;
+    t.v = v;
+    count_launches(1);
+    k_transport<<<nblocks((long long)(c.L - 1) * c.S), kThreads, 0, st>>>(t);
 }
 
 void launch_grid(const Col &c, cudaStream_t st)

@@ -80,6 +80,92 @@ struct Policy {
     double dt_max, rel_reject, rel_target, grow_max, shrink_min, neg_tol, f_floor, dt_min, ss_dt, ss_tol;
 };
 
+// Mass-action terms of reaction r in layer k at densities nk (Sec. 2.3): w = k_f prod n_reac -
+// k_r prod n_prod, and d[slot] = d(k_f prod n_reac)/d n_reac[slot] (slots 0-2),
+// -d(k_r prod n_prod)/d n_prod[slot] (slots 3-5).  Photolysis rows take k_f from kph, no reverse.
+__device__ __forceinline__ void reaction_terms_at(const Col &c, int k, int r, const double *nk, double *w, double *d)
+{
+    const long long idx = (long long)k * c.R + r;
+    double kfv, krv;
+    if (c.rtype[r] == XK_RX_PHOTO) {
+        kfv = c.kph[(long long)k * c.Rph + c.prow[r]];
+        krv = 0.0;
+    } else {
+        kfv = c.kf[idx];
+        krv = c.kr[idx];
+    }
+    int ra[3], pa[3];
+    double na[3], pb[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        ra[s] = c.reac[3 * r + s];
+        pa[s] = c.prod[3 * r + s];
+        na[s] = ra[s] >= 0 ? nk[ra[s]] : 0.0;
+        pb[s] = pa[s] >= 0 ? nk[pa[s]] : 0.0;
+    }
+    double wf = kfv, wb = krv;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        if (ra[s] >= 0) wf *= na[s];
+        if (pa[s] >= 0) wb *= pb[s];
+    }
+    *w = wf - wb;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        double df = 0.0, db = 0.0;
+        if (ra[s] >= 0) {
+            df = kfv;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t != s && ra[t] >= 0) df *= na[t];
+        }
+        if (pa[s] >= 0) {
+            db = -krv;
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t != s && pa[t] >= 0) db *= pb[t];
+        }
+        d[s] = df;
+        d[3 + s] = db;
+    }
+}
+
+// Entry q of the Jacobian pattern (row-grouped): sum of its terms, -dF_i/dn_j of one layer, in a
+// fixed order (dk: that layer's reaction derivatives [R][6]).
+__device__ __forceinline__ double jac_entry(const Col &c, int q, const double *dk)
+{
+    double acc = 0.0;
+    for (int t = c.jtp[q]; t < c.jtp[q + 1]; ++t) {
+        const int code = c.jrs[t];
+        const int rs = code >> 1;
+        const double dv = dk[(long long)(rs >> 3) * 6 + (rs & 7)];
+        acc += (code & 1) ? dv : -dv;
+    }
+    return acc;
+}
+
+// Lagrangian parcel scheme (Sec. 2, Fig. 2): buffers and state of one global iteration.
+struct ParcelState {
+    double h;              // trial step, carried from visit to visit and across iterations
+    long long steps, rejected;
+    int status;            // 0, XK_ESINGULAR, XK_ENEG (step below dt_min), XK_ENOCONV (visit step cap)
+    int visit;             // visit at which a failure happened
+    double max_change;     // largest |N_new - N_old| / N_new over entries above f_floor mixing ratio
+};
+struct ParcelArgs {
+    double *N;             // [L][S] stored profile (the column state), updated in place
+    double *Nold;          // [L][S] the profile at the start of the iteration
+    const double *um, *vm; // [L-1][S] molecular part of Eq. 2's interface coefficients
+    double *A;             // S x S matrix of the current implicit step (row-major, ld S)
+    double *x, *F, *vmr;   // [S] parcel densities, right-hand side then solution, carried mixing ratios
+    double *w, *dd;        // [R] rates, [R][6] their derivatives at the parcel's densities
+    Policy pol;
+    int max_visit_steps;
+    ParcelState *st;
+};
+// One global iteration on one CTA (photolysis and rate coefficients already in c).
+void launch_parcel_iteration(const Col &c, const ParcelArgs &a, cudaStream_t st);
+
 constexpr unsigned long long kSpinLimit = 1ull << 24;   // polls of a bounded wait: ~1-2 s with the sleep below
 
 // Barrier over the nblk CTAs that share the counter pair bar[0..1] (the whole grid by default).
@@ -127,6 +213,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, Ctl *ctl, unsigned n
 void launch_grid(const Col &c, cudaStream_t st);
 void launch_thermo(const Col &c, cudaStream_t st);
 void launch_rates(const Col &c, cudaStream_t st);
+// u, v of Eq. 2 for the eddy profile Kzz (a zero profile leaves the molecular part only)
+void launch_transport_coeffs(const Col &c, const double *Kzz, double *u, double *v, cudaStream_t st);
 void launch_photolysis(const Col &c, const double *n, cudaStream_t st);
 void launch_reaction_terms(const Col &c, const double *n, cudaStream_t st);
 void launch_residual(const Col &c, const double *n, double *F, const Ctl *ctl, double f_floor, cudaStream_t st);

@@ -47,6 +47,10 @@ class StepInfo(C.Structure):
                 ("solver_iters", C.c_int), ("solver_resid", C.c_double), ("used_fp64", C.c_int)]
 
 
+class ParcelInfo(C.Structure):
+    _fields_ = [("h", C.c_double), ("steps", C.c_longlong), ("rejected", C.c_longlong), ("max_change", C.c_double)]
+
+
 class RunInfo(C.Structure):
     _fields_ = [("converged", C.c_int), ("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int),
                 ("t", C.c_double), ("dt", C.c_double), ("max_rel", C.c_double), ("solver_iters", C.c_longlong),
@@ -77,6 +81,8 @@ SIGNATURES = {
     "xk_set_rate_coefficients": (C.c_int, [_vp]),
     "xk_step": (C.c_int, [_vp, C.c_double, C.POINTER(StepInfo)]),
     "xk_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(RunInfo)]),
+    "xk_parcel_iteration": (C.c_int, [_vp, C.c_int, C.POINTER(ParcelInfo)]),
+    "xk_parcel_run": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.POINTER(ParcelInfo), C.POINTER(C.c_int)]),
     "xk_eval_grid": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xk_eval_thermo": (C.c_int, [_vp, _vp, _vp]),
     "xk_eval_rates": (C.c_int, [_vp, _vp, _vp]),
@@ -289,6 +295,23 @@ class Column:
             msg = lib().xk_last_error(self.h)
             raise XkError("xk_run_to_steady", rc, msg.decode() if msg else "")
         return info
+
+    # -- Lagrangian parcel scheme (Sec. 2, Fig. 2) ---------------------------
+    def parcel_iteration(self, h=1e-8, max_visit_steps=100000):
+        """One global iteration on the context's state; returns ParcelInfo (h = the next trial step)."""
+        info = ParcelInfo(h=float(h))
+        self._call("xk_parcel_iteration", int(max_visit_steps), C.byref(info))
+        return info
+
+    def parcel_run(self, h=1e-8, max_iter=200, tol=1e-3, max_visit_steps=100000):
+        """Global iterations until the change is below tol; returns (iterations, ParcelInfo, converged)."""
+        info = ParcelInfo(h=float(h))
+        it = C.c_int(0)
+        rc = lib().xk_parcel_run(self.h, int(max_visit_steps), int(max_iter), float(tol), C.byref(info), C.byref(it))
+        if rc not in (XK_OK, -3):
+            msg = lib().xk_last_error(self.h)
+            raise XkError("xk_parcel_run", rc, msg.decode() if msg else "")
+        return int(it.value), info, rc == XK_OK
 
     # -- rows ----------------------------------------------------------------
     def eval_grid(self):
