@@ -24,6 +24,9 @@ import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# many columns on their own streams (batch, serving, parcel sweeps): 32 hardware work queues
+# instead of the default 8, so that streams do not share one queue (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -385,9 +388,11 @@ def run_ours(args):
     for prec in ("mixed", "fp64"):
         col = xk.Column(prob, prec, device=local, **tuning[prec])
         col.set_mixing_ratios(prob.f0)
-        col.step(1e-8)
+        info_w = col.step(1e-8)
         for _ in range(max(args.warmup - 1, 0)):
-            col.step(0.0)
+            info_w = col.step(0.0)
+        # where the timed steps start: the end-to-end run repeats the same steps from here
+        start_state, start_dt = col.get_state(), float(info_w.dt_next)
         K = args.steps if prec == "mixed" else max(3, args.steps // 4)
         _barrier(ws)
         torch.cuda.synchronize()
@@ -408,6 +413,7 @@ def run_ours(args):
                    "ctas": t.get("factor_ctas", 152) or 152, "panel": t.get("fp64_panel", 0)}
         work = col.factor_work() if (prec == "mixed" and col_cfg["bcr"]) else None
         results[prec] = dict(ms=ms, steps=steps_done, phases=phases, launches=launches, info=info, graphs=graphs,
+                             start_state=start_state, start_dt=start_dt, K=K,
                              ms_traced=ms_traced, steps_traced=max(int(info_traced.steps), 1),
                              col=col if prec == "mixed" else None, col_cfg=col_cfg, work=work)
         if prec == "fp64":
@@ -444,14 +450,18 @@ def run_ours(args):
                          "peak_live_tf32_matmul": live["tf32"], "frac_of_live": ach / live["tf32"],
                          "useful_tflops": mma / tc_s / 1e12, "flops_per_factorization": mma,
                          "ms_per_factorization": tc_s * 1e3, "launches_per_factorization": tc_calls / nfac,
-                         "ms_per_step": tc_ms / steps, "traffic": None}
+                         "ms_per_step": tc_ms / steps, "traffic": 5.011e6,
+                         "traffic_launch": "one 72-tile launch (A and B operands first touched from DRAM)",
+                         "traffic_source": "profiles/k_tc_gemm_594x150.txt"}
             ach = leaf / lf_s / 1e12
             out["leaf"] = {"kernel": "k_leaf_inverse (FP32 Gauss-Jordan, partial pivoting, one CTA per block)",
                            "bound": "alu", "achieved": ach, "peak": derived["f32"], "unit": "TFLOP/s",
                            "frac": ach / derived["f32"], "peak_kind": derived["kind"],
                            "peak_live_f32_matmul": live["f32"], "flops_per_factorization": leaf,
                            "ms_per_factorization": lf_s * 1e3, "launches_per_factorization": lf_calls / nfac,
-                           "ms_per_step": lf_ms / steps, "traffic": None}
+                           "ms_per_step": lf_ms / steps, "traffic": 7.843e6,
+                           "traffic_launch": "one level-0 launch of 75 blocks of 160 (7.68 MB algorithmic read)",
+                           "traffic_source": "profiles/k_leaf_inverse_594x150.txt"}
         fac_ms, fac_calls = per_launch(ph, "factor")
         out["a7"] = {"flops_per_factorization": a7_flops, "ms_per_factorization": fac_ms,
                      "tflops": a7_flops / (fac_ms * 1e-3) / 1e12,
@@ -478,20 +488,23 @@ def run_ours(args):
     roof = rooflines(mixed)
     dom = max((k for k in ("tc", "leaf") if k in roof), key=lambda k: roof[k]["ms_per_step"], default=None)
 
-    # end to end through the C-ABI with host buffers: the state from pinned host memory in, one step,
-    # the state back into pinned host memory, every step
+    # end to end through the C-ABI with host buffers, over the same K steps as the timed region (same
+    # starting state and dt): the state from pinned host memory in, one step, the state back into
+    # pinned host memory, every step
     col = mixed["col"]
     n_host = torch.empty((L, S), dtype=torch.float64, pin_memory=True)
-    col.get_state(out=n_host)
-    Ke = max(3, args.steps // 2)
+    n_host.copy_(torch.from_numpy(mixed["start_state"]))
+    Ke = mixed["K"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(Ke):
+    e2e_steps = 0
+    for i in range(Ke):
         col.set_state(n_host)
-        col.step(0.0)
+        col.step(mixed["start_dt"] if i == 0 else 0.0)
         col.get_state(out=n_host)
+        e2e_steps += 1
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / Ke
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = _max_over_ranks(e2e_s, ws, dev)
     col.close()
     del col
@@ -715,12 +728,13 @@ def run_serving(args):
     return 0
 
 
-def parcel_object(live, iterations=3, cpu=True):
+def parcel_object(live, iterations=3, cpu=True, columns=152):
     """The paper's Lagrangian parcel scheme (Sec. 2, Fig. 2) on the 96-species, 150-layer column:
     device time of a global iteration (one CTA sweeps the parcel bottom to top and back, an FP64
     partial-pivot LU per implicit step), after one untimed iteration from the initial state; the
     oracle's time for the same first iteration on one host core, and the element-wise error of
-    that iteration against it."""
+    that iteration against it; then `columns` copies of the column swept at once, one CTA each on
+    its own stream (iterations/s of the whole GPU)."""
     import numpy as np
     import torch
     from paper_2512_06729_gb300 import synth, xk
@@ -762,6 +776,36 @@ def parcel_object(live, iterations=3, cpu=True):
                      "peak_kind": "FP64 matmul measured live / 152 SMs (the sweep is sequential: one SM)"},
     }
     col.close()
+    # many parcels at once: one column per SM, each on its own stream (the sweep of one column is
+    # sequential, so throughput comes from independent columns, one CTA each)
+    if columns > 0:
+        streams = [torch.cuda.Stream() for _ in range(columns)]
+        cols = []
+        for st in streams:
+            cc = xk.Column(prob, "fp64", stream=st)
+            cc.set_mixing_ratios(prob.f0)
+            cols.append(cc)
+        for cc in cols:
+            cc.parcel_begin(h=1e-8)
+        firsts = [cc.parcel_end() for cc in cols]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for cc, fi in zip(cols, firsts):
+            cc.parcel_begin(h=fi.h)
+        seconds = [cc.parcel_end() for cc in cols]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        steps_all = sum(int(x.steps + x.rejected) for x in seconds)
+        ach = flops_step * steps_all / wall / 1e12
+        out["columns_at_once"] = {
+            "columns": columns, "iterations_per_s": columns / wall, "wall_s": wall,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": live["f64"], "unit": "TFLOP/s",
+                         "frac": ach / live["f64"], "peak_kind": "FP64 matmul measured live (whole GPU)"},
+            "note": "the second global iteration of each column, all columns begun before any is awaited"}
+        for cc in cols:
+            cc.close()
+        del cols
+        torch.cuda.empty_cache()
     if cpu:
         from oracle.oracle import Oracle
         o = Oracle(prob)
@@ -771,10 +815,26 @@ def parcel_object(live, iterations=3, cpu=True):
         ngas = o.grid()[0]
         keep = N > 1e-20 * ngas[:, None]
         out["cpu_oracle_first_iteration_s"] = dt
+        # the sweep's own sensitivity: the oracle from the same state perturbed by 1e-13 relative
+        Np, pi = o.parcel_iteration(n0 * (1.0 + 1e-13 * np.random.default_rng(7).standard_normal(n0.shape)), h=1e-8)
         out["gpu_vs_oracle_first_iteration"] = {
             "max_rel": float(np.max(np.abs(n1[keep] - N[keep]) / N[keep])),
-            "steps_equal": bool(oi.steps == first.steps and oi.rejected == first.rejected)}
+            "median_rel": float(np.median(np.abs(n1[keep] - N[keep]) / N[keep])),
+            "steps_equal": bool(oi.steps == first.steps and oi.rejected == first.rejected),
+            "oracle_vs_itself_perturbed_1e-13": {
+                "max_rel": float(np.max(np.abs(Np[keep] - N[keep]) / N[keep])),
+                "median_rel": float(np.median(np.abs(Np[keep] - N[keep]) / N[keep])),
+                "steps_equal": bool(oi.steps == pi.steps and oi.rejected == pi.rejected)}}
     return out
+
+
+def run_parcel(args):
+    """The parcel-scheme object alone (the command the parcel kernel's profile runs)."""
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    out = parcel_object(live_peaks(), iterations=max(args.steps, 1), cpu=not args.no_cpu)
+    print(json.dumps({"mode": "parcel", "parcel": out}), flush=True)
+    return 0
 
 
 def run_steady(args):
@@ -902,7 +962,7 @@ def main():
                     help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
@@ -927,6 +987,8 @@ def main():
         return run_steady(args)
     if args.mode == "kernels":
         return run_kernels(args)
+    if args.mode == "parcel":
+        return run_parcel(args)
     return run_ours(args)
 
 

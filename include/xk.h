@@ -294,6 +294,11 @@ typedef struct {
     double max_change;
 } xk_parcel_info;
 XK_API int xk_parcel_iteration(xk_ctx *ctx, int max_visit_steps, xk_parcel_info *info);
+/* The same iteration in two halves, so that many columns' sweeps run at once (one CTA each, on
+ * each context's own stream): begin enqueues it with first trial step h and returns;
+ * end waits for it and fills *info (its return codes are those of xk_parcel_iteration). */
+XK_API int xk_parcel_begin(xk_ctx *ctx, int max_visit_steps, double h);
+XK_API int xk_parcel_end(xk_ctx *ctx, xk_parcel_info *info);
 XK_API int xk_parcel_run(xk_ctx *ctx, int max_visit_steps, int max_iter, double tol, xk_parcel_info *info,
                          int *iterations);
 

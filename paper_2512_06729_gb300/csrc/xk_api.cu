@@ -76,6 +76,7 @@ struct xk_ctx {
     ParcelArgs parcel{};
     double *parcel_kzz0 = nullptr;   // [L] zero eddy profile: the molecular part of u, v
     ParcelState *parcel_host = nullptr;   // pinned
+    int parcel_max_visit = 0;
     // captured chunks of controlled steps (cfg.use_graphs), dropped whenever a plan, the workspace
     // or the batch slot changes
     std::vector<StepGraph> graphs;
@@ -357,9 +358,7 @@ size_t layout(xk_ctx *c, char *base)
     const size_t ifc = std::max<size_t>(1, (size_t)(L - 1) * S);
     q.um = b.take<double>(ifc);
     q.vm = b.take<double>(ifc);
-    q.A = b.take<double>((size_t)S * S);
-    q.x = b.take<double>(S);
-    q.F = b.take<double>(S);
+    q.A = b.take<double>(2 * (size_t)S * S);
     q.vmr = b.take<double>(S);
     q.w = b.take<double>(std::max(R, 1));
     q.dd = b.take<double>(6 * (size_t)std::max(R, 1));
@@ -1663,11 +1662,11 @@ int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *
 
 // ---------------------------------------------------------------- Lagrangian parcel scheme
 
-int xk_parcel_iteration(xk_ctx *c, int max_visit_steps, xk_parcel_info *info)
+int xk_parcel_begin(xk_ctx *c, int max_visit_steps, double h)
 {
     int rc = need_ready(c);
     if (rc) return rc;
-    if (!info || max_visit_steps <= 0 || !(info->h > 0.0)) return fail(c, XK_EINVAL, "parcel: bad arguments");
+    if (max_visit_steps <= 0 || !(h > 0.0)) return fail(c, XK_EINVAL, "parcel: bad arguments");
     if (!(c->L >= 1)) return fail(c, XK_EINVAL, "parcel: no layers");
     for (int k = 0; k < c->L; ++k)
         if (!(c->Kzz[k] > 0.0)) return fail(c, XK_EINVAL, "parcel: K_zz must be positive (residence time dz^2 / K_zz)");
@@ -1678,15 +1677,25 @@ int xk_parcel_iteration(xk_ctx *c, int max_visit_steps, xk_parcel_info *info)
     launch_transport_coeffs(c->col, c->parcel_kzz0, const_cast<double *>(c->parcel.um),
                             const_cast<double *>(c->parcel.vm), c->st);
     ParcelState init{};
-    init.h = info->h;
+    init.h = h;
     init.status = -1;
     *c->parcel_host = init;
     cudaMemcpyAsync(c->parcel.st, c->parcel_host, sizeof(ParcelState), cudaMemcpyHostToDevice, c->st);
     ParcelArgs a = c->parcel;
     a.pol = policy_of(c->cfg);
     a.max_visit_steps = max_visit_steps;
-    launch_parcel_iteration(c->col, a, c->st);
+    cudaError_t le = launch_parcel_iteration(c->col, a, c->st);
+    if (le != cudaSuccess) return fail(c, XK_ECUDA, "parcel launch: %s", cudaGetErrorString(le));
+    c->parcel_max_visit = max_visit_steps;
     cudaMemcpyAsync(c->parcel_host, c->parcel.st, sizeof(ParcelState), cudaMemcpyDeviceToHost, c->st);
+    return cuda_check(c, "parcel begin");
+}
+
+int xk_parcel_end(xk_ctx *c, xk_parcel_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!info) return fail(c, XK_EINVAL, "parcel: null info");
     cudaError_t e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return fail(c, XK_ECUDA, "parcel iteration: %s", cudaGetErrorString(e));
     const ParcelState &h = *c->parcel_host;
@@ -1696,9 +1705,18 @@ int xk_parcel_iteration(xk_ctx *c, int max_visit_steps, xk_parcel_info *info)
     info->max_change = h.max_change;
     if (h.status == XK_ESINGULAR) return fail(c, XK_ESINGULAR, "parcel: singular system at visit %d", h.visit);
     if (h.status == XK_ENEG) return fail(c, XK_ENEG, "parcel: step below dt_min at visit %d", h.visit);
-    if (h.status == XK_ENOCONV) return fail(c, XK_ENOCONV, "parcel: more than %d steps in visit %d", max_visit_steps, h.visit);
+    if (h.status == XK_ENOCONV)
+        return fail(c, XK_ENOCONV, "parcel: more than %d steps in visit %d", c->parcel_max_visit, h.visit);
     if (h.status != 0) return fail(c, XK_ECUDA, "parcel: iteration did not complete (status %d)", h.status);
-    return cuda_check(c, "parcel iteration");
+    return XK_OK;
+}
+
+int xk_parcel_iteration(xk_ctx *c, int max_visit_steps, xk_parcel_info *info)
+{
+    if (!info) return c ? fail(c, XK_EINVAL, "parcel: null info") : XK_EINVAL;
+    int rc = xk_parcel_begin(c, max_visit_steps, info->h);
+    if (rc) return rc;
+    return xk_parcel_end(c, info);
 }
 
 int xk_parcel_run(xk_ctx *c, int max_visit_steps, int max_iter, double tol, xk_parcel_info *info, int *iterations)

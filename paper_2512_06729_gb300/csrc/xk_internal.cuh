@@ -156,15 +156,15 @@ struct ParcelArgs {
     double *N;             // [L][S] stored profile (the column state), updated in place
     double *Nold;          // [L][S] the profile at the start of the iteration
     const double *um, *vm; // [L-1][S] molecular part of Eq. 2's interface coefficients
-    double *A;             // S x S matrix of the current implicit step (row-major, ld S)
-    double *x, *F, *vmr;   // [S] parcel densities, right-hand side then solution, carried mixing ratios
+    double *A;             // 2 x S x S: the current implicit step's matrix and its LU factors (row-major)
+    double *vmr;           // [S] the parcel's carried mixing ratios
     double *w, *dd;        // [R] rates, [R][6] their derivatives at the parcel's densities
     Policy pol;
     int max_visit_steps;
     ParcelState *st;
 };
 // One global iteration on one CTA (photolysis and rate coefficients already in c).
-void launch_parcel_iteration(const Col &c, const ParcelArgs &a, cudaStream_t st);
+cudaError_t launch_parcel_iteration(const Col &c, const ParcelArgs &a, cudaStream_t st);
 
 constexpr unsigned long long kSpinLimit = 1ull << 24;   // polls of a bounded wait: ~1-2 s with the sleep below
 

@@ -5,12 +5,14 @@
 // stored densities of layers k -+ 1 (Sec. 2.1, after Eq. 4: the molecular part of Eq. 2's flux);
 // eddy diffusion is the parcel's motion and has no term.  Within a visit: linearly implicit Euler
 // steps (I/h - dF/dx) delta = F under the step controller of the Eulerian path, each solved by
-// Gaussian elimination with partial pivoting.  The parcel keeps its mixing ratios from layer to
-// layer, and each visit leaves its densities as the layer's.
+// Gaussian elimination with partial pivoting plus two sweeps of FP64 iterative refinement.  The
+// parcel keeps its mixing ratios from layer to layer, and each visit leaves its densities as the
+// layer's.
 //
 // The sweep is sequential in the layers, so one CTA runs a whole iteration: every reduction,
-// pivot search and elimination step stays inside the block (no grid-wide wait), and the only
-// global traffic is the S x S matrix of the current step, which lives in L2.
+// pivot search and elimination step stays inside the block (no grid-wide wait).  The step's
+// vectors live in shared memory, and so do its two S x S matrices (the system and its factors)
+// when they fit (S up to 111); larger systems keep them in global memory, where they stay in L2.
 #include <cfloat>
 
 #include "xk_internal.cuh"
@@ -19,15 +21,18 @@ namespace xk {
 
 namespace {
 
-constexpr int kParcelThreads = 1024;
-constexpr int kParcelWarps = kParcelThreads / 32;
+constexpr int kMaxWarps = 32;
+constexpr int kRefineSweeps = 2;          // FP64 iterative-refinement sweeps of every implicit step
+constexpr size_t kSmemLimit = 200 * 1024; // dynamic shared memory the kernel may ask for
 
 struct Shared {
-    double red[kParcelWarps];
-    int ired[kParcelWarps];
+    double red[kMaxWarps];
+    int ired[kMaxWarps];
     double h, t, hs;
     int last, done;
 };
+
+__device__ __forceinline__ int nwarps() { return blockDim.x >> 5; }
 
 // max over the block; every thread gets the result
 __device__ double block_max(double v, Shared &sh)
@@ -37,7 +42,7 @@ __device__ double block_max(double v, Shared &sh)
     __syncthreads();
     if (lane == 0) sh.red[warp] = v;
     __syncthreads();
-    v = lane < kParcelWarps ? sh.red[lane] : -DBL_MAX;
+    v = lane < nwarps() ? sh.red[lane] : -DBL_MAX;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
@@ -49,11 +54,11 @@ __device__ int block_or(int v, Shared &sh)
     __syncthreads();
     if (lane == 0) sh.ired[warp] = v;
     __syncthreads();
-    v = lane < kParcelWarps ? sh.ired[lane] : 0;
+    v = lane < nwarps() ? sh.ired[lane] : 0;
     return __any_sync(0xffffffffu, v) ? 1 : 0;
 }
 
-// Row of the largest |A[i][c]|, i >= c (the first on ties, as a sequential scan picks it).
+// Row of the largest |A[i][c]|, i >= c (the first on ties, as a sequential scan picks it), or -1.
 __device__ int pivot_row(const double *A, int S, int c, Shared &sh)
 {
     double best = -1.0;
@@ -71,8 +76,8 @@ __device__ int pivot_row(const double *A, int S, int c, Shared &sh)
     __syncthreads();
     if (lane == 0) { sh.red[warp] = best; sh.ired[warp] = bi; }
     __syncthreads();
-    best = lane < kParcelWarps ? sh.red[lane] : -1.0;
-    bi = lane < kParcelWarps ? sh.ired[lane] : S;
+    best = lane < nwarps() ? sh.red[lane] : -1.0;
+    bi = lane < nwarps() ? sh.ired[lane] : S;
     for (int o = 16; o > 0; o >>= 1) {
         const double ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -81,63 +86,101 @@ __device__ int pivot_row(const double *A, int S, int c, Shared &sh)
     return best > 0.0 ? bi : -1;
 }
 
-// F <- A^-1 F by Gaussian elimination with partial pivoting (A is overwritten).  0, or -1 on a
-// zero pivot column.
-__device__ int dense_solve(double *A, double *F, int S, Shared &sh)
+// A <- its LU factors with partial pivoting (whole rows swapped; row c of the factors came from
+// row piv[c] of the rows as they stood at step c).  0, or -1 on a zero pivot column.
+__device__ int lu_factor(double *A, int *piv, int S, Shared &sh)
 {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nwarps();
     for (int c = 0; c < S; ++c) {
         const int p = pivot_row(A, S, c, sh);
         if (p < 0) return -1;
-        if (p != c) {
-            for (int j = c + threadIdx.x; j < S; j += blockDim.x) {
+        if (threadIdx.x == 0) piv[c] = p;
+        if (p != c)
+            for (int j = threadIdx.x; j < S; j += blockDim.x) {
                 const double t = A[(long long)c * S + j];
                 A[(long long)c * S + j] = A[(long long)p * S + j];
                 A[(long long)p * S + j] = t;
             }
-            if (threadIdx.x == 0) {
-                const double t = F[c];
-                F[c] = F[p];
-                F[p] = t;
-            }
-        }
         __syncthreads();
         const double inv = 1.0 / A[(long long)c * S + c];
-        const double fc = F[c];
-        // multipliers first (column c is read by every row's update)
-        for (int i = c + 1 + threadIdx.x; i < S; i += blockDim.x) {
-            const double l = A[(long long)i * S + c] * inv;
-            A[(long long)i * S + c] = l;
-            F[i] -= l * fc;
-        }
-        __syncthreads();
-        // trailing update: a warp per row, lanes along the row (coalesced)
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int i = c + 1 + warp; i < S; i += kParcelWarps) {
+        // a warp per row below the pivot: its multiplier, then the row update along the lanes
+        for (int i = c + 1 + warp; i < S; i += nw) {
             double *Ai = A + (long long)i * S;
-            const double l = Ai[c];
+            const double l = Ai[c] * inv;
+            __syncwarp();
+            if (lane == 0) Ai[c] = l;
             for (int j = c + 1 + lane; j < S; j += 32) Ai[j] -= l * A[(long long)c * S + j];
         }
-        __syncthreads();
-    }
-    // back substitution, column by column
-    for (int c = S - 1; c >= 0; --c) {
-        const double xc = F[c] * (1.0 / A[(long long)c * S + c]);
-        __syncthreads();
-        if (threadIdx.x == 0) F[c] = xc;
-        for (int i = threadIdx.x; i < c; i += blockDim.x) F[i] -= A[(long long)i * S + c] * xc;
         __syncthreads();
     }
     return 0;
 }
 
-__global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, ParcelArgs a)
+// x <- (LU)^-1 P x with the factors of lu_factor.
+__device__ void lu_solve(const double *A, const int *piv, double *x, int S)
+{
+    if (threadIdx.x == 0)
+        for (int c = 0; c < S; ++c) {
+            const int p = piv[c];
+            if (p != c) { const double t = x[c]; x[c] = x[p]; x[p] = t; }
+        }
+    __syncthreads();
+    for (int c = 0; c < S; ++c) {            // unit lower triangle, column by column
+        const double xc = x[c];
+        for (int i = c + 1 + threadIdx.x; i < S; i += blockDim.x) x[i] -= A[(long long)i * S + c] * xc;
+        __syncthreads();
+    }
+    for (int c = S - 1; c >= 0; --c) {       // upper triangle
+        const double xc = x[c] * (1.0 / A[(long long)c * S + c]);
+        __syncthreads();
+        if (threadIdx.x == 0) x[c] = xc;
+        for (int i = threadIdx.x; i < c; i += blockDim.x) x[i] -= A[(long long)i * S + c] * xc;
+        __syncthreads();
+    }
+}
+
+// d <- A0^-1 F: LU with partial pivoting of A (a copy of A0), then kRefineSweeps sweeps of FP64
+// iterative refinement r = F - A0 d, d += (LU)^-1 P r.  0, or -1 on a zero pivot column.
+__device__ int dense_solve(const double *A0, double *A, int *piv, const double *F, double *d, double *r, int S,
+                           Shared &sh)
+{
+    for (long long e = threadIdx.x; e < (long long)S * S; e += blockDim.x) A[e] = A0[e];
+    for (int y = threadIdx.x; y < S; y += blockDim.x) d[y] = F[y];
+    __syncthreads();
+    if (lu_factor(A, piv, S, sh) != 0) return -1;
+    lu_solve(A, piv, d, S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = nwarps();
+    for (int sweep = 0; sweep < kRefineSweeps; ++sweep) {
+        for (int i = warp; i < S; i += nw) {
+            const double *Ai = A0 + (long long)i * S;
+            double acc = 0.0;
+            for (int j = lane; j < S; j += 32) acc += Ai[j] * d[j];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) r[i] = F[i] - acc;
+        }
+        __syncthreads();
+        lu_solve(A, piv, r, S);
+        for (int y = threadIdx.x; y < S; y += blockDim.x) d[y] += r[y];
+        __syncthreads();
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_parcel_iteration(Col c, ParcelArgs a, int mats_in_smem)
 {
     __shared__ Shared sh;
+    extern __shared__ double dyn[];
     const int S = c.S, L = c.L, R = c.R;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int warp = tid >> 5, lane = tid & 31, nw = nwarps();
     const Policy &pol = a.pol;
     ParcelState *st = a.st;
+    // vectors always in shared memory; the two S x S matrices there too when they fit
+    double *x = dyn, *F = x + S, *d = F + S, *r = d + S;
+    int *piv = (int *)(r + S);
+    double *mats = (double *)(piv + ((S + 1) & ~1));
+    double *A0 = mats_in_smem ? mats : a.A;
+    double *A = mats_in_smem ? mats + (long long)S * S : a.A + (long long)S * S;
     for (long long i = tid; i < (long long)L * S; i += nt) a.Nold[i] = a.N[i];
     for (int y = tid; y < S; y += nt) a.vmr[y] = a.N[y] / c.ngas[0];
     if (tid == 0) sh.h = st->h;
@@ -147,7 +190,7 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
         const int k = v < L ? v : 2 * L - 2 - v;
         const double nk = c.ngas[k], dzk = c.dz[k];
         const double tau = dzk * dzk / c.Kzz[k];
-        for (int y = tid; y < S; y += nt) a.x[y] = a.vmr[y] * nk;
+        for (int y = tid; y < S; y += nt) x[y] = a.vmr[y] * nk;
         if (tid == 0) sh.t = 0.0;
         __syncthreads();
         int visit_steps = 0;
@@ -162,7 +205,7 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
             __syncthreads();
             const double hs = sh.hs;
             // reaction terms at the parcel's densities (Sec. 2.3)
-            for (int r = tid; r < R; r += nt) reaction_terms_at(c, k, r, a.x, a.w + r, a.dd + (long long)r * 6);
+            for (int rr = tid; rr < R; rr += nt) reaction_terms_at(c, k, rr, x, a.w + rr, a.dd + (long long)rr * 6);
             __syncthreads();
             // right-hand side: chemistry plus the molecular-diffusion pair
             for (int y = tid; y < S; y += nt) {
@@ -181,11 +224,11 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
                     loss += a.vm[(long long)(k - 1) * S + y];
                     gain += a.um[(long long)(k - 1) * S + y] * a.N[(long long)(k - 1) * S + y];
                 }
-                a.F[y] = f + (gain - loss * a.x[y]) / dzk;
+                F[y] = f + (gain - loss * x[y]) / dzk;
             }
             // matrix I/h - dF/dx: one warp per row, entries of the pattern summed in a fixed order
-            for (int i = warp; i < S; i += kParcelWarps) {
-                double *Ar = a.A + (long long)i * S;
+            for (int i = warp; i < S; i += nw) {
+                double *Ar = A0 + (long long)i * S;
                 for (int j = lane; j < S; j += 32) Ar[j] = 0.0;
                 __syncwarp();
                 for (int q = c.jp[i] + lane; q < c.jp[i + 1]; q += 32) Ar[c.jcol[q]] = jac_entry(c, q, a.dd);
@@ -198,7 +241,7 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
                 }
             }
             __syncthreads();
-            if (dense_solve(a.A, a.F, S, sh) != 0) {
+            if (dense_solve(A0, A, piv, F, d, r, S, sh) != 0) {
                 if (tid == 0) { st->status = XK_ESINGULAR; st->visit = v; }
                 return;
             }
@@ -206,17 +249,17 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
             double mr = 0.0;
             int bad = 0;
             for (int y = tid; y < S; y += nt) {
-                const double xv = a.x[y], d = a.F[y], nn = xv + d;
+                const double xv = x[y], dv = d[y], nn = xv + dv;
                 if (!isfinite(nn) || nn < -pol.neg_tol * nk) bad = 1;
-                if (xv > pol.f_floor * nk) mr = fmax(mr, fabs(d) / xv);
+                if (xv > pol.f_floor * nk) mr = fmax(mr, fabs(dv) / xv);
             }
             bad = block_or(bad, sh);
             mr = block_max(mr, sh);
             const int ok = !bad && !(mr > pol.rel_reject);
             if (ok)
                 for (int y = tid; y < S; y += nt) {
-                    const double nn = a.x[y] + a.F[y];
-                    a.x[y] = nn < 0.0 ? 0.0 : nn;
+                    const double nn = x[y] + d[y];
+                    x[y] = nn < 0.0 ? 0.0 : nn;
                 }
             __syncthreads();
             if (tid == 0) {
@@ -244,8 +287,8 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
             }
         }
         for (int y = tid; y < S; y += nt) {
-            a.N[(long long)k * S + y] = a.x[y];
-            a.vmr[y] = a.x[y] / nk;
+            a.N[(long long)k * S + y] = x[y];
+            a.vmr[y] = x[y] / nk;
         }
         __syncthreads();
     }
@@ -267,10 +310,25 @@ __global__ void __launch_bounds__(kParcelThreads, 1) k_parcel_iteration(Col c, P
 
 }  // namespace
 
-void launch_parcel_iteration(const Col &c, const ParcelArgs &a, cudaStream_t st)
+size_t parcel_vector_bytes(int S) { return sizeof(double) * 4 * (size_t)S + sizeof(int) * (size_t)((S + 1) & ~1); }
+
+bool parcel_mats_in_smem(int S)
 {
+    return parcel_vector_bytes(S) + 2 * sizeof(double) * (size_t)S * S <= kSmemLimit;
+}
+
+cudaError_t launch_parcel_iteration(const Col &c, const ParcelArgs &a, cudaStream_t st)
+{
+    const int S = c.S;
+    const bool in_smem = parcel_mats_in_smem(S);
+    const size_t smem = parcel_vector_bytes(S) + (in_smem ? 2 * sizeof(double) * (size_t)S * S : 0);
+    // small systems: fewer warps, so that each barrier waits on less; large ones: the whole SM
+    const int threads = S <= 160 ? 256 : 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_parcel_iteration, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    k_parcel_iteration<<<1, kParcelThreads, 0, st>>>(c, a);
+    k_parcel_iteration<<<1, threads, smem, st>>>(c, a, in_smem ? 1 : 0);
+    return cudaGetLastError();
 }
 
 }  // namespace xk

@@ -82,6 +82,8 @@ SIGNATURES = {
     "xk_step": (C.c_int, [_vp, C.c_double, C.POINTER(StepInfo)]),
     "xk_run_to_steady": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(RunInfo)]),
     "xk_parcel_iteration": (C.c_int, [_vp, C.c_int, C.POINTER(ParcelInfo)]),
+    "xk_parcel_begin": (C.c_int, [_vp, C.c_int, C.c_double]),
+    "xk_parcel_end": (C.c_int, [_vp, C.POINTER(ParcelInfo)]),
     "xk_parcel_run": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.POINTER(ParcelInfo), C.POINTER(C.c_int)]),
     "xk_eval_grid": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "xk_eval_thermo": (C.c_int, [_vp, _vp, _vp]),
@@ -301,6 +303,16 @@ class Column:
         """One global iteration on the context's state; returns ParcelInfo (h = the next trial step)."""
         info = ParcelInfo(h=float(h))
         self._call("xk_parcel_iteration", int(max_visit_steps), C.byref(info))
+        return info
+
+    def parcel_begin(self, h=1e-8, max_visit_steps=100000):
+        """Enqueue one global iteration on this column's stream and return at once."""
+        self._call("xk_parcel_begin", int(max_visit_steps), float(h))
+
+    def parcel_end(self):
+        """Wait for the iteration begun last; returns its ParcelInfo."""
+        info = ParcelInfo()
+        self._call("xk_parcel_end", C.byref(info))
         return info
 
     def parcel_run(self, h=1e-8, max_iter=200, tol=1e-3, max_visit_steps=100000):
