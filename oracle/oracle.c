@@ -893,3 +893,264 @@ int ora_parcel_run(const ora_problem *p, const ora_policy *pol, int max_visit_st
         return rc;
     return info->max_change < tol ? 0 : 1;
 }
+
+/* ------------------------------------------- equilibrium initial state */
+/*
+ * Sec. 2.5, option (i): the initial composition in chemical equilibrium.  Per layer,
+ * at the layer's T and P, the ideal-gas mixture of minimum Gibbs energy
+ *     G/RT = sum_y N_y (g_y + ln(P/p0) + ln(N_y / N)),   N = sum_y N_y,
+ * subject to the element totals sum_y a_ey N_y = b_e, with g_y = G_y/RT from the NASA-7
+ * sets (Appendix A).  At the minimum every species satisfies
+ *     g_y + ln(P/p0) + ln x_y = sum_e pi_e a_ey
+ * with element potentials pi_e.  Solved by Newton iterations on that condition,
+ * linearised in ln N_y, ln N and pi (the reduced Gibbs iteration of the NASA
+ * equilibrium program, Gordon & McBride 1994): each iteration solves one
+ * (E+1) x (E+1) system for pi and d ln N, then sets
+ *     d ln N_y = -(g_y + ln(P/p0) + ln N_y - ln N) + sum_e pi_e a_ey + d ln N,
+ * with the step limited so that no major species' ln N_y moves by more than 2 and
+ * no trace species rises above about 1e-4 of N in one step.  Start: every species
+ * 1/S_active, N = 1, b normalised to sum 1.  At convergence the mole fractions are
+ * taken from the potentials, x_y = exp(sum_e pi_e a_ey - g_y - ln(P/p0)), normalised,
+ * which keeps trace species exact in relative terms.  An element with b_e <= 0 is
+ * absent: its potential is not solved for and every species containing it has x = 0.
+ */
+int ora_equilibrium(const ora_problem *p, const double *b, double *x, int max_iter, double tol, int *iters)
+{
+    int S = p->S, E = p->E, M = p->E + 1;
+    double *lnN = malloc(sizeof(double) * S * 3), *nj = lnN + S, *mu = nj + S;
+    double *A = malloc(sizeof(double) * M * (M + 1)), *sol = malloc(sizeof(double) * M);
+    int *act = malloc(sizeof(int) * (S + E)), *eact = act + S;
+    int worst = 0, rc = 0, notconv = 0;
+    for (int k = 0; k < p->L && rc == 0; ++k) {
+        const double *bk = b + (size_t)k * E;
+        double *xk = x + (size_t)k * S;
+        double T = p->T[k], lnP = log(p->P_bar[k]);
+        double bsum = 0.0;
+        for (int e = 0; e < E; ++e) {
+            eact[e] = bk[e] > 0.0;
+            if (eact[e]) bsum += bk[e];
+        }
+        int nact = 0;
+        for (int y = 0; y < S; ++y) {
+            act[y] = 1;
+            for (int e = 0; e < E; ++e)
+                if (p->elem[y * E + e] > 0 && !eact[e]) act[y] = 0;
+            nact += act[y];
+        }
+        if (nact == 0 || bsum <= 0.0) { rc = -1; break; }
+        for (int y = 0; y < S; ++y)
+            lnN[y] = act[y] ? log(1.0 / nact) : 0.0;
+        double lntot = 0.0;
+        int it, done = 0;
+        for (it = 0; it < max_iter; ++it) {
+            double ntot = exp(lntot);
+            for (int y = 0; y < S; ++y) {
+                if (!act[y]) { nj[y] = 0.0; mu[y] = 0.0; continue; }
+                nj[y] = exp(lnN[y]);
+                mu[y] = ora_gibbs_rt(p->nasa + 15 * y, T) + lnP + lnN[y] - lntot;
+            }
+            /* the (E+1) x (E+1) system, augmented with its right-hand side in column M */
+            for (int i = 0; i < M * (M + 1); ++i)
+                A[i] = 0.0;
+            for (int i = 0; i < E; ++i) {
+                if (!eact[i]) { A[i * (M + 1) + i] = 1.0; continue; }
+                for (int j = 0; j < E; ++j) {
+                    if (!eact[j]) continue;
+                    double s = 0.0;
+                    for (int y = 0; y < S; ++y)
+                        s += (double)p->elem[y * E + i] * p->elem[y * E + j] * nj[y];
+                    A[i * (M + 1) + j] = s;
+                }
+                double c = 0.0, d = 0.0;
+                for (int y = 0; y < S; ++y) {
+                    c += p->elem[y * E + i] * nj[y];
+                    d += p->elem[y * E + i] * nj[y] * mu[y];
+                }
+                A[i * (M + 1) + E] = c;
+                A[E * (M + 1) + i] = c;
+                A[i * (M + 1) + M] = bk[i] / bsum - c + d;
+            }
+            double sn = 0.0, snm = 0.0;
+            for (int y = 0; y < S; ++y) {
+                sn += nj[y];
+                snm += nj[y] * mu[y];
+            }
+            A[E * (M + 1) + E] = sn - ntot;
+            A[E * (M + 1) + M] = ntot - sn + snm;
+            /* Gaussian elimination with partial pivoting */
+            for (int c = 0; c < M && rc == 0; ++c) {
+                int best = c;
+                for (int i = c + 1; i < M; ++i)
+                    if (fabs(A[i * (M + 1) + c]) > fabs(A[best * (M + 1) + c])) best = i;
+                if (A[best * (M + 1) + c] == 0.0) { rc = -1; break; }
+                if (best != c)
+                    for (int j = 0; j <= M; ++j) {
+                        double t = A[c * (M + 1) + j];
+                        A[c * (M + 1) + j] = A[best * (M + 1) + j];
+                        A[best * (M + 1) + j] = t;
+                    }
+                for (int i = c + 1; i < M; ++i) {
+                    double l = A[i * (M + 1) + c] / A[c * (M + 1) + c];
+                    for (int j = c; j <= M; ++j)
+                        A[i * (M + 1) + j] -= l * A[c * (M + 1) + j];
+                }
+            }
+            if (rc) break;
+            for (int i = M - 1; i >= 0; --i) {
+                double s = A[i * (M + 1) + M];
+                for (int j = i + 1; j < M; ++j)
+                    s -= A[i * (M + 1) + j] * sol[j];
+                sol[i] = s / A[i * (M + 1) + i];
+            }
+            double dlntot = sol[E];
+            /* step limit and convergence measure */
+            double big = 5.0 * fabs(dlntot), lam2 = 1.0, conv = 0.0;
+            for (int y = 0; y < S; ++y) {
+                if (!act[y]) continue;
+                double d = -mu[y] + dlntot;
+                for (int e = 0; e < E; ++e)
+                    if (eact[e]) d += sol[e] * p->elem[y * E + e];
+                mu[y] = d;   /* now d ln N_y */
+                double lx = lnN[y] - lntot;
+                if (lx > log(1e-8)) {
+                    if (fabs(d) > big) big = fabs(d);
+                } else if (d - dlntot > 0.0) {
+                    double v = fabs((-lx - 9.2103) / (d - dlntot));
+                    if (v < lam2) lam2 = v;
+                }
+                conv += nj[y] * fabs(d);
+            }
+            conv /= sn;
+            double lam = 1.0;
+            if (big > 2.0) lam = 2.0 / big;
+            if (lam2 < lam) lam = lam2;
+            for (int y = 0; y < S; ++y)
+                if (act[y]) lnN[y] += lam * mu[y];
+            lntot += lam * dlntot;
+            if (conv < tol && fabs(dlntot) < tol) { done = 1; break; }
+        }
+        if (rc) break;
+        if (it + 1 > worst) worst = it + 1;
+        if (!done) { notconv = 1; worst = max_iter; }
+        /* mole fractions from the potentials of the last solve, normalised */
+        double amax = -INFINITY;
+        for (int y = 0; y < S; ++y) {
+            if (!act[y]) continue;
+            double a = -ora_gibbs_rt(p->nasa + 15 * y, T) - lnP;
+            for (int e = 0; e < E; ++e)
+                if (eact[e]) a += sol[e] * p->elem[y * E + e];
+            xk[y] = a;
+            if (a > amax) amax = a;
+        }
+        double z = 0.0;
+        for (int y = 0; y < S; ++y)
+            if (act[y]) z += exp(xk[y] - amax);
+        for (int y = 0; y < S; ++y)
+            xk[y] = act[y] ? exp(xk[y] - amax - log(z)) : 0.0;
+    }
+    if (iters) *iters = worst;
+    free(lnN);
+    free(A);
+    free(sol);
+    free(act);
+    return rc ? rc : notconv;
+}
+
+/* ------------------------------------------------ reaction pathways */
+/*
+ * Sec. 4, the reaction-pathway analyser: the kinetically fastest route between two
+ * species is the path of least total inverse rate, found with Dijkstra's algorithm.
+ * Graph of one layer: each reaction direction with a positive rate q (molecules
+ * cm^-3 s^-1; forward q = k_f prod n_reac, reverse q = k_r prod n_prod, photolysis
+ * forward only) gives an edge from each species it consumes to each species it
+ * produces (other than itself), of weight 1/q.  Edge code = 2 r + direction
+ * (0 forward, 1 reverse).  The rate-limiting step of a path is its edge of largest
+ * weight (the slowest reaction).
+ */
+void ora_fluxes(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                const double *n, double *q)
+{
+    int L = p->L, S = p->S, R = p->R;
+    double *kf_k = malloc(sizeof(double) * R * 2), *kr_k = kf_k + R;
+    for (int k = 0; k < L; ++k) {
+        const double *nk = n + (size_t)k * S;
+        layer_rates(p, k, kf, kr, kph, kf_k, kr_k);
+        for (int r = 0; r < R; ++r) {
+            double wf = kf_k[r], wb = kr_k[r];
+            for (int s = 0; s < 3; ++s) {
+                if (p->reac[3 * r + s] >= 0) wf *= nk[p->reac[3 * r + s]];
+                if (p->prod[3 * r + s] >= 0) wb *= nk[p->prod[3 * r + s]];
+            }
+            q[((size_t)k * R + r) * 2 + 0] = wf;
+            q[((size_t)k * R + r) * 2 + 1] = wb;
+        }
+    }
+    free(kf_k);
+}
+
+static int side_has(const int *side3, int y)
+{
+    return side3[0] == y || side3[1] == y || side3[2] == y;
+}
+
+/* Dijkstra from src on the graph of one layer (q: R x 2 rates).  The unfinished species
+ * of least distance is taken next (the lower index on ties); an edge replaces a
+ * predecessor only when it makes the distance strictly smaller, edges scanned in
+ * increasing edge code.  dist = +inf and pred = -1 where unreachable. */
+void ora_pathways(const ora_problem *p, const double *q, int src, double *dist, int *pred_sp,
+                  int *pred_edge, int *lim_edge, double *lim_w)
+{
+    int S = p->S, R = p->R;
+    int *done = malloc(sizeof(int) * S * 2), *order = done + S;
+    for (int y = 0; y < S; ++y) {
+        dist[y] = INFINITY;
+        pred_sp[y] = -1;
+        pred_edge[y] = -1;
+        lim_edge[y] = -1;
+        lim_w[y] = 0.0;
+        done[y] = 0;
+    }
+    dist[src] = 0.0;
+    int nord = 0;
+    for (;;) {
+        int u = -1;
+        for (int y = 0; y < S; ++y)
+            if (!done[y] && dist[y] < INFINITY && (u < 0 || dist[y] < dist[u])) u = y;
+        if (u < 0) break;
+        done[u] = 1;
+        order[nord++] = u;
+        for (int r = 0; r < R; ++r)
+            for (int dir = 0; dir < 2; ++dir) {
+                const int *from = dir == 0 ? p->reac + 3 * r : p->prod + 3 * r;
+                const int *to = dir == 0 ? p->prod + 3 * r : p->reac + 3 * r;
+                double rate = q[(size_t)r * 2 + dir];
+                if (!(rate > 0.0) || !side_has(from, u)) continue;
+                double w = 1.0 / rate;
+                for (int s = 0; s < 3; ++s) {
+                    int v = to[s];
+                    if (v < 0 || v == u) continue;
+                    double cand = dist[u] + w;
+                    if (cand < dist[v]) {
+                        dist[v] = cand;
+                        pred_sp[v] = u;
+                        pred_edge[v] = 2 * r + dir;
+                    }
+                }
+            }
+    }
+    /* slowest step along each path, in the order the species were finished */
+    for (int i = 0; i < nord; ++i) {
+        int v = order[i], u = pred_sp[v];
+        if (u < 0) continue;
+        int e = pred_edge[v];
+        double w = 1.0 / q[e];
+        if (u == src || w > lim_w[u]) {
+            lim_edge[v] = e;
+            lim_w[v] = w;
+        } else {
+            lim_edge[v] = lim_edge[u];
+            lim_w[v] = lim_w[u];
+        }
+    }
+    free(done);
+}

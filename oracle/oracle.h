@@ -118,6 +118,23 @@ int ora_parcel_iteration(const ora_problem *p, const ora_policy *pol, int max_vi
 int ora_parcel_run(const ora_problem *p, const ora_policy *pol, int max_visit_steps, int max_iter, double tol,
                    double *N, ora_parcel_info *info, int *iterations);
 
+/* Sec. 2.5 option (i): chemical-equilibrium composition per layer at the layer's T and P, the
+ * ideal-gas mixture of minimum Gibbs energy with element totals b [L][E] (any common unit; an
+ * element with b <= 0 is absent).  x [L][S] receives mole fractions (sum 1).  Returns 0, 1 when a
+ * layer did not converge within max_iter (tol on the Newton update of ln N_y and ln N), -1 on a
+ * singular system.  *iters: the most iterations any layer took. */
+int ora_equilibrium(const ora_problem *p, const double *b, double *x, int max_iter, double tol, int *iters);
+/* Forward and reverse rate of every reaction in every layer at state n: q [L][R][2] (molecules
+ * cm^-3 s^-1; photolysis forward only). */
+void ora_fluxes(const ora_problem *p, const double *kf, const double *kr, const double *kph,
+                const double *n, double *q);
+/* Sec. 4 reaction-pathway analyser on one layer (q: that layer's [R][2] rates): Dijkstra from src
+ * with edge weights 1/q from each consumed to each produced species.  dist [S] (+inf unreachable),
+ * pred_sp [S] predecessor species, pred_edge [S] edge code 2 r + direction (0 forward, 1 reverse),
+ * lim_edge / lim_w [S] the slowest step of the path and its weight; -1 where there is none. */
+void ora_pathways(const ora_problem *p, const double *q, int src, double *dist, int *pred_sp,
+                  int *pred_edge, int *lim_edge, double *lim_w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -104,6 +104,12 @@ def lib():
         l.ora_parcel_run.argtypes = [P, C.POINTER(Policy), C.c_int, C.c_int, C.c_double, _dp,
                                      C.POINTER(ParcelInfo), _ip]
         l.ora_parcel_run.restype = C.c_int
+        l.ora_equilibrium.argtypes = [P, _dp, _dp, C.c_int, C.c_double, _ip]
+        l.ora_equilibrium.restype = C.c_int
+        l.ora_fluxes.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
+        l.ora_fluxes.restype = None
+        l.ora_pathways.argtypes = [P, _dp, C.c_int, _dp, _ip, _ip, _ip, _dp]
+        l.ora_pathways.restype = None
         _lib = l
     return _lib
 
@@ -271,3 +277,41 @@ class Oracle:
         if rc < 0:
             raise ArithmeticError(f"parcel run failed ({rc})")
         return m, it.value, info, rc == 0
+
+    # -- equilibrium initial state (Sec. 2.5) and pathway analysis (Sec. 4) ---------
+    def element_totals(self, n):
+        """Element totals b [L][E] = sum_y a_ey n_y of a state (a plain contraction)."""
+        return np.ascontiguousarray(np.asarray(n, np.float64) @ self.p.elem.astype(np.float64))
+
+    def equilibrium(self, b, max_iter=300, tol=1e-12):
+        """Mole fractions [L][S] of the Gibbs minimum for element totals b [L][E]; returns
+        (x, iterations, converged)."""
+        b = np.ascontiguousarray(b, np.float64)
+        x = np.zeros((self.L, self.S))
+        it = C.c_int(0)
+        rc = lib().ora_equilibrium(C.byref(self.st), _d(b), _d(x), int(max_iter), float(tol), C.byref(it))
+        if rc < 0:
+            raise ArithmeticError("equilibrium: singular system")
+        return x, it.value, rc == 0
+
+    def fluxes(self, n, kf=None, kr=None, kph=None):
+        """Forward and reverse rate of every reaction: q [L][R][2]."""
+        if kf is None:
+            kf, kr = self.rate_coefficients()
+        if kph is None:
+            kph = self.photolysis(n)
+        q = np.zeros((self.L, self.R, 2))
+        lib().ora_fluxes(C.byref(self.st), _d(np.ascontiguousarray(kf)), _d(np.ascontiguousarray(kr)),
+                         _d(np.ascontiguousarray(kph if np.size(kph) else np.zeros(1))),
+                         _d(np.ascontiguousarray(n, np.float64)), _d(q))
+        return q
+
+    def pathways(self, q_layer, src):
+        """Dijkstra from src on one layer's rates q_layer [R][2]; returns dict of dist, pred_sp,
+        pred_edge, lim_edge, lim_w."""
+        S = self.S
+        dist = np.zeros(S); lim_w = np.zeros(S)
+        pred_sp = np.zeros(S, np.int32); pred_edge = np.zeros(S, np.int32); lim_edge = np.zeros(S, np.int32)
+        lib().ora_pathways(C.byref(self.st), _d(np.ascontiguousarray(q_layer, np.float64)), int(src), _d(dist),
+                           _i(pred_sp), _i(pred_edge), _i(lim_edge), _d(lim_w))
+        return dict(dist=dist, pred_sp=pred_sp, pred_edge=pred_edge, lim_edge=lim_edge, lim_w=lim_w)
