@@ -525,7 +525,7 @@ def run_ours(args):
             errs = err_vs_oracle(prob, tuning)
         if not args.no_steady:
             steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
-    batch = serving_obj = parcel = None
+    batch = serving_obj = parcel = analysis = None
     if rank == 0 and ws == 1:
         if not args.no_batch:
             batch = batch_object(args.columns, steps=5, warmup=3, tune=not args.no_tune)
@@ -533,6 +533,8 @@ def run_ours(args):
             serving_obj = serving_object(args.requests, args.rate, args.slots, args.serving_deadline)
         if not args.no_parcel:
             parcel = parcel_object(live, cpu=not args.no_cpu)
+        if not args.no_analysis:
+            analysis = analysis_object(live, cpu=not args.no_cpu)
     if rank == 0:
         ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items() if v[1]}
         ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items() if v[1]}
@@ -566,6 +568,7 @@ def run_ours(args):
             "batch": batch,
             "serving": serving_obj,
             "parcel": parcel,
+            "analysis": analysis,
             "traced": {"ms_per_step": mixed["ms_traced"] / mixed["steps_traced"],
                        "note": "the next steps with every kernel launched from the host between CUDA event "
                                "pairs (phases_ms comes from this run)"},
@@ -837,6 +840,91 @@ def run_parcel(args):
     return 0
 
 
+def analysis_object(live, calls=5, cpu=True, sources=8):
+    """Equilibrium initial state (Sec. 2.5) and reaction-pathway analyser (Sec. 4) on the
+    594-species, 7,720-reaction, 150-layer column from its initial state: device time of one
+    equilibrium solve of all layers (one CTA per layer) and of Dijkstra searches from `sources`
+    species in every layer (one warp each), each the mean of `calls` calls after one untimed call;
+    errors against the oracle (equilibrium: every layer; pathways: bitwise on the oracle's rates)."""
+    import numpy as np
+    import torch
+    from paper_2512_06729_gb300 import synth, xk
+    prob = synth.full_column()
+    S, L, E, R = prob.S, prob.L, prob.E, prob.R
+    col = xk.Column(prob, "fp64")
+    col.set_mixing_ratios(prob.f0)
+    n0 = col.get_state(device=True)
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(calls):
+            res = fn()
+        end.record(stream)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end) / calls, res
+
+    ms_eq, (x, info) = timed(lambda: col.equilibrium())
+    # sums of the reduced Newton system per iteration and layer: (E(E+1)/2 + 2E + 2) S multiply-adds
+    flops_it = 2.0 * (E * (E + 1) / 2 + 2 * E + 2) * S * L
+    ach = flops_it * info.iters_max / (ms_eq * 1e-3) / 1e12
+    src = list(range(2, 2 + sources))
+    q = col.reaction_fluxes(n0)
+    ms_path, out = timed(lambda: col.pathways(q, src))
+    edges = sum(len({a for a in (prob.reac[r] if d == 0 else prob.prod[r]) if a >= 0}) *
+                len({a for a in (prob.prod[r] if d == 0 else prob.reac[r]) if a >= 0}) for r in range(R) for d in (0, 1)
+                if not (d == 1 and prob.rtype[r] == synth.RX_PHOTO))
+    res = {
+        "workload": f"{S} species x {R} reactions x {L} layers, initial state",
+        "equilibrium": {"ms_per_call": ms_eq, "layers_per_s": L / (ms_eq * 1e-3),
+                        "newton_iters_max": int(info.iters_max),
+                        "roofline": {"kernel": "k_equilibrium (one CTA per layer)", "bound": "alu",
+                                     "achieved": ach, "peak": live["f64"], "unit": "TFLOP/s",
+                                     "frac": ach / live["f64"],
+                                     "peak_kind": "FP64 matmul measured live; the solve is latency-bound "
+                                                  "(150 CTAs, a barrier-separated chain per Newton iteration)"}},
+        "pathways": {"sources": sources, "searches": sources * L, "ms_per_call": ms_path,
+                     "searches_per_s": sources * L / (ms_path * 1e-3), "edges_per_layer": edges,
+                     "edge_relaxations_per_s": sources * L * edges / (ms_path * 1e-3)},
+    }
+    if cpu:
+        from oracle.oracle import Oracle
+        o = Oracle(prob)
+        nh = n0.cpu().numpy()
+        t0 = time.perf_counter()
+        ref, _, _ = o.equilibrium(o.element_totals(nh))
+        res["equilibrium"]["cpu_oracle_s"] = time.perf_counter() - t0
+        xg = x.cpu().numpy()
+        m = ref > 1e-250
+        res["equilibrium"]["err_vs_oracle"] = {"max_rel": float(np.max(np.abs(xg[m] - ref[m]) / ref[m])),
+                                               "species_compared": int(m.sum())}
+        qo = o.fluxes(nh)
+        got = col.pathways(torch.as_tensor(qo, device=q.device), src[:1])
+        d = got["dist"].cpu().numpy()
+        pe = got["pred_edge"].cpu().numpy()
+        same, t_cpu = True, 0.0
+        for k in (0, L // 2, L - 1):
+            t0 = time.perf_counter()
+            r = o.pathways(qo[k], src[0])
+            t_cpu += time.perf_counter() - t0
+            same &= bool(np.array_equal(r["dist"], d[0, k]) and np.array_equal(r["pred_edge"], pe[0, k]))
+        res["pathways"]["bitwise_equal_to_oracle"] = same
+        res["pathways"]["cpu_oracle_s_per_search"] = t_cpu / 3
+    col.close()
+    return res
+
+
+def run_analysis(args):
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    out = analysis_object(live_peaks(), calls=max(args.steps, 1), cpu=not args.no_cpu)
+    print(json.dumps({"mode": "analysis", "analysis": out}), flush=True)
+    return 0
+
+
 def run_steady(args):
     """Time to steady state of the 594 x 150 column: mixed path (FP64 factorization reused as the
     FGMRES preconditioner once steps go to FP64) against the plain FP64 path, the two end states
@@ -958,11 +1046,13 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the default line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving object of the default line")
     ap.add_argument("--no-parcel", action="store_true", help="skip the parcel-scheme object of the default line")
+    ap.add_argument("--no-analysis", action="store_true",
+                    help="skip the equilibrium and pathway-analyser object of the default line")
     ap.add_argument("--serving-deadline", type=float, default=75.0,
                     help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
@@ -989,6 +1079,8 @@ def main():
         return run_kernels(args)
     if args.mode == "parcel":
         return run_parcel(args)
+    if args.mode == "analysis":
+        return run_analysis(args)
     return run_ours(args)
 
 

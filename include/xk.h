@@ -261,6 +261,55 @@ XK_API int xk_block_solve32(xk_ctx *ctx, const double *A, const double *lo, cons
  * refinement iterations around the FP64 factorization). */
 XK_API int xk_step_delta(xk_ctx *ctx, const double *n, double dt, double *delta, int *iters, double *resid);
 
+/* ---- chemical-equilibrium initial state (Sec. 2.5, option (i)) ----
+ * For each layer, the ideal-gas mixture of minimum Gibbs energy
+ *     G/RT = sum_y N_y (G_y/RT + ln(P/p0) + ln(N_y / N)),  N = sum_y N_y,
+ * at the layer's T and P (G_y/RT from the NASA-7 sets, Appendix A), with fixed element totals
+ * sum_y a_ey N_y = b_e (a = the network's element counts).  The paper starts runs from such a
+ * composition computed by its equilibrium solver; every thermal reaction is then in balance,
+ * sum nu ln n = ln K_c (Sec. 2.3.4).  Solved per layer on one CTA by Newton iterations on the
+ * element potentials and the total moles; the mole fractions of species far below 1e-100 are exact
+ * in relative terms, since they are rebuilt from the converged potentials.
+ *  b [L*E]: element totals per layer (device; any common unit, e.g. atoms cm^-3), or NULL to take
+ *    them from the context's current state; an element with b_e <= 0 is absent and every species
+ *    holding it gets x = 0.
+ *  x [L*S]: mole fractions, summing to 1 per layer (device; may be NULL).
+ *  set_state: 1 also sets the context's state to n = x n_gas.
+ *  max_iter, tol: Newton iterations per layer, and the bound on the N-weighted mean |d ln N_y| and
+ *    on |d ln N| that ends them (1e-12 gives full FP64 accuracy in about 20-60 iterations).
+ * Returns XK_OK, XK_ENOCONV (some layer did not converge: info says how many; x and the state hold
+ * the last iterate), XK_ESINGULAR, XK_EINVAL (more than 30 elements, bad arguments).  Synchronizes. */
+typedef struct {
+    int iters_max;              /* most Newton iterations any layer took */
+    int layers_not_converged;
+    int layers_singular;
+} xk_equilibrium_info;
+XK_API int xk_equilibrium(xk_ctx *ctx, const double *b, double *x, int set_state, int max_iter, double tol,
+                          xk_equilibrium_info *info);
+
+/* ---- reaction-pathway analyser (Sec. 4) ----
+ * The paper finds the kinetically fastest conversion route between two species with Dijkstra's
+ * algorithm, minimising the summed inverse reaction rates, and names the slowest reaction of the
+ * route its rate-limiting step.
+ * xk_reaction_fluxes: forward and reverse rate of every reaction in every layer at state n
+ *   (device [L*S]): q [L*R*2] (device), q[(k R + r) 2 + 0] = k_f prod n_reac (photolysis: k_ph n_A,
+ *   with k_ph at state n), q[.. + 1] = k_r prod n_prod (0 for photolysis), molecules cm^-3 s^-1.
+ * xk_pathways: the graph of layer k has an edge from every species a reaction direction consumes
+ *   to every species it produces (itself excepted), of weight 1 / q for that direction's rate q > 0.
+ *   Edge code = 2 r + direction (0 forward, 1 reverse).  For each source src[j] (host array,
+ *   0 < nsrc <= S) and each layer, Dijkstra's search on one warp writes, at [(j L + k) S + y]
+ *   (device arrays; any may be NULL, but lim_edge and lim_w go together):
+ *     dist: least summed inverse rate from the source to y (s cm^3; +inf unreachable, 0 at the source);
+ *     pred_sp, pred_edge: predecessor species and edge of y on that route (-1 none);
+ *     lim_edge, lim_w: the route's slowest step (largest 1/q, the first on ties) and its weight.
+ *   Ties are broken deterministically: the unfinished species of least distance with the lower
+ *   index is finished next, and an edge replaces a predecessor only when it makes the distance
+ *   strictly smaller, edges taken in increasing code; the same inputs give the same tree bit for
+ *   bit.  Returns XK_OK or XK_EINVAL.  Synchronizes. */
+XK_API int xk_reaction_fluxes(xk_ctx *ctx, const double *n, double *q);
+XK_API int xk_pathways(xk_ctx *ctx, const double *q, int nsrc, const int *src, double *dist, int *pred_sp,
+                       int *pred_edge, int *lim_edge, double *lim_w);
+
 /* ---- Lagrangian parcel scheme (Sec. 2, Fig. 1 and Fig. 2) ----
  * The paper's own driver.  One global iteration carries an air parcel from the
  * bottom layer to the top and back (layers 0 .. L-1, then L-2 .. 0).  In layer

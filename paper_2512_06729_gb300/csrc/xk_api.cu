@@ -39,6 +39,7 @@ struct xk_ctx {
     bool rates_valid = false;      // k_f, k_r of the loaded network and atmosphere are in the workspace
     // host index structures
     std::vector<int> yp, yent, jp, jcol, jtp, jrs, jdq, abs_sp;
+    std::vector<int> pg_p, pg_v, pg_s, pg_code;   // reaction graph of the pathway analyser
     std::vector<double> sig_abs_c;
     // device
     char *ws = nullptr;
@@ -72,6 +73,9 @@ struct xk_ctx {
     BcrPlan bcr;           // block cyclic reduction on the tensor cores (mixed path, fp32_bcr)
     bool use_bcr = false;
     bool ready = false;
+    // equilibrium initial state and pathway analyser
+    PathGraph pgraph{};
+    int *eq_iters = nullptr, *eq_status = nullptr, *path_src = nullptr;
     // Lagrangian parcel scheme: its buffers in the workspace (ParcelArgs without the policy)
     ParcelArgs parcel{};
     double *parcel_kzz0 = nullptr;   // [L] zero eddy profile: the molecular part of u, v
@@ -233,6 +237,41 @@ void build_indices(xk_ctx *c)
             c->sig_abs_c.insert(c->sig_abs_c.end(), c->sigma_abs.begin() + (size_t)y * c->W,
                                 c->sigma_abs.begin() + (size_t)(y + 1) * c->W);
         }
+    // pathway graph: each reaction direction gives an edge from every species it consumes to every
+    // species it produces (itself excepted), grouped by source, then target, codes increasing
+    std::vector<std::vector<std::pair<int, int>>> out(S);   // (target, code) per source
+    for (int r = 0; r < R; ++r)
+        for (int dir = 0; dir < 2; ++dir) {
+            const int *frm = dir == 0 ? &c->reac[3 * r] : &c->prod[3 * r];
+            const int *to = dir == 0 ? &c->prod[3 * r] : &c->reac[3 * r];
+            for (int a = 0; a < 3; ++a) {
+                const int u = frm[a];
+                if (u < 0 || (a > 0 && frm[0] == u) || (a > 1 && frm[1] == u)) continue;
+                for (int t = 0; t < 3; ++t) {
+                    const int v = to[t];
+                    if (v < 0 || v == u || (t > 0 && to[0] == v) || (t > 1 && to[1] == v)) continue;
+                    out[u].push_back({v, 2 * r + dir});
+                }
+            }
+        }
+    c->pg_p.assign(S + 1, 0);
+    c->pg_v.clear();
+    c->pg_s.assign(1, 0);
+    c->pg_code.clear();
+    for (int u = 0; u < S; ++u) {
+        auto &ev = out[u];
+        std::stable_sort(ev.begin(), ev.end(),
+                         [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
+        for (size_t i = 0; i < ev.size(); ++i) {
+            if (i == 0 || ev[i].first != ev[i - 1].first) {
+                if (i > 0) c->pg_s.push_back((int)c->pg_code.size());
+                c->pg_v.push_back(ev[i].first);
+            }
+            c->pg_code.push_back(ev[i].second);
+        }
+        if (!ev.empty()) c->pg_s.push_back((int)c->pg_code.size());
+        c->pg_p[u + 1] = (int)c->pg_v.size();
+    }
 }
 
 // Krylov basis size: FGMRES(m) of the mixed path; in FP64 mode only the refinement around the
@@ -255,6 +294,7 @@ size_t layout(xk_ctx *c, char *base)
     Col &k = c->col;
     Col t{};
     t.S = S; t.E = c->E; t.R = R; t.L = L; t.W = W; t.Rph = Rph; t.Sabs = Sabs; t.ld = ld;
+    t.elem = b.take<int>(std::max<size_t>(1, (size_t)S * c->E));
     t.mass = b.take<double>(S); t.nasa = b.take<double>(15 * (size_t)S); t.dcoef = b.take<double>(S);
     t.arr = b.take<double>(9 * (size_t)R); t.troe = b.take<double>(4 * (size_t)R);
     t.rtype = b.take<int>(R); t.reac = b.take<int>(3 * (size_t)R); t.prod = b.take<int>(3 * (size_t)R);
@@ -364,6 +404,14 @@ size_t layout(xk_ctx *c, char *base)
     q.dd = b.take<double>(6 * (size_t)std::max(R, 1));
     q.st = b.take<ParcelState>(1);
     c->parcel_kzz0 = b.take<double>(L);
+    // equilibrium initial state and pathway analyser
+    c->eq_iters = b.take<int>(L);
+    c->eq_status = b.take<int>(L);
+    c->path_src = b.take<int>(std::max(S, 1));
+    c->pgraph.gp = b.take<int>(S + 1);
+    c->pgraph.gv = b.take<int>(std::max<size_t>(1, c->pg_v.size()));
+    c->pgraph.gs = b.take<int>(std::max<size_t>(1, c->pg_s.size()));
+    c->pgraph.gcode = b.take<int>(std::max<size_t>(1, c->pg_code.size()));
     return b.off + 256;
 }
 
@@ -974,6 +1022,9 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
                         c->S, nbc);
     }
     Col &k = c->col;
+    up(c, k.elem, c->elem);
+    up(c, c->pgraph.gp, c->pg_p); up(c, c->pgraph.gv, c->pg_v); up(c, c->pgraph.gs, c->pg_s);
+    up(c, c->pgraph.gcode, c->pg_code);
     up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
     up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
     up(c, k.prod, c->prod); up(c, k.form, c->form); up(c, k.prow, c->prow);
@@ -1658,6 +1709,68 @@ int xk_batch_poll(xk_batch *b, int slot, xk_run_info *info, int *finished, int *
     if (finished) *finished = b->slots[slot].finished ? 1 : 0;
     if (status) *status = h.err_timeout ? XK_ETIMEOUT : h.status;
     return XK_OK;
+}
+
+// ------------------------------------------- equilibrium initial state and pathway analyser
+
+int xk_equilibrium(xk_ctx *c, const double *b, double *x, int set_state, int max_iter, double tol,
+                   xk_equilibrium_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (max_iter <= 0 || !(tol > 0.0)) return fail(c, XK_EINVAL, "equilibrium: bad max_iter or tol");
+    if (c->E + 1 > 31) return fail(c, XK_EINVAL, "equilibrium: at most 30 elements");
+    ensure_rates(c);   // G/RT of the atmosphere
+    cudaError_t e = launch_equilibrium(c->col, b, x, set_state ? c->col.n : nullptr, max_iter, tol, c->eq_iters,
+                                       c->eq_status, c->st);
+    if (e != cudaSuccess) return fail(c, XK_EINVAL, "equilibrium launch: %s", cudaGetErrorString(e));
+    std::vector<int> its(c->L), sts(c->L);
+    cudaMemcpyAsync(its.data(), c->eq_iters, sizeof(int) * c->L, cudaMemcpyDeviceToHost, c->st);
+    cudaMemcpyAsync(sts.data(), c->eq_status, sizeof(int) * c->L, cudaMemcpyDeviceToHost, c->st);
+    rc = finish_eval(c, "equilibrium");
+    if (rc) return rc;
+    int worst = 0, bad = 0, sing = 0;
+    for (int k = 0; k < c->L; ++k) {
+        worst = std::max(worst, its[k]);
+        bad += sts[k] == 1;
+        sing += sts[k] < 0;
+    }
+    if (info) {
+        info->iters_max = worst;
+        info->layers_not_converged = bad;
+        info->layers_singular = sing;
+    }
+    if (sing) return fail(c, XK_ESINGULAR, "equilibrium: %d layers with a singular system or no species", sing);
+    if (bad) return fail(c, XK_ENOCONV, "equilibrium: %d layers not converged in %d iterations", bad, max_iter);
+    return XK_OK;
+}
+
+int xk_reaction_fluxes(xk_ctx *c, const double *n, double *q)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!n || !q) return fail(c, XK_EINVAL, "null pointer");
+    ensure_rates(c);
+    launch_photolysis(c->col, n, c->st);
+    launch_fluxes(c->col, n, q, c->st);
+    return finish_eval(c, "reaction_fluxes");
+}
+
+int xk_pathways(xk_ctx *c, const double *q, int nsrc, const int *src, double *dist, int *pred_sp, int *pred_edge,
+                int *lim_edge, double *lim_w)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!q || !src || nsrc <= 0 || nsrc > c->S) return fail(c, XK_EINVAL, "pathways: bad sources");
+    if ((lim_edge == nullptr) != (lim_w == nullptr))
+        return fail(c, XK_EINVAL, "pathways: lim_edge and lim_w go together");
+    for (int j = 0; j < nsrc; ++j)
+        if (src[j] < 0 || src[j] >= c->S) return fail(c, XK_EINVAL, "pathways: source %d out of range", src[j]);
+    cudaMemcpyAsync(c->path_src, src, sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st);
+    cudaError_t e = launch_pathways(c->col, c->pgraph, q, nsrc, c->path_src, dist, pred_sp, pred_edge, lim_edge,
+                                    lim_w, c->st);
+    if (e != cudaSuccess) return fail(c, XK_EINVAL, "pathways launch: %s", cudaGetErrorString(e));
+    return finish_eval(c, "pathways");
 }
 
 // ---------------------------------------------------------------- Lagrangian parcel scheme

@@ -24,6 +24,7 @@ struct Col {
     int S, E, R, L, W, Rph, Sabs;
     int ld;               // leading dimension of a dense S x S block (elements)
     // network
+    const int *elem;      // [S][E] element counts
     const double *mass, *nasa, *dcoef, *arr, *troe;
     const int *rtype, *reac, *prod, *form, *prow;
     // species-major stoichiometry (residual gather): entries r * 16 + (nu + 8)
@@ -143,6 +144,26 @@ __device__ __forceinline__ double jac_entry(const Col &c, int q, const double *d
     }
     return acc;
 }
+
+// Reaction graph of the pathway analyser (Sec. 4), the same in every layer: species u's out-edges
+// are grouped by target, groups gp[u] .. gp[u+1); group g leads to species gv[g] through the edge
+// codes gcode[gs[g] .. gs[g+1]) (2 r + direction, 0 forward, 1 reverse) in increasing order.
+struct PathGraph {
+    const int *gp, *gv, *gs, *gcode;
+};
+// Equilibrium composition per layer (xk_analysis.cu): element totals b [L][E] (nullptr: from the
+// state c.n); mole fractions into x [L][S] (may be nullptr) and, when nout is set, number densities
+// x n_gas into nout; per layer the iterations taken and a status (0 converged, 1 not converged,
+// -1 singular system).  Needs c.grt of the current atmosphere.
+cudaError_t launch_equilibrium(const Col &c, const double *b, double *x, double *nout, int max_iter, double tol,
+                               int *iters, int *status, cudaStream_t st);
+// Forward and reverse rate of every reaction in every layer at state n: q [L][R][2].
+void launch_fluxes(const Col &c, const double *n, double *q, cudaStream_t st);
+// Dijkstra from each source src[j] (device, nsrc) in every layer of rates q [L][R][2]: outputs
+// [nsrc][L][S] (any output pointer may be nullptr).
+cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, int nsrc, const int *src,
+                            double *dist, int *pred_sp, int *pred_edge, int *lim_edge, double *lim_w,
+                            cudaStream_t st);
 
 // Lagrangian parcel scheme (Sec. 2, Fig. 2): buffers and state of one global iteration.
 struct ParcelState {

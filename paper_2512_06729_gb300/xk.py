@@ -57,6 +57,10 @@ class RunInfo(C.Structure):
                 ("fp64_steps", C.c_longlong), ("refactors", C.c_longlong)]
 
 
+class EquilibriumInfo(C.Structure):
+    _fields_ = [("iters_max", C.c_int), ("layers_not_converged", C.c_int), ("layers_singular", C.c_int)]
+
+
 class XkError(RuntimeError):
     def __init__(self, where, code, msg):
         super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
@@ -114,6 +118,9 @@ SIGNATURES = {
                              _vp]),
     "xk_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "xk_factor_work": (C.c_int, [_vp, _dp, _dp]),
+    "xk_equilibrium": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_double, C.POINTER(EquilibriumInfo)]),
+    "xk_reaction_fluxes": (C.c_int, [_vp, _vp, _vp]),
+    "xk_pathways": (C.c_int, [_vp, _vp, C.c_int, _ip, _vp, _vp, _vp, _vp, _vp]),
 }
 
 PHASES = ["rates", "photolysis", "reaction", "residual", "jacobian", "factor", "solve", "control", "fallback",
@@ -363,6 +370,38 @@ class Column:
         lo, up = self._dev(self.L, self.S), self._dev(self.L, self.S)
         self._call("xk_eval_jacobian", self._ptr(n.contiguous()), float(dt), self._ptr(A), self._ptr(lo), self._ptr(up))
         return A, lo, up
+
+    # -- equilibrium initial state (Sec. 2.5) and pathway analyser (Sec. 4) --------
+    def equilibrium(self, b=None, set_state=False, max_iter=300, tol=1e-12):
+        """Mole fractions [L, S] (device) of the Gibbs minimum at element totals b ([L, E] device
+        tensor, or None for the current state's); set_state also makes n = x n_gas the state."""
+        x = self._dev(self.L, self.S)
+        bp = None if b is None else self._ptr(b.contiguous())
+        info = EquilibriumInfo()
+        self._call("xk_equilibrium", bp, self._ptr(x), int(bool(set_state)), int(max_iter), float(tol),
+                   C.byref(info))
+        return x, info
+
+    def reaction_fluxes(self, n):
+        """Forward and reverse rate of every reaction at state n: [L, R, 2] (device)."""
+        q = self._dev(self.L, self.R, 2)
+        self._call("xk_reaction_fluxes", self._ptr(n.contiguous()), self._ptr(q))
+        return q
+
+    def pathways(self, q, sources):
+        """Dijkstra from each source species in every layer of rates q [L, R, 2]: dict of device
+        tensors [nsrc, L, S] dist, pred_sp, pred_edge, lim_edge, lim_w."""
+        t = self._torch
+        src = np.ascontiguousarray(np.atleast_1d(sources), np.int32)
+        shape = (len(src), self.L, self.S)
+        out = dict(dist=self._dev(*shape), lim_w=self._dev(*shape),
+                   pred_sp=t.empty(shape, dtype=t.int32, device=self.device),
+                   pred_edge=t.empty(shape, dtype=t.int32, device=self.device),
+                   lim_edge=t.empty(shape, dtype=t.int32, device=self.device))
+        self._call("xk_pathways", self._ptr(q.contiguous()), len(src), src.ctypes.data_as(_ip),
+                   self._ptr(out["dist"]), _vp(out["pred_sp"].data_ptr()), _vp(out["pred_edge"].data_ptr()),
+                   _vp(out["lim_edge"].data_ptr()), self._ptr(out["lim_w"]))
+        return out
 
     def block_solve(self, A, lo, up, f):
         x = self._dev(self.L, self.S)
