@@ -19,9 +19,11 @@
  *    ln K_c = -sum nu G/RT + dnu ln(p0 / (k_B T)), p0 = 1 bar (Sec. 2.3.4).
  *  - three-body fall-off: Lindemann (Sec. 2.3.2) times the Troe broadening
  *    factor when a Troe set is given; [M] = n_gas.
- *  - photolysis: direct beam only, optical depth to the layer midpoint,
- *    rates lagged (evaluated at the start of a step, not differentiated);
- *    photolysis is irreversible.
+ *  - photolysis: the direct beam, optical depth (absorption plus Rayleigh
+ *    scattering) to the layer midpoint, plus optionally the diffuse field of a
+ *    layer-by-layer two-stream photon budget (ora_two_stream); rates lagged
+ *    (evaluated at the start of a step, not differentiated); photolysis is
+ *    irreversible.
  *  - zero-flux top and bottom boundaries (Sec. 2.5).
  */
 #include "oracle.h"
@@ -168,6 +170,95 @@ void ora_rate_coefficients(const ora_problem *p, double *kf, double *kr)
     free(ngas);
 }
 
+/*
+ * Sec. 2.3.3 diffuse field, where the paper gives J_diff = (J_up + J_down) / 2 but not how the two
+ * fluxes are found.  Reading: a two-stream photon budget layer by layer.  The beam loses
+ * mu F0 (e^{-tau_top/mu} - e^{-tau_bot/mu}) photons per unit horizontal area in layer k; the
+ * scattered fraction omega_k = dtau_s / (dtau_a + dtau_s) of them is shared equally between the
+ * two hemispheres (isotropic, as Rayleigh scattering is in the mean).  A diffuse flux crossing the
+ * layer goes through with probability t = exp(-dtau / mubar), mubar = 1/2 (the hemispheric mean
+ * path 2 dtau); otherwise it interacts, and is scattered (half back, half on) with probability
+ * omega or absorbed.  So layer k reflects r = (1 - t) omega / 2 and transmits T = t + (1 - t) omega / 2
+ * of each diffuse flux.  The lower boundary reflects the fraction `albedo` of what reaches it
+ * (diffuse and beam); nothing diffuse enters at the top.  Unknowns: U_i, D_i at the L + 1
+ * interfaces (D_L = 0), solved as one banded system
+ *     D_k     - T_k D_{k+1} - r_k U_k = P_k / 2,
+ *     U_{k+1} - T_k U_k - r_k D_{k+1} = P_k / 2,
+ *     U_0     - albedo D_0            = albedo B_bottom,
+ * by Gaussian elimination without pivoting (each row is diagonally dominant: T + r <= 1).
+ */
+int ora_two_stream(int L, const double *dtau_a, const double *dtau_s, double F0, double mu, double albedo,
+                   double *U, double *D, double *Jdiff)
+{
+    /* unknowns v[2i] = U_i (i = 0..L), v[2i+1] = D_i (i = 0..L-1); band a[row][col - row + 2] */
+    int n = 2 * L + 1;
+    double *a = calloc((size_t)n * 5, sizeof(double)), *rhs = calloc((size_t)n, sizeof(double));
+    double *r = malloc(sizeof(double) * L * 3), *T = r + L, *P = T + L;
+    if (!a || !rhs || !r) { free(a); free(rhs); free(r); return -1; }
+    double tau_top = 0.0;
+    for (int k = L - 1; k >= 0; --k) {
+        double dt = dtau_a[k] + dtau_s[k];
+        double om = dt > 0.0 ? dtau_s[k] / dt : 0.0;
+        double t = exp(-dt / 0.5);
+        r[k] = (1.0 - t) * om / 2.0;
+        T[k] = t + (1.0 - t) * om / 2.0;
+        P[k] = om * mu * F0 * (exp(-tau_top / mu) - exp(-(tau_top + dt) / mu));
+        tau_top += dt;
+    }
+    double Bbot = mu * F0 * exp(-tau_top / mu);
+#define BAND(i, j) a[(size_t)(i) * 5 + (j) - (i) + 2]
+    /* bottom boundary, row 0 (U_0) */
+    BAND(0, 0) = 1.0;
+    BAND(0, 1) = -albedo;
+    rhs[0] = albedo * Bbot;
+    for (int k = 0; k < L; ++k) {
+        int rd = 2 * k + 1, ru = 2 * k + 2;            /* rows of D_k and U_{k+1} */
+        BAND(rd, rd) = 1.0;
+        if (k + 1 < L) BAND(rd, 2 * k + 3) = -T[k];   /* D_{k+1} */
+        BAND(rd, 2 * k) = -r[k];                       /* U_k */
+        rhs[rd] = P[k] / 2.0;
+        BAND(ru, ru) = 1.0;
+        BAND(ru, 2 * k) = -T[k];                       /* U_k */
+        if (k + 1 < L) BAND(ru, 2 * k + 3) = -r[k];   /* D_{k+1} */
+        rhs[ru] = P[k] / 2.0;
+    }
+    /* elimination below the diagonal (lower bandwidth 2, upper bandwidth 2, no fill outside) */
+    int rc = 0;
+    for (int c = 0; c < n; ++c) {
+        double piv = BAND(c, c);
+        if (piv == 0.0) { rc = -1; break; }
+        for (int i = c + 1; i <= c + 2 && i < n; ++i) {
+            double l = BAND(i, c) / piv;
+            if (l == 0.0) continue;
+            for (int j = c; j <= c + 2 && j < n; ++j)
+                BAND(i, j) -= l * BAND(c, j);
+            rhs[i] -= l * rhs[c];
+        }
+    }
+    if (rc == 0)
+        for (int i = n - 1; i >= 0; --i) {
+            double s = rhs[i];
+            for (int j = i + 1; j <= i + 2 && j < n; ++j)
+                s -= BAND(i, j) * rhs[j];
+            rhs[i] = s / BAND(i, i);
+        }
+#undef BAND
+    if (rc == 0) {
+        for (int i = 0; i <= L; ++i) {
+            U[i] = rhs[2 * i];
+            D[i] = i < L ? rhs[2 * i + 1] : 0.0;
+        }
+        for (int k = 0; k < L; ++k) {
+            double up = 0.5 * (U[k] + U[k + 1]), dn = 0.5 * (D[k] + D[k + 1]);
+            Jdiff[k] = 0.5 * (up + dn);
+        }
+    }
+    free(a);
+    free(rhs);
+    free(r);
+    return rc;
+}
+
 void ora_photolysis(const ora_problem *p, const double *n, double *kph)
 {
     int L = p->L, S = p->S, W = p->W, R = p->R, Rph = p->Rph;
@@ -176,22 +267,37 @@ void ora_photolysis(const ora_problem *p, const double *n, double *kph)
     double *ngas = malloc(sizeof(double) * L * 4);
     double *z = ngas + L, *dz = z + L, *dzi = dz + L;
     ora_grid(p, ngas, z, dz, dzi);
-    double *alpha = malloc(sizeof(double) * L);
+    double *alpha = malloc(sizeof(double) * L * 2), *alpha_s = alpha + L;
     double *J = malloc(sizeof(double) * L * W);
+    double *ta = malloc(sizeof(double) * (L * 3 + 2 * (L + 1))), *ts = ta + L, *Jd = ts + L;
+    double *U = Jd + L, *D = U + L + 1;
     for (int w = 0; w < W; ++w) {
-        /* absorption coefficient per layer: sum_i sigma_i n_i */
+        /* absorption and Rayleigh-scattering coefficients per layer: sum_i sigma_i n_i */
         for (int k = 0; k < L; ++k) {
-            double s = 0.0;
-            for (int i = 0; i < S; ++i)
+            double s = 0.0, sc = 0.0;
+            for (int i = 0; i < S; ++i) {
                 s += p->sigma_abs[(size_t)i * W + w] * n[(size_t)k * S + i];
+                if (p->sigma_s) sc += p->sigma_s[(size_t)i * W + w] * n[(size_t)k * S + i];
+            }
             alpha[k] = s;
+            alpha_s[k] = sc;
         }
-        /* optical depth from the top down to the layer midpoint */
+        /* total optical depth (absorption plus scattering) from the top down to the layer midpoint */
         double above = 0.0;
         for (int k = L - 1; k >= 0; --k) {
-            double tau = above + 0.5 * alpha[k] * dz[k];
+            double ext = alpha[k] + alpha_s[k];
+            double tau = above + 0.5 * ext * dz[k];
             J[(size_t)k * W + w] = p->J0[w] * exp(-tau / p->mu);
-            above += alpha[k] * dz[k];
+            above += ext * dz[k];
+        }
+        if (p->diffuse) {
+            for (int k = 0; k < L; ++k) {
+                ta[k] = alpha[k] * dz[k];
+                ts[k] = alpha_s[k] * dz[k];
+            }
+            if (ora_two_stream(L, ta, ts, p->J0[w], p->mu, p->albedo, U, D, Jd) == 0)
+                for (int k = 0; k < L; ++k)
+                    J[(size_t)k * W + w] += Jd[k];
         }
     }
     for (int k = 0; k < L; ++k)
@@ -202,6 +308,7 @@ void ora_photolysis(const ora_problem *p, const double *n, double *kph)
             kph[(size_t)k * Rph + q] = p->tf * s;
         }
     (void)R;
+    free(ta);
     free(J);
     free(alpha);
     free(ngas);

@@ -36,6 +36,11 @@ typedef struct {
     const double *P_bar, *T, *Kzz;   /* L */
     const double *dcoef;    /* S */
     double g, mbar, alpha_T;
+    /* Sec. 2.3.3 extinction and diffuse field (optional): sigma_s S x W Rayleigh scattering cross
+     * sections (NULL: none), albedo of the lower boundary, diffuse = 1 adds J_diff to the beam */
+    const double *sigma_s;
+    double albedo;
+    int diffuse;
 } ora_problem;
 
 typedef struct {
@@ -72,6 +77,13 @@ void ora_thermo(const ora_problem *p, double *grt, double *lnkc);
 void ora_rate_coefficients(const ora_problem *p, double *kf, double *kr);
 /* Sec. 2.3.3: photolysis rate constants per layer and photolysis reaction. */
 void ora_photolysis(const ora_problem *p, const double *n, double *kph);
+/* Sec. 2.3.3 diffuse field of one wavelength on L layers: dtau_a, dtau_s [L] absorption and
+ * scattering optical thickness of each layer (layer 0 at the bottom), beam photon flux F0 at the top
+ * with cos(zenith) mu, lower-boundary albedo.  U, D [L+1]: upward and downward diffuse fluxes
+ * (photons per unit horizontal area) crossing interface i (0 bottom, L top); Jdiff [L] =
+ * (J_up + J_down) / 2 per layer, each the mean of the layer's two interfaces.  Returns 0 or -1. */
+int ora_two_stream(int L, const double *dtau_a, const double *dtau_s, double F0, double mu, double albedo,
+                   double *U, double *D, double *Jdiff);
 /* Eq. 2: interface flux phi_{k+1/2} = u n_k - v n_{k+1}, per interface and species. */
 void ora_transport(const ora_problem *p, double *u, double *v);
 /* Eq. 1: F = P - L - d(phi)/dz at state n (kf/kr/kph supplied). */

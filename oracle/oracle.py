@@ -28,6 +28,7 @@ class _Problem(C.Structure):
         ("mu", C.c_double), ("tf", C.c_double),
         ("P_bar", _dp), ("T", _dp), ("Kzz", _dp), ("dcoef", _dp),
         ("g", C.c_double), ("mbar", C.c_double), ("alpha_T", C.c_double),
+        ("sigma_s", _dp), ("albedo", C.c_double), ("diffuse", C.c_int),
     ]
 
 
@@ -104,6 +105,8 @@ def lib():
         l.ora_parcel_run.argtypes = [P, C.POINTER(Policy), C.c_int, C.c_int, C.c_double, _dp,
                                      C.POINTER(ParcelInfo), _ip]
         l.ora_parcel_run.restype = C.c_int
+        l.ora_two_stream.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
+        l.ora_two_stream.restype = C.c_int
         l.ora_equilibrium.argtypes = [P, _dp, _dp, C.c_int, C.c_double, _ip]
         l.ora_equilibrium.restype = C.c_int
         l.ora_fluxes.argtypes = [P, _dp, _dp, _dp, _dp, _dp]
@@ -136,6 +139,9 @@ class Oracle:
             sigma=c(prob.sigma if prob.sigma.size else np.zeros(1)),
             sigma_abs=c(prob.sigma_abs if prob.sigma_abs.size else np.zeros(1)),
             P_bar=c(prob.P_bar), T=c(prob.T), Kzz=c(prob.Kzz), dcoef=c(prob.dcoef))
+        sig_s = getattr(prob, "sigma_s", None)
+        if sig_s is not None:
+            self._keep["sigma_s"] = c(sig_s)
         k = self._keep
         for key in ("lam", "dlam", "J0"):
             if k[key].size == 0:
@@ -148,7 +154,9 @@ class Oracle:
             J0=_d(k["J0"]), sigma=_d(k["sigma"]), sigma_abs=_d(k["sigma_abs"]),
             mu=float(prob.mu), tf=float(prob.tf), P_bar=_d(k["P_bar"]), T=_d(k["T"]),
             Kzz=_d(k["Kzz"]), dcoef=_d(k["dcoef"]), g=float(prob.g), mbar=float(prob.mbar),
-            alpha_T=float(prob.alpha_T))
+            alpha_T=float(prob.alpha_T),
+            sigma_s=_d(k["sigma_s"]) if "sigma_s" in k else None,
+            albedo=float(getattr(prob, "albedo", 0.0)), diffuse=int(getattr(prob, "diffuse", 0)))
         self.L, self.S, self.R = prob.L, prob.S, prob.R
 
     # -- rows of the step --------------------------------------------------
@@ -315,3 +323,15 @@ class Oracle:
         lib().ora_pathways(C.byref(self.st), _d(np.ascontiguousarray(q_layer, np.float64)), int(src), _d(dist),
                            _i(pred_sp), _i(pred_edge), _i(lim_edge), _d(lim_w))
         return dict(dist=dist, pred_sp=pred_sp, pred_edge=pred_edge, lim_edge=lim_edge, lim_w=lim_w)
+
+
+def two_stream(dtau_a, dtau_s, F0, mu, albedo):
+    """Diffuse field of one wavelength (Sec. 2.3.3): returns (U [L+1], D [L+1], Jdiff [L])."""
+    ta = np.ascontiguousarray(dtau_a, np.float64)
+    ts = np.ascontiguousarray(dtau_s, np.float64)
+    L = ta.shape[0]
+    U = np.zeros(L + 1); D = np.zeros(L + 1); Jd = np.zeros(L)
+    rc = lib().ora_two_stream(int(L), _d(ta), _d(ts), float(F0), float(mu), float(albedo), _d(U), _d(D), _d(Jd))
+    if rc != 0:
+        raise ArithmeticError("two-stream system singular")
+    return U, D, Jd

@@ -56,6 +56,8 @@ class Problem:
       P_bar[L], T[L], Kzz[L]   layer pressure (bar), temperature (K), eddy coefficient (cm^2/s)
       dcoef[S]           molecular-diffusion coefficient b_y in D_y = b_y T^0.75 / n_gas
       f0[L, S]           initial mixing ratios
+      sigma_s[S, W]      Rayleigh scattering cross sections (None: no scattering)
+      albedo, diffuse    lower-boundary albedo; 1 adds the diffuse field to the direct beam
     Layer 0 is the bottom of the atmosphere.
     """
 
@@ -86,6 +88,11 @@ class Problem:
     mbar: float
     alpha_T: float
     f0: np.ndarray
+    # extinction by Rayleigh scattering and the diffuse field (Sec. 2.3.3), off unless given:
+    # sigma_s[S, W] scattering cross sections (cm^2), albedo of the lower boundary, diffuse 1/0
+    sigma_s: np.ndarray = None
+    albedo: float = 0.0
+    diffuse: int = 0
 
     @property
     def S(self):
@@ -367,6 +374,51 @@ def _photo_inputs(rng, W, Rph, reac, prow, S):
     for r in np.flatnonzero(prow >= 0):
         sigma_abs[reac[r, 0]] += sigma[prow[r]]     # absorption taken as the sum of dissociation channels
     return lam, dlam, J0, sigma, sigma_abs
+
+
+def rayleigh_cross_sections(elem, elements, lam):
+    """Rayleigh scattering cross sections sigma_s[S, W] (cm^2), lambda^-4 in shape: H2 at
+    8.14e-13 / lambda^4 (lambda in Angstrom), He at 0.0838 times that, and every other species in
+    proportion to the square of its atom count (polarisability grows with size) times H2's per atom
+    pair; species are drawn as scatterers only if they hold at most three atoms."""
+    S = elem.shape[0]
+    atoms = elem.sum(axis=1).astype(float)
+    base = 8.14e-13 / lam ** 4
+    sig = np.zeros((S, lam.shape[0]))
+    for y in range(S):
+        if y == 0:
+            sig[y] = base                                  # H2, the bath gas
+        elif y == 1:
+            sig[y] = 0.0838 * base                         # He
+        elif atoms[y] <= 3:
+            sig[y] = base * (atoms[y] / 2.0) ** 2
+    return sig
+
+
+def with_scattering(prob, albedo=0.0, diffuse=1, bins=None):
+    """The same column with Rayleigh scattering in the extinction and the diffuse field on.  With
+    bins, the photolysis grid becomes `bins` bins of about 1 A from 1 A to 10,000 A (the paper's
+    10,000-bin grid at bins=10000), the cross sections redrawn on it with the same seeds."""
+    if bins is not None:
+        rng = np.random.default_rng(1234)
+        edges = np.linspace(1.0, 10000.0, bins + 1)
+        lam = 0.5 * (edges[1:] + edges[:-1])
+        dlam = np.diff(edges)
+        J0 = _stellar_photon_flux(lam)
+        Rph = prob.Rph
+        sigma = np.zeros((Rph, bins))
+        for i in range(Rph):
+            peak = 10.0 ** rng.uniform(-19.0, -16.0)
+            centre = rng.uniform(1000.0, 2500.0)
+            width = rng.uniform(0.1, 0.3)
+            sigma[i] = peak * np.exp(-np.log(lam / centre) ** 2 / (2.0 * width ** 2))
+        sigma_abs = np.zeros((prob.S, bins))
+        for r in np.flatnonzero(prob.prow >= 0):
+            sigma_abs[prob.reac[r, 0]] += sigma[prob.prow[r]]
+        prob = prob.replace(lam=lam, dlam=dlam, J0=J0, sigma=sigma, sigma_abs=sigma_abs)
+    sig_s = rayleigh_cross_sections(prob.elem, prob.elements, prob.lam)
+    return prob.replace(sigma_s=sig_s, albedo=float(albedo), diffuse=int(diffuse),
+                        name=prob.name + f"-rt{prob.W}")
 
 
 # ---------------------------------------------------------------------------
