@@ -525,7 +525,7 @@ def run_ours(args):
             errs = err_vs_oracle(prob, tuning)
         if not args.no_steady:
             steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
-    batch = serving_obj = parcel = analysis = None
+    batch = serving_obj = parcel = analysis = radiation = None
     if rank == 0 and ws == 1:
         if not args.no_batch:
             batch = batch_object(args.columns, steps=5, warmup=3, tune=not args.no_tune)
@@ -535,6 +535,7 @@ def run_ours(args):
             parcel = parcel_object(live, cpu=not args.no_cpu)
         if not args.no_analysis:
             analysis = analysis_object(live, cpu=not args.no_cpu)
+            radiation = radiation_object(live, cpu=not args.no_cpu)
     if rank == 0:
         ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items() if v[1]}
         ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items() if v[1]}
@@ -569,6 +570,7 @@ def run_ours(args):
             "serving": serving_obj,
             "parcel": parcel,
             "analysis": analysis,
+            "radiation": radiation,
             "traced": {"ms_per_step": mixed["ms_traced"] / mixed["steps_traced"],
                        "note": "the next steps with every kernel launched from the host between CUDA event "
                                "pairs (phases_ms comes from this run)"},
@@ -925,6 +927,65 @@ def run_analysis(args):
     return 0
 
 
+def radiation_object(live, calls=5, cpu=True):
+    """Photolysis rates with the extinction and diffuse field of Sec. 2.3.3 on the 594-species,
+    150-layer column: the 1,000-bin direct beam of the headline workload beside Rayleigh scattering
+    plus the two-stream diffuse field on the paper's 10,000-bin grid (1-10,000 A).  Device time of
+    one evaluation (extinction sums, beam and diffuse recursion, rate integrals), mean of `calls`
+    after one untimed call; the FP64 work of the two contractions (extinction sum_i sigma_i n_i per
+    layer and bin, and sum_w J sigma dlambda per layer and reaction) over that time; error against
+    the oracle on every rate."""
+    import numpy as np
+    import torch
+    from paper_2512_06729_gb300 import synth, xk
+    out = {}
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, prob in (("direct_1000", synth.full_column()),
+                       ("scattering_diffuse_10000", synth.with_scattering(synth.full_column(), bins=10000))):
+        col = xk.Column(prob, "fp64")
+        col.set_mixing_ratios(prob.f0)
+        n = col.get_state(device=True)
+        col.eval_photolysis(n)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(calls):
+            kph = col.eval_photolysis(n)
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end) / calls
+        S, L, W, Rph = prob.S, prob.L, prob.W, prob.Rph
+        n_abs = int(np.count_nonzero(np.any(prob.sigma_abs != 0, axis=1)))
+        n_sca = 0 if prob.sigma_s is None else int(np.count_nonzero(np.any(prob.sigma_s != 0, axis=1)))
+        flops = 2.0 * L * W * (n_abs + n_sca) + 3.0 * L * Rph * W
+        ach = flops / (ms * 1e-3) / 1e12
+        o = {"bins": W, "absorbers": n_abs, "scatterers": n_sca, "diffuse": int(prob.diffuse),
+             "ms_per_evaluation": ms,
+             "roofline": {"kernels": "k_photo_alpha + k_photo_J + k_photo_k", "bound": "alu", "achieved": ach,
+                          "peak": live["f64"], "unit": "TFLOP/s", "frac": ach / live["f64"],
+                          "peak_kind": "FP64 matmul measured live; work = the two FP64 contractions"}}
+        if cpu:
+            from oracle.oracle import Oracle
+            nh = n.cpu().numpy()
+            t0 = time.perf_counter()
+            ref = Oracle(prob).photolysis(nh)
+            o["cpu_oracle_s"] = time.perf_counter() - t0
+            g = kph.cpu().numpy()
+            m = ref > 1e-300
+            o["err_vs_oracle_max_rel"] = float(np.max(np.abs(g[m] - ref[m]) / ref[m]))
+        out[name] = o
+        col.close()
+    return out
+
+
+def run_radiation(args):
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    out = radiation_object(live_peaks(), calls=max(args.steps, 1), cpu=not args.no_cpu)
+    print(json.dumps({"mode": "radiation", "radiation": out}), flush=True)
+    return 0
+
+
 def run_steady(args):
     """Time to steady state of the 594 x 150 column: mixed path (FP64 factorization reused as the
     FGMRES preconditioner once steps go to FP64) against the plain FP64 path, the two end states
@@ -1052,7 +1113,7 @@ def main():
                     help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis", "radiation"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
@@ -1081,6 +1142,8 @@ def main():
         return run_parcel(args)
     if args.mode == "analysis":
         return run_analysis(args)
+    if args.mode == "radiation":
+        return run_radiation(args)
     return run_ours(args)
 
 

@@ -188,6 +188,21 @@ XK_API int xk_load_photo(xk_ctx *ctx, int W, int Rph, const int *prow, const dou
                   const double *dlambda, const double *J0, const double *sigma,
                   const double *sigma_abs, double mu, double tf);
 
+/* Extinction by scattering and the diffuse field (Sec. 2.3.3), optional; after xk_load_photo and
+ * before xk_set_workspace.  sigma_s [S*W] (host; NULL: no scattering): Rayleigh scattering cross
+ * sections (cm^2) on the photolysis grid (W must equal its bin count), added to the absorption in
+ * the optical depth tau = sum_i (sigma_a,i + sigma_s,i) n_i dz.  diffuse = 1 adds the diffuse field
+ * J_diff = (J_up + J_down) / 2 to the direct beam J0 exp(-tau/mu).  The paper does not say how J_up
+ * and J_down are found; here they come from a two-stream photon budget, layer by layer: the beam
+ * photons a layer scatters (fraction dtau_s / dtau of those it removes) go half up, half down; a
+ * diffuse flux crosses a layer with probability exp(-2 dtau) (the hemispheric mean path) and is
+ * otherwise scattered (half back, half on) or absorbed; the lower boundary reflects the fraction
+ * albedo (0..1) of the diffuse and direct light reaching it; nothing diffuse enters at the top.
+ * J_up and J_down of a layer are the means of the fluxes through its two interfaces.  Photolysis
+ * rates stay lagged (evaluated at the start of a step, not differentiated in the Jacobian).
+ * XK_EINVAL on a grid mismatch, a negative or non-finite cross section, albedo outside [0, 1]. */
+XK_API int xk_load_scattering(xk_ctx *ctx, int W, const double *sigma_s, double albedo, int diffuse);
+
 /* Atmosphere (Sec. 2.1, Fig. 3), host arrays of length L: pressure (bar),
  * temperature (K), Kzz (cm^2/s); dcoef[S]: molecular diffusion
  * D_y = dcoef_y T^0.75 / n_gas; g (cm/s^2); mbar (u); alpha_T thermal

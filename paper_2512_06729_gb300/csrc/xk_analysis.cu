@@ -36,7 +36,7 @@ struct EqShared {
     double sol[kEqMaxE + 1];
     double bk[kEqMaxE];
     double red[3][kEqThreads / 32];
-    double lntot, bsum, sn;
+    double lntot, bsum, sn, snm;
     int eact[kEqMaxE];
     int done, singular, nact;
 };
@@ -77,6 +77,26 @@ __device__ void block_reduce3(EqShared &sh, double &mx, double &mn, double &sm)
         mx = fmax(mx, sh.red[0][i]);
         mn = fmin(mn, sh.red[1][i]);
         sm += sh.red[2][i];
+    }
+    __syncthreads();
+}
+
+// Block-wide sums of two values, the same in every thread.
+__device__ void block_sum2(EqShared &sh, double &a, double &b)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+        sh.red[0][w] = a;
+        sh.red[1][w] = b;
+    }
+    __syncthreads();
+    a = 0.0;
+    b = 0.0;
+    for (int i = 0; i < nw; ++i) {
+        a += sh.red[0][i];
+        b += sh.red[1][i];
     }
     __syncthreads();
 }
@@ -123,21 +143,19 @@ __device__ void warp_solve(EqShared &sh, int M)
     __syncwarp();
 }
 
-// Dynamic shared memory: lnN, nj, mu [S] doubles, then the element matrix [S][E] as bytes and the
-// activity flags [S].
-__global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double *b, double *x, double *nout,
-                                                             int max_iter, double tol, int *iters, int *status)
+// Dynamic shared memory: lnN, nj, mu [S] doubles, then the activity flags [S] as bytes.
+__global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, EqIndex ix, const double *b, double *x,
+                                                             double *nout, int max_iter, double tol, int *iters,
+                                                             int *status)
 {
     __shared__ EqShared sh;
     extern __shared__ double eq_dyn[];
     const int S = c.S, E = c.E, M = c.E + 1, k = blockIdx.x, tid = threadIdx.x;
     double *lnN = eq_dyn, *nj = lnN + S, *mu = nj + S;
-    unsigned char *a = (unsigned char *)(mu + S);
-    unsigned char *act = a + (size_t)S * E;
+    unsigned char *act = (unsigned char *)(mu + S);
     const double *g = c.grt + (size_t)k * S;
     const double lnP = log(c.P[k]);
 
-    for (int i = tid; i < S * E; i += blockDim.x) a[i] = (unsigned char)c.elem[i];
     if (tid < E) {
         double v = 0.0;
         if (b) v = b[(size_t)k * E + tid];
@@ -159,8 +177,8 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
     int cnt = 0;
     for (int y = tid; y < S; y += blockDim.x) {
         int on = 1;
-        for (int e = 0; e < E; ++e)
-            if (a[y * E + e] && !sh.eact[e]) on = 0;
+        for (int q = ix.sp[y]; q < ix.sp[y + 1]; ++q)
+            if (!sh.eact[ix.se[q]]) on = 0;
         act[y] = (unsigned char)on;
         cnt += on;
     }
@@ -180,6 +198,7 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
     int it = 0;
     for (; it < max_iter; ++it) {
         const double lntot = sh.lntot, ntot = exp(lntot);
+        double sn = 0.0, snm = 0.0;
         for (int y = tid; y < S; y += blockDim.x) {
             if (act[y]) {
                 nj[y] = exp(lnN[y]);
@@ -188,51 +207,46 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
                 nj[y] = 0.0;
                 mu[y] = 0.0;
             }
+            sn += nj[y];
+            snm += nj[y] * mu[y];
         }
-        __syncthreads();
-        // the system's sums over species, one per thread, in species order
-        const int npair = E * E, nent = npair + 2 * E + 2;
-        for (int t = tid; t < nent; t += blockDim.x) {
-            double s = 0.0;
-            if (t < npair) {
-                const int i = t / E, j = t % E;
-                if (j >= i && sh.eact[i] && sh.eact[j]) {
-                    for (int y = 0; y < S; ++y) s += (double)a[y * E + i] * a[y * E + j] * nj[y];
-                    sh.A[i][j] = s;
-                    sh.A[j][i] = s;
-                } else if (j >= i) {
-                    sh.A[i][j] = (i == j && !sh.eact[i]) ? 1.0 : 0.0;
-                    sh.A[j][i] = sh.A[i][j];
+        // the system starts from zero (pairs of elements no species shares stay zero)
+        for (int t = tid; t < M * (M + 1); t += blockDim.x) sh.A[t / (M + 1)][t % (M + 1)] = 0.0;
+        block_sum2(sh, sn, snm);
+        // each entry's sparse sum over the species holding its elements, in species order
+        for (int t = tid; t < ix.nent; t += blockDim.x) {
+            const int code = ix.eij[t];
+            double sv = 0.0, dv = 0.0;
+            for (int q = ix.ep[t]; q < ix.ep[t + 1]; ++q) {
+                const int y = ix.ey[q];
+                const double v = ix.ec[q] * nj[y];
+                sv += v;
+                if (code < 0) dv += v * mu[y];
+            }
+            if (code >= 0) {
+                const int i = code >> 5, j = code & 31;
+                if (sh.eact[i] && sh.eact[j]) {
+                    sh.A[i][j] = sv;
+                    sh.A[j][i] = sv;
                 }
-            } else if (t < npair + E) {
-                const int i = t - npair;
+            } else {
+                const int i = -1 - code;
                 if (sh.eact[i]) {
-                    double d = 0.0;
-                    for (int y = 0; y < S; ++y) {
-                        s += a[y * E + i] * nj[y];
-                        d += a[y * E + i] * nj[y] * mu[y];
-                    }
-                    sh.A[i][E] = s;
-                    sh.A[E][i] = s;
-                    sh.A[i][M] = sh.bk[i] / sh.bsum - s + d;
-                } else {
-                    sh.A[i][E] = 0.0;
-                    sh.A[E][i] = 0.0;
-                    sh.A[i][M] = 0.0;
+                    sh.A[i][E] = sv;
+                    sh.A[E][i] = sv;
+                    sh.A[i][M] = sh.bk[i] / sh.bsum - sv + dv;
                 }
-            } else if (t == npair + E) {
-                double sn = 0.0, snm = 0.0;
-                for (int y = 0; y < S; ++y) {
-                    sn += nj[y];
-                    snm += nj[y] * mu[y];
-                }
-                sh.A[E][E] = sn - ntot;
-                sh.A[E][M] = ntot - sn + snm;
-                sh.sn = sn;
             }
         }
+        if (tid == 0) {
+            sh.A[E][E] = sn - ntot;
+            sh.sn = sn;
+            sh.snm = snm;
+        }
         __syncthreads();
-        const double sn = sh.sn;
+        if (tid < E && !sh.eact[tid]) sh.A[tid][tid] = 1.0;
+        if (tid == 0) sh.A[E][M] = ntot - sh.sn + sh.snm;
+        __syncthreads();
         if (tid < 32) warp_solve(sh, M);
         __syncthreads();
         if (sh.singular) break;
@@ -242,8 +256,7 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
         for (int y = tid; y < S; y += blockDim.x) {
             if (!act[y]) continue;
             double d = -mu[y] + dlntot;
-            for (int e = 0; e < E; ++e)
-                if (sh.eact[e]) d += sh.sol[e] * a[y * E + e];
+            for (int q = ix.sp[y]; q < ix.sp[y + 1]; ++q) d += sh.sol[ix.se[q]] * ix.sc[q];
             mu[y] = d;
             const double lx = lnN[y] - lntot;
             if (lx > kLnMajor) big = fmax(big, fabs(d));
@@ -251,7 +264,7 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
             conv += nj[y] * fabs(d);
         }
         block_reduce3(sh, big, lam2, conv);
-        conv /= sn;
+        conv /= sh.sn;
         double lam = big > 2.0 ? 2.0 / big : 1.0;
         lam = fmin(lam, lam2);
         for (int y = tid; y < S; y += blockDim.x)
@@ -276,8 +289,7 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
     for (int y = tid; y < S; y += blockDim.x) {
         if (!act[y]) continue;
         double v = -g[y] - lnP;
-        for (int e = 0; e < E; ++e)
-            if (sh.eact[e]) v += sh.sol[e] * a[y * E + e];
+        for (int q = ix.sp[y]; q < ix.sp[y + 1]; ++q) v += sh.sol[ix.se[q]] * ix.sc[q];
         mu[y] = v;
         amax = fmax(amax, v);
     }
@@ -296,7 +308,6 @@ __global__ void __launch_bounds__(kEqThreads) k_equilibrium(Col c, const double 
         if (nout) nout[(size_t)k * S + y] = v * ng;
     }
 }
-
 
 __global__ void k_fluxes(Col c, const double *n, double *q)
 {
@@ -323,6 +334,20 @@ __global__ void k_fluxes(Col c, const double *n, double *q)
     }
 }
 
+// Edge weight of every reaction direction in every layer: 1/q for q > 0, +inf otherwise (no edge).
+// Computed once per layer and shared by every source's search.
+__global__ void k_path_weights(long long n, const double *q, double *wq)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double r = q[i];
+        wq[i] = r > 0.0 ? 1.0 / r : INFINITY;
+    }
+}
+
+// Distances are non-negative doubles (or +inf): their bit patterns order like the values, so the
+// search compares them on the integer pipes (FP64 compares are scarce on this GPU).
+__device__ __forceinline__ unsigned long long key_of(double d) { return (unsigned long long)__double_as_longlong(d); }
+
 // Per-warp shared memory of the pathway search: dist [S] doubles, then pred_sp, pred_e, order [S]
 // ints and done [S] bytes.
 __host__ __device__ inline size_t path_warp_bytes(int S)
@@ -330,7 +355,7 @@ __host__ __device__ inline size_t path_warp_bytes(int S)
     return ((size_t)S * (8 + 4 + 4 + 4 + 1) + 15) / 16 * 16;
 }
 
-__global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const int *src, int wpb,
+__global__ void k_pathways(Col c, PathGraph gr, const double *wq, int nsrc, const int *src, int wpb,
                            double *dist_out, int *pred_out, int *edge_out, int *lim_out, double *limw_out)
 {
     extern __shared__ double path_dyn[];
@@ -343,7 +368,7 @@ __global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const
     double *dist = (double *)base;
     int *pred = (int *)(dist + S), *pe = pred + S, *order = pe + S;
     unsigned char *done = (unsigned char *)(order + S);
-    const double *qk = q + (size_t)k * c.R * 2;
+    const double *wk = wq + (size_t)k * c.R * 2;
     for (int y = lane; y < S; y += 32) {
         dist[y] = INFINITY;
         pred[y] = -1;
@@ -356,22 +381,25 @@ __global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const
     int nord = 0;
     for (;;) {
         // the unfinished species of least distance, the lower index on ties
-        double bd = INFINITY;
+        const unsigned long long kinf = key_of(INFINITY);
+        unsigned long long bd = kinf;
         int bi = S;
-        for (int y = lane; y < S; y += 32)
-            if (!done[y] && dist[y] < bd) {
-                bd = dist[y];
+        for (int y = lane; y < S; y += 32) {
+            const unsigned long long ky = key_of(dist[y]);
+            if (!done[y] && ky < bd) {
+                bd = ky;
                 bi = y;
             }
+        }
         for (int o = 16; o; o >>= 1) {
-            const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+            const unsigned long long od = __shfl_xor_sync(0xffffffffu, bd, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (od < bd || (od == bd && oi < bi)) {
                 bd = od;
                 bi = oi;
             }
         }
-        if (!(bd < INFINITY)) break;
+        if (!(bd < kinf)) break;
         const int u = bi;
         if (lane == 0) {
             done[u] = 1;
@@ -384,16 +412,16 @@ __global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const
         for (int g = gr.gp[u] + lane; g < gr.gp[u + 1]; g += 32) {
             const int v = gr.gv[g];
             double best = dist[v];
+            unsigned long long kb = key_of(best);
             int be = -1;
             for (int t = gr.gs[g]; t < gr.gs[g + 1]; ++t) {
                 const int e = gr.gcode[t];
-                const double rate = qk[e];
-                if (rate > 0.0) {
-                    const double cand = du + 1.0 / rate;
-                    if (cand < best) {
-                        best = cand;
-                        be = e;
-                    }
+                const double cand = du + wk[e];   // +inf for a direction without rate
+                const unsigned long long kc = key_of(cand);
+                if (kc < kb) {
+                    kb = kc;
+                    best = cand;
+                    be = e;
                 }
             }
             if (be >= 0) {
@@ -421,7 +449,7 @@ __global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const
             const int v = order[i], u = pred[v];
             if (u < 0) continue;
             const int e = pe[v];
-            const double wv = 1.0 / qk[e];
+            const double wv = wk[e];
             if (u == s0 || wv > limw_out[o + u]) {
                 lim_out[o + v] = e;
                 limw_out[o + v] = wv;
@@ -434,17 +462,17 @@ __global__ void k_pathways(Col c, PathGraph gr, const double *q, int nsrc, const
 
 }  // namespace
 
-cudaError_t launch_equilibrium(const Col &c, const double *b, double *x, double *nout, int max_iter, double tol,
-                               int *iters, int *status, cudaStream_t st)
+cudaError_t launch_equilibrium(const Col &c, const EqIndex &ix, const double *b, double *x, double *nout,
+                               int max_iter, double tol, int *iters, int *status, cudaStream_t st)
 {
     if (c.E + 1 > kEqMaxE) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)c.S * 3 * sizeof(double) + (size_t)c.S * (c.E + 1);
+    const size_t smem = (size_t)c.S * 3 * sizeof(double) + (size_t)c.S;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_equilibrium, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_equilibrium<<<c.L, kEqThreads, smem, st>>>(c, b, x, nout, max_iter, tol, iters, status);
+    k_equilibrium<<<c.L, kEqThreads, smem, st>>>(c, ix, b, x, nout, max_iter, tol, iters, status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -457,10 +485,15 @@ void launch_fluxes(const Col &c, const double *n, double *q, cudaStream_t st)
     count_launches(1);
 }
 
-cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, int nsrc, const int *src,
-                            double *dist, int *pred_sp, int *pred_edge, int *lim_edge, double *lim_w,
-                            cudaStream_t st)
+cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, double *wbuf, int nsrc,
+                            const int *src, double *dist, int *pred_sp, int *pred_edge, int *lim_edge,
+                            double *lim_w, cudaStream_t st)
 {
+    const long long nw = (long long)c.L * c.R * 2;
+    if (nw > 0) {
+        k_path_weights<<<(int)std::min<long long>((nw + 255) / 256, 152LL * 8), 256, 0, st>>>(nw, q, wbuf);
+        count_launches(1);
+    }
     const size_t per = path_warp_bytes(c.S);
     const size_t cap = 96 * 1024;
     if (per > 200 * 1024) return cudaErrorInvalidValue;
@@ -472,7 +505,8 @@ cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, i
     }
     const long long probs = (long long)nsrc * c.L;
     const int blocks = (int)((probs + wpb - 1) / wpb);
-    k_pathways<<<blocks, 32 * wpb, smem, st>>>(c, g, q, nsrc, src, wpb, dist, pred_sp, pred_edge, lim_edge, lim_w);
+    k_pathways<<<blocks, 32 * wpb, smem, st>>>(c, g, wbuf, nsrc, src, wpb, dist, pred_sp, pred_edge, lim_edge,
+                                              lim_w);
     count_launches(1);
     return cudaGetLastError();
 }

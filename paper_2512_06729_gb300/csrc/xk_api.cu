@@ -35,12 +35,19 @@ struct xk_ctx {
     std::vector<int> elem, rtype, reac, prod, form, prow;
     std::vector<double> mass, arr, troe, nasa, lam, dlam, J0, sigma, sigma_abs, P, T, Kzz, dcoef;
     double mu = 0.5, tf = 0.5, g = 0, mbar = 0, alpha_T = 0;
+    std::vector<double> sigma_s;   // Rayleigh cross sections S x W (empty: none)
+    double albedo = 0.0;
+    int diffuse = 0;
     bool have_net = false, have_photo = false, have_atm = false;
     bool rates_valid = false;      // k_f, k_r of the loaded network and atmosphere are in the workspace
     // host index structures
     std::vector<int> yp, yent, jp, jcol, jtp, jrs, jdq, abs_sp;
     std::vector<int> pg_p, pg_v, pg_s, pg_code;   // reaction graph of the pathway analyser
+    std::vector<int> eq_sp, eq_se, eq_ep, eq_ey, eq_eij;   // sparse element structure (equilibrium)
+    std::vector<double> eq_sc, eq_ec;
     std::vector<double> sig_abs_c;
+    std::vector<int> sca_sp;           // species with a non-zero scattering cross section
+    std::vector<double> sig_sca_c;
     // device
     char *ws = nullptr;
     size_t ws_bytes = 0;
@@ -75,7 +82,9 @@ struct xk_ctx {
     bool ready = false;
     // equilibrium initial state and pathway analyser
     PathGraph pgraph{};
+    EqIndex eqix{};
     int *eq_iters = nullptr, *eq_status = nullptr, *path_src = nullptr;
+    double *path_w = nullptr;   // [L][R][2] edge weights of the pathway search
     // Lagrangian parcel scheme: its buffers in the workspace (ParcelArgs without the policy)
     ParcelArgs parcel{};
     double *parcel_kzz0 = nullptr;   // [L] zero eddy profile: the molecular part of u, v
@@ -237,6 +246,51 @@ void build_indices(xk_ctx *c)
             c->sig_abs_c.insert(c->sig_abs_c.end(), c->sigma_abs.begin() + (size_t)y * c->W,
                                 c->sigma_abs.begin() + (size_t)(y + 1) * c->W);
         }
+    // scatterers with a non-zero cross section somewhere
+    c->sca_sp.clear();
+    c->sig_sca_c.clear();
+    if (c->have_photo && c->W > 0 && !c->sigma_s.empty())
+        for (int y = 0; y < S; ++y) {
+            bool nz = false;
+            for (int w = 0; w < c->W; ++w) nz |= c->sigma_s[(size_t)y * c->W + w] != 0.0;
+            if (!nz) continue;
+            c->sca_sp.push_back(y);
+            c->sig_sca_c.insert(c->sig_sca_c.end(), c->sigma_s.begin() + (size_t)y * c->W,
+                                c->sigma_s.begin() + (size_t)(y + 1) * c->W);
+        }
+    // equilibrium: each species' elements, and each Newton-system entry's species (increasing)
+    const int E = c->E;
+    c->eq_sp.assign(S + 1, 0);
+    c->eq_se.clear();
+    c->eq_sc.clear();
+    for (int y = 0; y < S; ++y) {
+        for (int e = 0; e < E; ++e)
+            if (c->elem[(size_t)y * E + e] != 0) {
+                c->eq_se.push_back(e);
+                c->eq_sc.push_back((double)c->elem[(size_t)y * E + e]);
+            }
+        c->eq_sp[y + 1] = (int)c->eq_se.size();
+    }
+    c->eq_ep.assign(1, 0);
+    c->eq_ey.clear();
+    c->eq_ec.clear();
+    c->eq_eij.clear();
+    auto add_entry = [&](int code, int i, int j) {
+        for (int y = 0; y < S; ++y) {
+            const double ai = c->elem[(size_t)y * E + i], aj = j >= 0 ? c->elem[(size_t)y * E + j] : 1.0;
+            if (ai != 0.0 && aj != 0.0) {
+                c->eq_ey.push_back(y);
+                c->eq_ec.push_back(ai * aj);
+            }
+        }
+        c->eq_eij.push_back(code);
+        c->eq_ep.push_back((int)c->eq_ey.size());
+    };
+    if (E <= 30) {
+        for (int i = 0; i < E; ++i)
+            for (int j = i; j < E; ++j) add_entry(i * 32 + j, i, j);
+        for (int i = 0; i < E; ++i) add_entry(-1 - i, i, -1);
+    }
     // pathway graph: each reaction direction gives an edge from every species it consumes to every
     // species it produces (itself excepted), grouped by source, then target, codes increasing
     std::vector<std::vector<std::pair<int, int>>> out(S);   // (target, code) per source
@@ -309,6 +363,14 @@ size_t layout(xk_ctx *c, char *base)
     t.sig_abs = b.take<double>(std::max<size_t>(1, (size_t)Sabs * W));
     t.abs_sp = b.take<int>(std::max(Sabs, 1));
     t.mu = c->mu; t.tf = c->tf;
+    const int Ssca = (int)c->sca_sp.size();
+    t.Ssca = Ssca;
+    t.diffuse = (c->diffuse && W > 0) ? 1 : 0;
+    t.albedo = c->albedo;
+    t.sig_sca = b.take<double>(std::max<size_t>(1, (size_t)Ssca * W));
+    t.sca_sp = b.take<int>(std::max(Ssca, 1));
+    t.alpha_s = b.take<double>((size_t)L * std::max(W, 1));
+    t.rt = b.take<double>(t.diffuse ? 4 * (size_t)L * W : 1);
     t.P = b.take<double>(L); t.T = b.take<double>(L); t.Kzz = b.take<double>(L);
     t.g = c->g; t.mbar = c->mbar; t.alpha_T = c->alpha_T;
     t.ngas = b.take<double>(L); t.z = b.take<double>(L); t.dz = b.take<double>(L); t.dzi = b.take<double>(L);
@@ -408,6 +470,16 @@ size_t layout(xk_ctx *c, char *base)
     c->eq_iters = b.take<int>(L);
     c->eq_status = b.take<int>(L);
     c->path_src = b.take<int>(std::max(S, 1));
+    c->path_w = b.take<double>(std::max<size_t>(1, 2 * LR));
+    EqIndex &ei = c->eqix;
+    ei.sp = b.take<int>(S + 1);
+    ei.se = b.take<int>(std::max<size_t>(1, c->eq_se.size()));
+    ei.sc = b.take<double>(std::max<size_t>(1, c->eq_sc.size()));
+    ei.ep = b.take<int>(c->eq_ep.size());
+    ei.ey = b.take<int>(std::max<size_t>(1, c->eq_ey.size()));
+    ei.ec = b.take<double>(std::max<size_t>(1, c->eq_ec.size()));
+    ei.eij = b.take<int>(std::max<size_t>(1, c->eq_eij.size()));
+    ei.nent = (int)c->eq_eij.size();
     c->pgraph.gp = b.take<int>(S + 1);
     c->pgraph.gv = b.take<int>(std::max<size_t>(1, c->pg_v.size()));
     c->pgraph.gs = b.take<int>(std::max<size_t>(1, c->pg_s.size()));
@@ -922,6 +994,7 @@ int xk_load_photo(xk_ctx *c, int W, int Rph, const int *prow, const double *lamb
             return fail(c, XK_EINVAL, "reaction %d is not photolysis but has a sigma row", r);
         }
     }
+    if (W != c->W) c->sigma_s.clear();   // scattering cross sections belong to the old grid
     c->W = W; c->Rph = Rph;
     c->prow.assign(prow, prow + c->R);
     c->lam.assign(lambda, lambda + W);
@@ -933,6 +1006,27 @@ int xk_load_photo(xk_ctx *c, int W, int Rph, const int *prow, const double *lamb
     c->have_photo = true;
     c->ready = false;
     (void)nph;
+    return XK_OK;
+}
+
+int xk_load_scattering(xk_ctx *c, int W, const double *sigma_s, double albedo, int diffuse)
+{
+    if (!c) return XK_EINVAL;
+    if (!c->have_photo) return fail(c, XK_EINVAL, "load the photolysis inputs first");
+    if (W != c->W) return fail(c, XK_EINVAL, "scattering grid of %d bins, photolysis grid of %d", W, c->W);
+    if (!(albedo >= 0.0 && albedo <= 1.0)) return fail(c, XK_EINVAL, "albedo must lie in [0, 1]");
+    if (diffuse != 0 && diffuse != 1) return fail(c, XK_EINVAL, "diffuse must be 0 or 1");
+    if (sigma_s) {
+        for (size_t i = 0; i < (size_t)c->S * W; ++i)
+            if (!(sigma_s[i] >= 0.0) || !std::isfinite(sigma_s[i]))
+                return fail(c, XK_EINVAL, "scattering cross sections must be finite and non-negative");
+        c->sigma_s.assign(sigma_s, sigma_s + (size_t)c->S * W);
+    } else {
+        c->sigma_s.clear();
+    }
+    c->albedo = albedo;
+    c->diffuse = diffuse;
+    c->ready = false;
     return XK_OK;
 }
 
@@ -1025,6 +1119,9 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     up(c, k.elem, c->elem);
     up(c, c->pgraph.gp, c->pg_p); up(c, c->pgraph.gv, c->pg_v); up(c, c->pgraph.gs, c->pg_s);
     up(c, c->pgraph.gcode, c->pg_code);
+    up(c, c->eqix.sp, c->eq_sp); up(c, c->eqix.se, c->eq_se); up(c, c->eqix.sc, c->eq_sc);
+    up(c, c->eqix.ep, c->eq_ep); up(c, c->eqix.ey, c->eq_ey); up(c, c->eqix.ec, c->eq_ec);
+    up(c, c->eqix.eij, c->eq_eij);
     up(c, k.mass, c->mass); up(c, k.nasa, c->nasa); up(c, k.dcoef, c->dcoef);
     up(c, k.arr, c->arr); up(c, k.troe, c->troe); up(c, k.rtype, c->rtype); up(c, k.reac, c->reac);
     up(c, k.prod, c->prod); up(c, k.form, c->form); up(c, k.prow, c->prow);
@@ -1032,6 +1129,7 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     up(c, k.jdq, c->jdq);
     up(c, k.J0, c->J0); up(c, k.dlam, c->dlam); up(c, k.sigma, c->sigma); up(c, k.sig_abs, c->sig_abs_c);
     up(c, k.abs_sp, c->abs_sp);
+    up(c, k.sig_sca, c->sig_sca_c); up(c, k.sca_sp, c->sca_sp);
     up(c, k.P, c->P); up(c, k.T, c->T); up(c, k.Kzz, c->Kzz);
     cudaMemsetAsync(c->bar, 0, 8 * sizeof(unsigned), c->st);
     if (c->counter) cudaMemsetAsync(c->counter, 0, 8 * sizeof(unsigned), c->st);
@@ -1721,8 +1819,8 @@ int xk_equilibrium(xk_ctx *c, const double *b, double *x, int set_state, int max
     if (max_iter <= 0 || !(tol > 0.0)) return fail(c, XK_EINVAL, "equilibrium: bad max_iter or tol");
     if (c->E + 1 > 31) return fail(c, XK_EINVAL, "equilibrium: at most 30 elements");
     ensure_rates(c);   // G/RT of the atmosphere
-    cudaError_t e = launch_equilibrium(c->col, b, x, set_state ? c->col.n : nullptr, max_iter, tol, c->eq_iters,
-                                       c->eq_status, c->st);
+    cudaError_t e = launch_equilibrium(c->col, c->eqix, b, x, set_state ? c->col.n : nullptr, max_iter, tol,
+                                       c->eq_iters, c->eq_status, c->st);
     if (e != cudaSuccess) return fail(c, XK_EINVAL, "equilibrium launch: %s", cudaGetErrorString(e));
     std::vector<int> its(c->L), sts(c->L);
     cudaMemcpyAsync(its.data(), c->eq_iters, sizeof(int) * c->L, cudaMemcpyDeviceToHost, c->st);
@@ -1767,8 +1865,8 @@ int xk_pathways(xk_ctx *c, const double *q, int nsrc, const int *src, double *di
     for (int j = 0; j < nsrc; ++j)
         if (src[j] < 0 || src[j] >= c->S) return fail(c, XK_EINVAL, "pathways: source %d out of range", src[j]);
     cudaMemcpyAsync(c->path_src, src, sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st);
-    cudaError_t e = launch_pathways(c->col, c->pgraph, q, nsrc, c->path_src, dist, pred_sp, pred_edge, lim_edge,
-                                    lim_w, c->st);
+    cudaError_t e = launch_pathways(c->col, c->pgraph, q, c->path_w, nsrc, c->path_src, dist, pred_sp, pred_edge,
+                                    lim_edge, lim_w, c->st);
     if (e != cudaSuccess) return fail(c, XK_EINVAL, "pathways launch: %s", cudaGetErrorString(e));
     return finish_eval(c, "pathways");
 }

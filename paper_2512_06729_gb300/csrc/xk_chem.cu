@@ -148,35 +148,103 @@ __global__ void k_rates(Col c)
 }
 
 // ---------------------------------------------------------------------------
-// photolysis (Sec. 2.3.3): direct beam, optical depth to the layer midpoint
+// photolysis (Sec. 2.3.3): extinction by absorption and Rayleigh scattering, direct beam with the
+// optical depth to the layer midpoint, and optionally the diffuse field J_diff = (J_up + J_down) / 2
 // ---------------------------------------------------------------------------
+constexpr int kExtLayers = 4;   // layers per thread of the extinction sums (sigma loaded once for them)
+
+// alpha (absorption) and alpha_s (scattering) per (layer, wavelength): one thread per wavelength and
+// kExtLayers consecutive layers, reading each cross section once for all of them (coalesced in w)
 __global__ void k_photo_alpha(Col c, const double *n)
 {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)c.L * c.W) return;
-    int k = (int)(idx / c.W), w = (int)(idx % c.W);
-    const double *nk = n + (long long)k * c.S;
-    double s = 0.0;
-    for (int i = 0; i < c.Sabs; ++i)
-        s += c.sig_abs[(long long)i * c.W + w] * nk[c.abs_sp[i]];
-    c.alpha[idx] = s;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0 = blockIdx.y * kExtLayers;
+    if (w >= c.W) return;
+    const int nk = min(kExtLayers, c.L - k0);
+    double sa[kExtLayers], ss[kExtLayers];
+#pragma unroll
+    for (int j = 0; j < kExtLayers; ++j) sa[j] = ss[j] = 0.0;
+    for (int i = 0; i < c.Sabs; ++i) {
+        const double sg = c.sig_abs[(long long)i * c.W + w];
+        const int y = c.abs_sp[i];
+#pragma unroll
+        for (int j = 0; j < kExtLayers; ++j)
+            if (j < nk) sa[j] += sg * n[(long long)(k0 + j) * c.S + y];
+    }
+    for (int i = 0; i < c.Ssca; ++i) {
+        const double sg = c.sig_sca[(long long)i * c.W + w];
+        const int y = c.sca_sp[i];
+#pragma unroll
+        for (int j = 0; j < kExtLayers; ++j)
+            if (j < nk) ss[j] += sg * n[(long long)(k0 + j) * c.S + y];
+    }
+#pragma unroll
+    for (int j = 0; j < kExtLayers; ++j)
+        if (j < nk) {
+            c.alpha[(long long)(k0 + j) * c.W + w] = sa[j];
+            c.alpha_s[(long long)(k0 + j) * c.W + w] = ss[j];
+        }
 }
 
+// One thread per wavelength.  Top-down: optical depth, direct beam into Jw and, with the diffuse
+// field, the two-stream recursion.  In layer k the diffuse fluxes leaving it, D_k down through its
+// bottom and U_k up through its top, obey
+//     D_k = T_k D_{k+1} + r_k U_{k-1} + P_k / 2,   U_k = T_k U_{k-1} + r_k D_{k+1} + P_k / 2,
+// with D_L = 0 and U_{-1} = albedo (D_0 + beam at the bottom); r_k = (1 - t) omega / 2,
+// T_k = t + (1 - t) omega / 2, t = exp(-2 dtau_k), omega_k = dtau_s / dtau, and P_k = omega_k mu J0
+// (e^{-tau_top/mu} - e^{-tau_bot/mu}) the beam photons the layer scatters.  Going down, each layer's
+// fluxes are written in terms of the flux entering from below: D_k = p_k U_{k-1} + h0_k,
+// U_k = q_k U_{k-1} + h1_k (p_k is the reflectance of the layers from k up, as in the adding
+// method); going up, U_{-1} is found from the boundary and the fluxes follow layer by layer.
 __global__ void k_photo_J(Col c)
 {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= c.W) return;
-    double above = 0.0;
-    double J0 = c.J0[w];
+    const long long LW = (long long)c.L * c.W;
+    const double J0 = c.J0[w], mu = c.mu;
+    double above = 0.0, pn = 0.0, h0n = 0.0;
     for (int k = c.L - 1; k >= 0; --k) {
-        double a = c.alpha[(long long)k * c.W + w];
-        double tau = above + 0.5 * a * c.dz[k];
-        c.Jw[(long long)k * c.W + w] = J0 * exp(-tau / c.mu);
-        above += a * c.dz[k];
+        const long long i = (long long)k * c.W + w;
+        const double ta = c.alpha[i] * c.dz[k], ts = c.alpha_s[i] * c.dz[k];
+        const double dt = ta + ts;
+        c.Jw[i] = J0 * exp(-(above + 0.5 * dt) / mu);
+        if (c.diffuse) {
+            const double om = dt > 0.0 ? ts / dt : 0.0;
+            const double t = exp(-dt / 0.5);
+            const double r = (1.0 - t) * om / 2.0, T = t + (1.0 - t) * om / 2.0;
+            const double P = om * mu * J0 * (exp(-above / mu) - exp(-(above + dt) / mu));
+            const double den = 1.0 - r * pn;
+            const double q = T / den, h1 = (r * h0n + P / 2.0) / den;
+            const double p = r + T * pn * q;
+            const double h0 = T * pn * h1 + T * h0n + P / 2.0;
+            c.rt[i] = p;
+            c.rt[LW + i] = q;
+            c.rt[2 * LW + i] = h0;
+            c.rt[3 * LW + i] = h1;
+            pn = p;
+            h0n = h0;
+        }
+        above += dt;
+    }
+    if (!c.diffuse) return;
+    const double A = c.albedo;
+    const double bottom = mu * J0 * exp(-above / mu);
+    // U_{-1} = A (D_0 + bottom), D_0 = p_0 U_{-1} + h0_0
+    double Ub = A * (c.rt[2 * LW + w] + bottom) / (1.0 - A * c.rt[w]);
+    for (int k = 0; k < c.L; ++k) {
+        const long long i = (long long)k * c.W + w;
+        const double Dk = c.rt[i] * Ub + c.rt[2 * LW + i];
+        const double Uk = c.rt[LW + i] * Ub + c.rt[3 * LW + i];
+        double Dn = 0.0;
+        if (k + 1 < c.L) Dn = c.rt[i + c.W] * Uk + c.rt[2 * LW + i + c.W];
+        const double up = 0.5 * (Ub + Uk), dn = 0.5 * (Dk + Dn);
+        c.Jw[i] += 0.5 * (up + dn);
+        Ub = Uk;
     }
 }
 
-// k_ph = t_f sum_w J(k, w) sigma(w) dlambda(w); one warp per (layer, reaction)
+// k_ph = t_f sum_w J(k, w) sigma(w) dlambda(w); one warp per (layer, reaction), lanes striding
+// the wavelengths (coalesced), partial sums added in lane order
 __global__ void k_photo_k(Col c)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -185,11 +253,8 @@ __global__ void k_photo_k(Col c)
     int k = warp / c.Rph, q = warp % c.Rph;
     const double *J = c.Jw + (long long)k * c.W;
     const double *sg = c.sigma + (long long)q * c.W;
-    // each lane sums a contiguous chunk in order; chunks are added in lane order
-    int per = (c.W + 31) / 32;
-    int w0 = lane * per, w1 = min(c.W, w0 + per);
     double s = 0.0;
-    for (int w = w0; w < w1; ++w)
+    for (int w = lane; w < c.W; w += 32)
         s += J[w] * sg[w] * c.dlam[w];
     double tot = 0.0;
     for (int l = 0; l < 32; ++l) {
@@ -667,7 +732,11 @@ void launch_photolysis(const Col &c, const double *n, cudaStream_t st)
 {
     if (c.Rph == 0) return;
     if (c.W > 0) {
-        if (((long long)c.L * c.W) > 0) { count_launches(1); k_photo_alpha<<<nblocks((long long)c.L * c.W), kThreads, 0, st>>>(c, n); }
+        if (c.L > 0) {
+            count_launches(1);
+            dim3 grid(nblocks(c.W, 128), (c.L + kExtLayers - 1) / kExtLayers);
+            k_photo_alpha<<<grid, 128, 0, st>>>(c, n);
+        }
         if ((c.W) > 0) { count_launches(1); k_photo_J<<<nblocks(c.W, 128), 128, 0, st>>>(c); }
     }
     if (((long long)c.L * c.Rph * 32) > 0) { count_launches(1); k_photo_k<<<nblocks((long long)c.L * c.Rph * 32), kThreads, 0, st>>>(c); }

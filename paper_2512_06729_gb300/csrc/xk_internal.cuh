@@ -37,6 +37,14 @@ struct Col {
     const double *J0, *dlam, *sigma, *sig_abs;   // sig_abs: Sabs x W
     const int *abs_sp;
     double mu, tf;
+    // Rayleigh scattering (Sec. 2.3.3): cross sections of the Ssca scattering species sca_sp,
+    // Ssca x W; the diffuse field (diffuse = 1) with lower-boundary albedo; alpha_s [L][W] the
+    // scattering coefficient; rt [4][L][W] the two-stream recursion's coefficients
+    int Ssca, diffuse;
+    const double *sig_sca;
+    const int *sca_sp;
+    double albedo;
+    double *alpha_s, *rt;
     // atmosphere
     const double *P, *T, *Kzz;
     double g, mbar, alpha_T;
@@ -151,19 +159,29 @@ __device__ __forceinline__ double jac_entry(const Col &c, int q, const double *d
 struct PathGraph {
     const int *gp, *gv, *gs, *gcode;
 };
+// Sparse element structure for the equilibrium solve, built on the host: species y holds elements
+// se[sp[y] .. sp[y+1]) with counts sc[..]; entry t of the Newton system (eij[t] = i * 32 + j for the
+// element pair i <= j, -1 - i for element i's own sums) is a sum over the species ey[ep[t] ..
+// ep[t+1]) (increasing) with coefficients ec[..] (a_iy a_jy, or a_iy).
+struct EqIndex {
+    const int *sp, *se, *ep, *ey, *eij;
+    const double *sc, *ec;
+    int nent;
+};
 // Equilibrium composition per layer (xk_analysis.cu): element totals b [L][E] (nullptr: from the
 // state c.n); mole fractions into x [L][S] (may be nullptr) and, when nout is set, number densities
 // x n_gas into nout; per layer the iterations taken and a status (0 converged, 1 not converged,
 // -1 singular system).  Needs c.grt of the current atmosphere.
-cudaError_t launch_equilibrium(const Col &c, const double *b, double *x, double *nout, int max_iter, double tol,
-                               int *iters, int *status, cudaStream_t st);
+cudaError_t launch_equilibrium(const Col &c, const EqIndex &ix, const double *b, double *x, double *nout,
+                               int max_iter, double tol, int *iters, int *status, cudaStream_t st);
 // Forward and reverse rate of every reaction in every layer at state n: q [L][R][2].
 void launch_fluxes(const Col &c, const double *n, double *q, cudaStream_t st);
 // Dijkstra from each source src[j] (device, nsrc) in every layer of rates q [L][R][2]: outputs
-// [nsrc][L][S] (any output pointer may be nullptr).
-cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, int nsrc, const int *src,
-                            double *dist, int *pred_sp, int *pred_edge, int *lim_edge, double *lim_w,
-                            cudaStream_t st);
+// [nsrc][L][S] (any output pointer may be nullptr).  wbuf: L * R * 2 doubles of scratch for the edge
+// weights 1/q.
+cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, double *wbuf, int nsrc,
+                            const int *src, double *dist, int *pred_sp, int *pred_edge, int *lim_edge,
+                            double *lim_w, cudaStream_t st);
 
 // Lagrangian parcel scheme (Sec. 2, Fig. 2): buffers and state of one global iteration.
 struct ParcelState {

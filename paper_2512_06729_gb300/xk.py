@@ -76,6 +76,7 @@ SIGNATURES = {
     "xk_last_error": (C.c_char_p, [_vp]),
     "xk_load_network": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _ip, _dp, _ip, _ip, _ip, _dp, _dp, _ip, _dp]),
     "xk_load_photo": (C.c_int, [_vp, C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_double]),
+    "xk_load_scattering": (C.c_int, [_vp, C.c_int, _dp, C.c_double, C.c_int]),
     "xk_load_atmosphere": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, C.c_double]),
     "xk_workspace_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "xk_set_workspace": (C.c_int, [_vp, _vp, C.c_size_t]),
@@ -208,6 +209,10 @@ class Column:
             self._call("xk_load_photo", W, Rph, i(p.prow), d(p.lam if W else one), d(p.dlam if W else one),
                        d(p.J0 if W else one), d(p.sigma if p.sigma.size else one),
                        d(p.sigma_abs if p.sigma_abs.size else one), float(p.mu), float(p.tf))
+            sig_s = getattr(p, "sigma_s", None)
+            if W > 0 and (sig_s is not None or getattr(p, "diffuse", 0)):
+                self._call("xk_load_scattering", W, d(sig_s) if sig_s is not None else None,
+                           float(getattr(p, "albedo", 0.0)), int(getattr(p, "diffuse", 0)))
         self._call("xk_load_atmosphere", p.L, d(p.P_bar), d(p.T), d(p.Kzz), d(p.dcoef), float(p.g),
                    float(p.mbar), float(p.alpha_T))
         nbytes = C.c_size_t()
