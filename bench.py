@@ -870,8 +870,11 @@ def analysis_object(live, calls=5, cpu=True, sources=8):
         return start.elapsed_time(end) / calls, res
 
     ms_eq, (x, info) = timed(lambda: col.equilibrium())
-    # sums of the reduced Newton system per iteration and layer: (E(E+1)/2 + 2E + 2) S multiply-adds
-    flops_it = 2.0 * (E * (E + 1) / 2 + 2 * E + 2) * S * L
+    # FP64 work per Newton iteration and layer: the system's sparse sums (a multiply-add per species
+    # and pair of its elements, three flops per species and element for the two element sums), the
+    # species' potentials and updates (a multiply-add per element), and the totals
+    ne = np.count_nonzero(prob.elem, axis=1).astype(float)
+    flops_it = L * (2.0 * np.sum(ne * (ne + 1) / 2) + 3.0 * np.sum(ne) + 2.0 * np.sum(ne) + 6.0 * S)
     ach = flops_it * info.iters_max / (ms_eq * 1e-3) / 1e12
     src = list(range(2, 2 + sources))
     q = col.reaction_fluxes(n0)

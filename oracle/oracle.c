@@ -1261,3 +1261,212 @@ void ora_pathways(const ora_problem *p, const double *q, int src, double *dist, 
     }
     free(done);
 }
+
+/* ------------------------------------------------------------ BDF integrator */
+/*
+ * Variable-order, variable-step backward differentiation formulas, the family of the paper's
+ * DLSODES (Sec. 2.1, "Commonly used methods"), applied to Eq. 1 on the Eulerian grid.  Order q uses
+ * the accepted states at tau_1 > ... > tau_q and asks that the interpolating polynomial through them
+ * and the new state at tau_0 = t + h have the derivative F at tau_0:
+ *     c_0 y_new + sum_{j>=1} c_j y(tau_j) = F(y_new),   c_j = l_j'(tau_0)  (Lagrange basis).
+ * Linearly implicit: F is linearised once about the predictor y_hat (the polynomial through the
+ * last q+1 states, fewer at the start, evaluated at tau_0), so each step solves
+ *     (c_0 I - J(y_hat)) delta = F(y_hat) - c_0 y_hat - sum_{j>=1} c_j y(tau_j),   y_new = y_hat + delta
+ * with the same block-tridiagonal solve as the backward-Euler step (q = 1 with y_hat = y_n is that
+ * step exactly).
+ * Error control: the local error of order q is estimated as (y_new - y_hat) / (q + 1) and measured
+ * relative to y_new over species above f_floor mixing ratio, in units of rtol (err <= 1 accepts).
+ * A step is also rejected when y_new is non-finite or below -neg_tol n_gas.  On rejection h shrinks
+ * by max(0.2, min(0.9, 0.9 err^{-1/(q+1)})) (0.25 for a bad state) and, after two rejections in a
+ * row, the order drops by one.  On acceptance negatives are clipped to zero, and after q + 1 steps
+ * at one order the next order is chosen among q - 1, q, q + 1 by the largest step factor
+ * eta = err_q'^{-1/(q'+1)} (divided by 1.3, 1.2, 1.4 respectively, favouring the current order),
+ * err_q' being the same estimate with the predictor of degree q'; otherwise eta = eta_q / 1.2.  The
+ * next step is h * clamp(eta, 0.2, grow), at most dt_max and no further than t_end.
+ */
+void ora_bdf_coeffs(int q, const double *tau, double *c)
+{
+    double c0 = 0.0;
+    for (int m = 1; m <= q; ++m)
+        c0 += 1.0 / (tau[0] - tau[m]);
+    c[0] = c0;
+    for (int j = 1; j <= q; ++j) {
+        double num = 1.0, den = 1.0;
+        for (int m = 0; m <= q; ++m) {
+            if (m == j) continue;
+            if (m != 0) num *= tau[0] - tau[m];
+            den *= tau[j] - tau[m];
+        }
+        c[j] = num / den;
+    }
+}
+
+void ora_bdf_extrap(int m, const double *tau, double t, double *w)
+{
+    for (int j = 0; j < m; ++j) {
+        double v = 1.0;
+        for (int i = 0; i < m; ++i)
+            if (i != j) v *= (t - tau[i]) / (tau[j] - tau[i]);
+        w[j] = v;
+    }
+}
+
+#define ORA_BDF_QMAX 5
+
+/* max over entries with y > floor n_gas of |y - yp| / (K rtol y) */
+static double bdf_err(const ora_problem *p, const double *ngas, double f_floor, const double *y,
+                      const double *yp, double K, double rtol)
+{
+    double e = 0.0;
+    for (int k = 0; k < p->L; ++k)
+        for (int s = 0; s < p->S; ++s) {
+            size_t i = (size_t)k * p->S + s;
+            if (y[i] > f_floor * ngas[k]) {
+                double v = fabs(y[i] - yp[i]) / (K * rtol * y[i]);
+                if (v > e) e = v;
+            }
+        }
+    return e;
+}
+
+int ora_bdf_run(const ora_problem *p, const ora_policy *pol, const ora_bdf_config *cfg, double *n,
+                double h0, double t_end, int stop_at_steady, int max_steps, ora_bdf_info *info)
+{
+    int L = p->L, S = p->S, R = p->R;
+    size_t LS = (size_t)L * S;
+    int qmax = cfg->qmax < 1 ? 1 : (cfg->qmax > ORA_BDF_QMAX ? ORA_BDF_QMAX : cfg->qmax);
+    int HMAX = qmax + 2;                          /* states kept: enough for the order q+1 predictor */
+    double *Y = malloc(sizeof(double) * LS * HMAX), th[ORA_BDF_QMAX + 2];
+    double *yhat = malloc(sizeof(double) * LS * 6), *g = yhat + LS, *rhs = g + LS, *delta = rhs + LS;
+    double *ynew = delta + LS, *yalt = ynew + LS;
+    double *kf = malloc(sizeof(double) * (size_t)L * R * 2), *kr = kf + (size_t)L * R;
+    double *kph = malloc(sizeof(double) * (size_t)L * (p->Rph > 0 ? p->Rph : 1));
+    double *F = malloc(sizeof(double) * LS * 3), *lo = F + LS, *up = lo + LS;
+    double *A = malloc(sizeof(double) * LS * S);
+    double *ngas = malloc(sizeof(double) * L * 4);
+    ora_grid(p, ngas, ngas + L, ngas + 2 * L, ngas + 3 * L);
+    ora_rate_coefficients(p, kf, kr);
+    memset(info, 0, sizeof(*info));
+    memcpy(Y, n, sizeof(double) * LS);
+    th[0] = 0.0;
+    int hist = 1, q = 1, nq = 0, nrej = 0, rc = 1;
+    double t = 0.0, h = h0;
+    if (h > t_end - t) h = t_end - t;
+    while (info->steps < max_steps) {
+        info->steps++;
+        int qe = q < hist ? q : hist;
+        double tau[ORA_BDF_QMAX + 2], c[ORA_BDF_QMAX + 1], w[ORA_BDF_QMAX + 2];
+        tau[0] = t + h;
+        for (int j = 1; j <= qe; ++j) tau[j] = th[j - 1];
+        ora_bdf_coeffs(qe, tau, c);
+        int m = qe + 1 < hist ? qe + 1 : hist;
+        ora_bdf_extrap(m, th, t + h, w);
+        for (size_t i = 0; i < LS; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < m; ++j) v += w[j] * Y[(size_t)j * LS + i];
+            yhat[i] = v;
+        }
+        for (size_t i = 0; i < LS; ++i) {
+            double v = c[0] * yhat[i];
+            for (int j = 1; j <= qe; ++j) v += c[j] * Y[(size_t)(j - 1) * LS + i];
+            g[i] = v;
+        }
+        ora_photolysis(p, yhat, kph);
+        ora_residual(p, kf, kr, kph, yhat, F);
+        for (size_t i = 0; i < LS; ++i) rhs[i] = F[i] - g[i];
+        ora_jacobian(p, kf, kr, kph, yhat, 1.0 / c[0], A, lo, up);
+        if (ora_block_solve_refined(L, S, A, lo, up, rhs, delta, ORA_REFINE_SWEEPS) != 0) { rc = -1; break; }
+        int bad = 0;
+        for (int k = 0; k < L; ++k)
+            for (int s = 0; s < S; ++s) {
+                size_t i = (size_t)k * S + s;
+                ynew[i] = yhat[i] + delta[i];
+                if (!isfinite(ynew[i]) || ynew[i] < -pol->neg_tol * ngas[k]) bad = 1;
+            }
+        double err = bad ? INFINITY : bdf_err(p, ngas, pol->f_floor, ynew, yhat, qe + 1.0, cfg->rtol);
+        if (cfg->fixed_step) {
+            if (bad) { rc = -2; break; }
+            err = 0.0;
+        }
+        if (bad || err > 1.0) {
+            info->rejected++;
+            nrej++;
+            double f = bad ? 0.25 : 0.9 * pow(err, -1.0 / (qe + 1));
+            if (!bad) { if (f > 0.9) f = 0.9; if (f < 0.2) f = 0.2; }
+            h *= f;
+            if (nrej >= 2 && q > 1) { q--; nq = 0; }
+            if (h < pol->dt_min) { rc = -2; break; }
+            continue;
+        }
+        /* accepted */
+        double relc = 0.0;
+        for (int k = 0; k < L; ++k)
+            for (int s = 0; s < S; ++s) {
+                size_t i = (size_t)k * S + s;
+                if (ynew[i] > pol->f_floor * ngas[k]) {
+                    double v = fabs(ynew[i] - Y[i]) / ynew[i];
+                    if (v > relc) relc = v;
+                }
+            }
+        /* order choice (needs the old history for the other predictors) */
+        double eta = pow(err > 1e-10 ? err : 1e-10, -1.0 / (qe + 1)) / 1.2;
+        int qnew = q;
+        nq++;
+        if (!cfg->fixed_order && nq >= qe + 1) {
+            if (qe > 1) {
+                ora_bdf_extrap(qe, th, t + h, w);
+                for (size_t i = 0; i < LS; ++i) {
+                    double v = 0.0;
+                    for (int j = 0; j < qe; ++j) v += w[j] * Y[(size_t)j * LS + i];
+                    yalt[i] = v;
+                }
+                double e1 = bdf_err(p, ngas, pol->f_floor, ynew, yalt, (double)qe, cfg->rtol);
+                double eta1 = pow(e1 > 1e-10 ? e1 : 1e-10, -1.0 / qe) / 1.3;
+                if (eta1 > eta) { eta = eta1; qnew = qe - 1; }
+            }
+            if (qe < qmax && hist >= qe + 2) {
+                ora_bdf_extrap(qe + 2, th, t + h, w);
+                for (size_t i = 0; i < LS; ++i) {
+                    double v = 0.0;
+                    for (int j = 0; j < qe + 2; ++j) v += w[j] * Y[(size_t)j * LS + i];
+                    yalt[i] = v;
+                }
+                double e2 = bdf_err(p, ngas, pol->f_floor, ynew, yalt, qe + 2.0, cfg->rtol);
+                double eta2 = pow(e2 > 1e-10 ? e2 : 1e-10, -1.0 / (qe + 2)) / 1.4;
+                if (eta2 > eta) { eta = eta2; qnew = qe + 1; }
+            }
+            if (qnew != q) nq = 0;
+        }
+        if (cfg->fixed_order > 0) qnew = cfg->fixed_order > qmax ? qmax : cfg->fixed_order;
+        /* push the state (negatives clipped) */
+        for (int j = HMAX - 1; j > 0; --j) {
+            memcpy(Y + (size_t)j * LS, Y + (size_t)(j - 1) * LS, sizeof(double) * LS);
+            th[j] = th[j - 1];
+        }
+        for (size_t i = 0; i < LS; ++i) Y[i] = ynew[i] < 0.0 ? 0.0 : ynew[i];
+        th[0] = t + h;
+        if (hist < HMAX) hist++;
+        info->accepted++;
+        info->order_steps[qe]++;
+        nrej = 0;
+        double hused = h;
+        t += h;
+        q = qnew;
+        if (!cfg->fixed_step) {
+            if (eta < 0.2) eta = 0.2;
+            if (eta > cfg->grow) eta = cfg->grow;
+            h *= eta;
+            if (h > pol->dt_max) h = pol->dt_max;
+        }
+        info->max_rel = relc;
+        if (stop_at_steady && hused >= pol->ss_dt && relc < pol->ss_tol) { info->converged = 1; rc = 0; break; }
+        if (t >= t_end * (1.0 - 1e-12)) { rc = 0; break; }
+        if (h > t_end - t) h = t_end - t;
+    }
+    info->t = t;
+    info->h = h;
+    info->q = q;
+    memcpy(n, Y, sizeof(double) * LS);
+    free(Y); free(yhat); free(kf); free(kph); free(F); free(A); free(ngas);
+    return rc;
+}

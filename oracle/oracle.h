@@ -147,6 +147,32 @@ void ora_fluxes(const ora_problem *p, const double *kf, const double *kr, const 
 void ora_pathways(const ora_problem *p, const double *q, int src, double *dist, int *pred_sp,
                   int *pred_edge, int *lim_edge, double *lim_w);
 
+/* Variable-order, variable-step BDF (the integrator family of the paper's DLSODES, Sec. 2.1),
+ * linearly implicit: one Newton iteration per step on the block-tridiagonal system.
+ * ora_bdf_coeffs: c[0..q] with y'(tau_0) ~ sum_j c_j y(tau_j) on nodes tau_0 > tau_1 > ... > tau_q
+ * (derivatives of the Lagrange basis at tau_0); ora_bdf_extrap: w[0..m-1] with
+ * y(t) ~ sum_j w_j y(tau_j) over m nodes (the degree m-1 interpolant at t). */
+void ora_bdf_coeffs(int q, const double *tau, double *c);
+void ora_bdf_extrap(int m, const double *tau, double t, double *w);
+typedef struct {
+    double rtol;        /* local error target, relative, on species above f_floor mixing ratio */
+    int qmax;           /* largest order (1..5) */
+    int fixed_order;    /* > 0: no order selection, this order once enough history exists */
+    int fixed_step;     /* 1: every step h0 (no error control; for order-of-accuracy checks) */
+    double grow;        /* largest step growth factor per step */
+} ora_bdf_config;
+typedef struct {
+    int steps, accepted, rejected, converged;
+    int order_steps[6]; /* accepted steps per order */
+    double t, h, max_rel;
+    int q;
+} ora_bdf_info;
+/* Integrates n from t = 0 to t_end (or to steady state when stop_at_steady), starting with step h0
+ * at order 1; n is updated.  Returns 0 (reached t_end or steady state), 1 (max_steps), -1 (a
+ * singular system), -2 (step below pol->dt_min). */
+int ora_bdf_run(const ora_problem *p, const ora_policy *pol, const ora_bdf_config *cfg, double *n,
+                double h0, double t_end, int stop_at_steady, int max_steps, ora_bdf_info *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,17 @@ class ParcelInfo(C.Structure):
     _fields_ = [("h", C.c_double), ("steps", C.c_int), ("rejected", C.c_int), ("max_change", C.c_double)]
 
 
+class BdfConfig(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("qmax", C.c_int), ("fixed_order", C.c_int), ("fixed_step", C.c_int),
+                ("grow", C.c_double)]
+
+
+class BdfInfo(C.Structure):
+    _fields_ = [("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int), ("converged", C.c_int),
+                ("order_steps", C.c_int * 6), ("t", C.c_double), ("h", C.c_double), ("max_rel", C.c_double),
+                ("q", C.c_int)]
+
+
 def default_policy(**kw):
     """The step-control policy shared (by value, not by code) with the CUDA path."""
     vals = dict(dt_max=1e8, rel_reject=1.0, rel_target=0.5, grow_max=3.0, shrink_min=0.5,
@@ -105,6 +116,13 @@ def lib():
         l.ora_parcel_run.argtypes = [P, C.POINTER(Policy), C.c_int, C.c_int, C.c_double, _dp,
                                      C.POINTER(ParcelInfo), _ip]
         l.ora_parcel_run.restype = C.c_int
+        l.ora_bdf_coeffs.argtypes = [C.c_int, _dp, _dp]
+        l.ora_bdf_coeffs.restype = None
+        l.ora_bdf_extrap.argtypes = [C.c_int, _dp, C.c_double, _dp]
+        l.ora_bdf_extrap.restype = None
+        l.ora_bdf_run.argtypes = [P, C.POINTER(Policy), C.POINTER(BdfConfig), _dp, C.c_double, C.c_double, C.c_int,
+                                  C.c_int, C.POINTER(BdfInfo)]
+        l.ora_bdf_run.restype = C.c_int
         l.ora_two_stream.argtypes = [C.c_int, _dp, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
         l.ora_two_stream.restype = C.c_int
         l.ora_equilibrium.argtypes = [P, _dp, _dp, C.c_int, C.c_double, _ip]
@@ -323,6 +341,35 @@ class Oracle:
         lib().ora_pathways(C.byref(self.st), _d(np.ascontiguousarray(q_layer, np.float64)), int(src), _d(dist),
                            _i(pred_sp), _i(pred_edge), _i(lim_edge), _d(lim_w))
         return dict(dist=dist, pred_sp=pred_sp, pred_edge=pred_edge, lim_edge=lim_edge, lim_w=lim_w)
+
+    # -- variable-order BDF (the DLSODES family, Sec. 2.1) -----------------------------
+    def bdf_run(self, n, h0=1e-8, t_end=1e30, stop_at_steady=False, max_steps=1000, rtol=1e-3, qmax=5,
+                fixed_order=0, fixed_step=0, grow=5.0, policy=None):
+        """Integrates from n (not modified); returns (state, BdfInfo, return code)."""
+        pol = policy or default_policy()
+        m = np.array(n, np.float64, order="C", copy=True)
+        cfg = BdfConfig(rtol=float(rtol), qmax=int(qmax), fixed_order=int(fixed_order), fixed_step=int(fixed_step),
+                        grow=float(grow))
+        info = BdfInfo()
+        rc = lib().ora_bdf_run(C.byref(self.st), C.byref(pol), C.byref(cfg), _d(m), float(h0), float(t_end),
+                               int(bool(stop_at_steady)), int(max_steps), C.byref(info))
+        return m, info, rc
+
+
+def bdf_coeffs(tau):
+    """Derivative weights c_j at tau[0] of the Lagrange basis on the nodes tau (q = len(tau) - 1)."""
+    t = np.ascontiguousarray(tau, np.float64)
+    c = np.zeros(len(t))
+    lib().ora_bdf_coeffs(len(t) - 1, _d(t), _d(c))
+    return c
+
+
+def bdf_extrap(tau, t):
+    """Weights of the interpolant through the nodes tau evaluated at t."""
+    tt = np.ascontiguousarray(tau, np.float64)
+    w = np.zeros(len(tt))
+    lib().ora_bdf_extrap(len(tt), _d(tt), float(t), _d(w))
+    return w
 
 
 def two_stream(dtau_a, dtau_s, F0, mu, albedo):

@@ -354,7 +354,8 @@ def _stellar_photon_flux(lam_A, Tstar=5000.0, rstar=0.8 * _RSUN, a=0.03 * _AU):
     of stellar spectra described with the actinic flux)."""
     lam = lam_A * 1e-8
     x = _H * _C / (lam * _KB * Tstar)
-    B = 2.0 * _H * _C ** 2 / lam ** 5 / np.expm1(x)              # erg s^-1 cm^-2 cm^-1 sr^-1
+    with np.errstate(over="ignore"):                               # far-UV bins of a cool star: B -> 0
+        B = 2.0 * _H * _C ** 2 / lam ** 5 / np.expm1(x)          # erg s^-1 cm^-2 cm^-1 sr^-1
     photons = np.pi * B / (_H * _C / lam) * 1e-8                   # per Angstrom
     return photons * (rstar / a) ** 2
 
