@@ -325,6 +325,47 @@ XK_API int xk_reaction_fluxes(xk_ctx *ctx, const double *n, double *q);
 XK_API int xk_pathways(xk_ctx *ctx, const double *q, int nsrc, const int *src, double *dist, int *pred_sp,
                        int *pred_edge, int *lim_edge, double *lim_w);
 
+/* ---- variable-order BDF integrator (the DLSODES family of Sec. 2.1) ----
+ * The paper integrates its stiff system with DLSODES, a variable-order, variable-step backward
+ * differentiation method.  xk_bdf_run advances the context's state with BDF orders 1..qmax on the
+ * same block-tridiagonal system as xk_step, linearly implicit (one Newton iteration per step):
+ * order q asks that the polynomial through the new state at t + h and the last q accepted states
+ * have the derivative F at t + h, c_0 y_new + sum_{j>=1} c_j y_j = F(y_new) with c_j the derivatives
+ * of the Lagrange basis at t + h (variable steps), and linearises F about the predictor y_hat (the
+ * polynomial through the last q + 1 states at t + h):
+ *     (c_0 I - J(y_hat)) delta = F(y_hat) - c_0 y_hat - sum_{j>=1} c_j y_j,   y_new = y_hat + delta,
+ * solved with the context's precision mode (order 1 from a constant predictor is the backward-Euler
+ * step).  Local error (y_new - y_hat) / (q + 1), relative to y_new on species above f_floor mixing
+ * ratio, in units of rtol; a step with error > 1, a non-finite state or a state below -neg_tol n_gas
+ * is redone with h * max(0.2, min(0.9, 0.9 err^{-1/(q+1)})) (h / 4 for a bad state), and after two
+ * rejections in a row the order drops by one.  Accepted states are clipped at zero.  After q + 1
+ * steps at an order the next order is the one of q - 1, q, q + 1 whose estimate allows the largest
+ * step (factors err^{-1/(order+1)} divided by 1.3, 1.2, 1.4); the step grows by at most `grow`
+ * per step, never beyond dt_max or t_end.  Starts at order 1 with step h0 at t = 0 and stops at
+ * t_end, or at steady state (an accepted step of h >= ss_dt with max relative change < ss_tol) when
+ * stop_at_steady.  fixed_order > 0 pins the order (once the history allows it); fixed_step = 1 takes
+ * every step h0 without error control.  The state is the last accepted one on return.
+ * Returns XK_OK, XK_ENOCONV (max_steps attempts), XK_ENEG (step below dt_min, or a bad state at a
+ * fixed step), XK_ESINGULAR, XK_ETIMEOUT, XK_EINVAL (rtol <= 0, qmax outside 1..5, grow < 1, h0,
+ * t_end or max_steps not positive).  Synchronizes the stream after every step. */
+typedef struct {
+    double rtol;          /* local error target (relative) */
+    int qmax;             /* largest order, 1..5 */
+    int fixed_order;      /* > 0: no order selection */
+    int fixed_step;       /* 1: constant step h0, no error control */
+    double grow;          /* largest step growth per step (>= 1) */
+} xk_bdf_config;
+typedef struct {
+    long long steps, accepted, rejected;
+    int converged;
+    long long order_steps[6];   /* accepted steps per order */
+    double t, h, max_rel;       /* time reached, next step, last max relative change */
+    int q;                      /* next order */
+    long long solver_iters;     /* FGMRES iterations (mixed) or refinement iterations (FP64) */
+} xk_bdf_info;
+XK_API int xk_bdf_run(xk_ctx *ctx, const xk_bdf_config *cfg, double h0, double t_end, int stop_at_steady,
+                      int max_steps, xk_bdf_info *info);
+
 /* ---- Lagrangian parcel scheme (Sec. 2, Fig. 1 and Fig. 2) ----
  * The paper's own driver.  One global iteration carries an air parcel from the
  * bottom layer to the top and back (layers 0 .. L-1, then L-2 .. 0).  In layer

@@ -1384,6 +1384,7 @@ int ora_bdf_run(const ora_problem *p, const ora_policy *pol, const ora_bdf_confi
                 if (!isfinite(ynew[i]) || ynew[i] < -pol->neg_tol * ngas[k]) bad = 1;
             }
         double err = bad ? INFINITY : bdf_err(p, ngas, pol->f_floor, ynew, yhat, qe + 1.0, cfg->rtol);
+        info->err = err;
         if (cfg->fixed_step) {
             if (bad) { rc = -2; break; }
             err = 0.0;

@@ -166,6 +166,7 @@ typedef struct {
     int order_steps[6]; /* accepted steps per order */
     double t, h, max_rel;
     int q;
+    double err;         /* local-error estimate of the last attempt, in units of rtol */
 } ora_bdf_info;
 /* Integrates n from t = 0 to t_end (or to steady state when stop_at_steady), starting with step h0
  * at order 1; n is updated.  Returns 0 (reached t_end or steady state), 1 (max_steps), -1 (a

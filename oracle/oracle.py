@@ -60,7 +60,7 @@ class BdfConfig(C.Structure):
 class BdfInfo(C.Structure):
     _fields_ = [("steps", C.c_int), ("accepted", C.c_int), ("rejected", C.c_int), ("converged", C.c_int),
                 ("order_steps", C.c_int * 6), ("t", C.c_double), ("h", C.c_double), ("max_rel", C.c_double),
-                ("q", C.c_int)]
+                ("q", C.c_int), ("err", C.c_double)]
 
 
 def default_policy(**kw):

@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libxk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
-SOURCES = ["xk_api.cu", "xk_chem.cu", "xk_factor.cu", "xk_gmres.cu", "xk_noalloc.cu", "xk_cluster.cu", "xk_tc.cu", "xk_bcr.cu", "xk_parcel.cu", "xk_analysis.cu"]
+SOURCES = ["xk_api.cu", "xk_chem.cu", "xk_factor.cu", "xk_gmres.cu", "xk_noalloc.cu", "xk_cluster.cu", "xk_tc.cu", "xk_bcr.cu", "xk_parcel.cu", "xk_analysis.cu", "xk_bdf.cu"]
 
 
 def nvcc():

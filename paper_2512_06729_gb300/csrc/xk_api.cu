@@ -85,6 +85,9 @@ struct xk_ctx {
     EqIndex eqix{};
     int *eq_iters = nullptr, *eq_status = nullptr, *path_src = nullptr;
     double *path_w = nullptr;   // [L][R][2] edge weights of the pathway search
+    // variable-order BDF: history buffers [kBdfHist][L][S], predictor, history terms, new state, step
+    double *bdfY = nullptr, *bdf_yhat = nullptr, *bdf_g = nullptr, *bdf_ynew = nullptr, *bdf_delta = nullptr;
+    BdfResult *bdf_res = nullptr;
     // Lagrangian parcel scheme: its buffers in the workspace (ParcelArgs without the policy)
     ParcelArgs parcel{};
     double *parcel_kzz0 = nullptr;   // [L] zero eddy profile: the molecular part of u, v
@@ -471,6 +474,12 @@ size_t layout(xk_ctx *c, char *base)
     c->eq_status = b.take<int>(L);
     c->path_src = b.take<int>(std::max(S, 1));
     c->path_w = b.take<double>(std::max<size_t>(1, 2 * LR));
+    c->bdfY = b.take<double>(kBdfHist * LS);
+    c->bdf_yhat = b.take<double>(LS);
+    c->bdf_g = b.take<double>(LS);
+    c->bdf_ynew = b.take<double>(LS);
+    c->bdf_delta = b.take<double>(LS);
+    c->bdf_res = b.take<BdfResult>(1);
     EqIndex &ei = c->eqix;
     ei.sp = b.take<int>(S + 1);
     ei.se = b.take<int>(std::max<size_t>(1, c->eq_se.size()));
@@ -1869,6 +1878,212 @@ int xk_pathways(xk_ctx *c, const double *q, int nsrc, const int *src, double *di
                                     lim_edge, lim_w, c->st);
     if (e != cudaSuccess) return fail(c, XK_EINVAL, "pathways launch: %s", cudaGetErrorString(e));
     return finish_eval(c, "pathways");
+}
+
+// ---------------------------------------------------------------- variable-order BDF
+
+namespace {
+
+// Derivative weights at tau[0] of the Lagrange basis on nodes tau[0..q] (the corrector), and the
+// weights of the interpolant through m nodes evaluated at t (the predictors).
+void bdf_weights(int q, const double *tau, double *c)
+{
+    double c0 = 0.0;
+    for (int m = 1; m <= q; ++m) c0 += 1.0 / (tau[0] - tau[m]);
+    c[0] = c0;
+    for (int j = 1; j <= q; ++j) {
+        double num = 1.0, den = 1.0;
+        for (int m = 0; m <= q; ++m) {
+            if (m == j) continue;
+            if (m != 0) num *= tau[0] - tau[m];
+            den *= tau[j] - tau[m];
+        }
+        c[j] = num / den;
+    }
+}
+
+void interp_weights(int m, const double *tau, double t, double *w)
+{
+    for (int j = 0; j < m; ++j) {
+        double v = 1.0;
+        for (int i = 0; i < m; ++i)
+            if (i != j) v *= (t - tau[i]) / (tau[j] - tau[i]);
+        w[j] = v;
+    }
+}
+
+BdfCombo make_combo(int m, const int *slot, const double *w)
+{
+    BdfCombo b{};
+    b.m = m;
+    for (int j = 0; j < m; ++j) {
+        b.slot[j] = slot[j];
+        b.w[j] = w[j];
+    }
+    return b;
+}
+
+double from_bits(unsigned long long u)
+{
+    double d;
+    std::memcpy(&d, &u, sizeof d);
+    return d;
+}
+
+}  // namespace
+
+int xk_bdf_run(xk_ctx *c, const xk_bdf_config *cfg, double h0, double t_end, int stop_at_steady, int max_steps,
+               xk_bdf_info *info)
+{
+    int rc = need_ready(c);
+    if (rc) return rc;
+    if (!cfg || !info || !(cfg->rtol > 0.0) || cfg->qmax < 1 || cfg->qmax > 5 || !(h0 > 0.0) || !(t_end > 0.0) ||
+        max_steps <= 0 || !(cfg->grow >= 1.0))
+        return fail(c, XK_EINVAL, "bdf: bad arguments");
+    ensure_rates(c);
+    const long long N = (long long)c->L * c->S;
+    const int HMAX = cfg->qmax + 2, qmax = cfg->qmax;
+    const Policy pol = policy_of(c->cfg);
+    int slot[kBdfHist];
+    for (int j = 0; j < kBdfHist; ++j) slot[j] = j;
+    double th[kBdfHist] = {0.0};
+    cudaMemcpyAsync(c->bdfY + (size_t)slot[0] * N, c->col.n, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st);
+    std::memset(info, 0, sizeof *info);
+    int hist = 1, q = 1, nq = 0, nrej = 0;
+    double t = 0.0, h = std::min(h0, t_end);
+    const double dto_fp64 = c->cfg.precision == XK_PREC_FP64;
+    int status = XK_ENOCONV;
+    while (info->steps < max_steps) {
+        info->steps++;
+        const int qe = std::min(q, hist);
+        double tau[kBdfHist], cc[kBdfHist], w[kBdfHist], w1[kBdfHist], w2[kBdfHist];
+        tau[0] = t + h;
+        for (int j = 1; j <= qe; ++j) tau[j] = th[j - 1];
+        bdf_weights(qe, tau, cc);
+        const int m = std::min(qe + 1, hist);
+        interp_weights(m, th, t + h, w);
+        BdfStepArgs a{};
+        a.pred = make_combo(m, slot, w);
+        a.hist = make_combo(qe, slot, cc + 1);
+        a.c0 = cc[0];
+        const bool sel = !cfg->fixed_order && nq + 1 >= qe + 1;
+        if (sel && qe > 1) {
+            interp_weights(qe, th, t + h, w1);
+            a.lo = make_combo(qe, slot, w1);
+        }
+        if (sel && qe < qmax && hist >= qe + 2) {
+            interp_weights(qe + 2, th, t + h, w2);
+            a.hi = make_combo(qe + 2, slot, w2);
+        }
+        a.K = qe + 1.0;
+        a.Klo = qe;
+        a.Khi = qe + 2.0;
+        a.rtol = cfg->rtol;
+        a.neg_tol = pol.neg_tol;
+        a.f_floor = pol.f_floor;
+        a.newest = slot[0];
+        launch_bdf_predict(N, c->bdfY, a, c->bdf_yhat, c->bdf_g, c->st);
+        // the backward-Euler system with dt = 1/c0 and the history terms off the right-hand side
+        Ctl init = fresh_ctl(c);
+        init.dt = 1.0 / cc[0];
+        init.dt_fp64 = 1e300;
+        *c->ctl_host = init;
+        cudaMemcpyAsync(c->ctl_aux, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st);
+        c->col.fshift = c->bdf_g;
+        rc = enqueue_linear_step(c, c->bdf_yhat, dto_fp64 ? 1.0 / cc[0] : 0.0, c->bdf_delta, c->ctl_aux);
+        c->col.fshift = nullptr;
+        if (rc) return rc;
+        cudaMemsetAsync(c->bdf_res, 0, sizeof(BdfResult), c->st);
+        launch_bdf_check(c->col, c->bdfY, a, c->bdf_yhat, c->bdf_delta, c->bdf_ynew, c->bdf_res, c->st);
+        BdfResult res{};
+        cudaMemcpyAsync(c->ctl_host, c->ctl_aux, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st);
+        cudaMemcpyAsync(&res, c->bdf_res, sizeof res, cudaMemcpyDeviceToHost, c->st);
+        if ((rc = finish_eval(c, "bdf step"))) return rc;
+        if (c->ctl_host->err_timeout) return timed_out(c);
+        if (c->ctl_host->err_singular) return fail(c, XK_ESINGULAR, "bdf: zero pivot in a diagonal block");
+        info->solver_iters += std::max(c->ctl_host->solver_iters, 0);
+        const bool bad = res.bad != 0;
+        double err = bad ? INFINITY : from_bits(res.err);
+        if (cfg->fixed_step) {
+            if (bad) return fail(c, XK_ENEG, "bdf: non-finite or negative state at a fixed step");
+            err = 0.0;
+        }
+        if (bad || err > 1.0) {
+            info->rejected++;
+            nrej++;
+            double f = bad ? 0.25 : 0.9 * std::pow(err, -1.0 / (qe + 1));
+            if (!bad) f = std::min(0.9, std::max(0.2, f));
+            h *= f;
+            if (nrej >= 2 && q > 1) {
+                q--;
+                nq = 0;
+            }
+            if (h < pol.dt_min) return fail(c, XK_ENEG, "bdf: step %.3g below dt_min", h);
+            continue;
+        }
+        const double relc = from_bits(res.relc);
+        double eta = std::pow(std::max(err, 1e-10), -1.0 / (qe + 1)) / 1.2;
+        int qnew = q;
+        nq++;
+        if (!cfg->fixed_order && nq >= qe + 1) {
+            if (qe > 1) {
+                const double e1 = from_bits(res.err_lo);
+                const double eta1 = std::pow(std::max(e1, 1e-10), -1.0 / qe) / 1.3;
+                if (eta1 > eta) {
+                    eta = eta1;
+                    qnew = qe - 1;
+                }
+            }
+            if (qe < qmax && hist >= qe + 2) {
+                const double e2 = from_bits(res.err_hi);
+                const double eta2 = std::pow(std::max(e2, 1e-10), -1.0 / (qe + 2)) / 1.4;
+                if (eta2 > eta) {
+                    eta = eta2;
+                    qnew = qe + 1;
+                }
+            }
+            if (qnew != q) nq = 0;
+        }
+        if (cfg->fixed_order > 0) qnew = std::min(cfg->fixed_order, qmax);
+        // push: the oldest buffer takes the new state
+        const int nb = slot[HMAX - 1];
+        for (int j = HMAX - 1; j > 0; --j) {
+            slot[j] = slot[j - 1];
+            th[j] = th[j - 1];
+        }
+        slot[0] = nb;
+        th[0] = t + h;
+        launch_bdf_accept(N, c->bdf_ynew, c->bdfY + (size_t)nb * N, c->col.n, c->st);
+        if (hist < HMAX) hist++;
+        info->accepted++;
+        info->order_steps[qe]++;
+        nrej = 0;
+        const double hused = h;
+        t += h;
+        q = qnew;
+        if (!cfg->fixed_step) {
+            eta = std::min(cfg->grow, std::max(0.2, eta));
+            h *= eta;
+            h = std::min(h, pol.dt_max);
+        }
+        info->max_rel = relc;
+        if (stop_at_steady && hused >= pol.ss_dt && relc < pol.ss_tol) {
+            info->converged = 1;
+            status = XK_OK;
+            break;
+        }
+        if (t >= t_end * (1.0 - 1e-12)) {
+            status = XK_OK;
+            break;
+        }
+        h = std::min(h, t_end - t);
+    }
+    info->t = t;
+    info->h = h;
+    info->q = q;
+    if ((rc = finish_eval(c, "bdf run"))) return rc;
+    if (status != XK_OK) return fail(c, XK_ENOCONV, "bdf: %d attempts without reaching the end", max_steps);
+    return XK_OK;
 }
 
 // ---------------------------------------------------------------- Lagrangian parcel scheme

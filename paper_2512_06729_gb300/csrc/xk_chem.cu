@@ -300,6 +300,7 @@ __global__ void k_residual(Col c, const double *n, double *F, const Ctl *ctl, do
     if (k + 1 < L) upf = c.u[(long long)k * S + y] * nk - c.v[(long long)k * S + y] * n[idx + S];
     if (k > 0) dnf = c.u[(long long)(k - 1) * S + y] * n[idx - S] - c.v[(long long)(k - 1) * S + y] * nk;
     f += -(upf - dnf) / c.dz[k];
+    if (c.fshift) f -= c.fshift[idx];
     F[idx] = f;
     if (c.s) {
         double sc = fmax(nk, f_floor * c.ngas[k]);

@@ -57,6 +57,7 @@ struct Col {
     // per step
     double *grt, *lnkc, *kf, *kr, *kph, *alpha, *Jw, *w, *d;
     double *dw;           // [L][R] directional derivative of each rate along a vector (J v)
+    const double *fshift; // [L][S] subtracted from the residual when set (the BDF step's history terms)
     double *n, *F, *s, *b, *x, *delta, *tmp;
 };
 
@@ -182,6 +183,35 @@ void launch_fluxes(const Col &c, const double *n, double *q, cudaStream_t st);
 cudaError_t launch_pathways(const Col &c, const PathGraph &g, const double *q, double *wbuf, int nsrc,
                             const int *src, double *dist, int *pred_sp, int *pred_edge, int *lim_edge,
                             double *lim_w, cudaStream_t st);
+
+// Variable-order BDF (xk_bdf.cu): the history's linear combinations for one step attempt.
+constexpr int kBdfHist = 7;      // states kept: order 5 plus the two needed by the order-6 predictor
+struct BdfCombo {
+    int m;                       // terms
+    int slot[kBdfHist];          // history buffer of each term
+    double w[kBdfHist];
+};
+struct BdfStepArgs {
+    BdfCombo pred;               // predictor y_hat at t + h
+    BdfCombo hist;               // sum_{j>=1} c_j y_j of the corrector
+    double c0;
+    BdfCombo lo, hi;             // predictors of one degree lower / higher (m = 0: not needed)
+    double K, Klo, Khi;          // error constants q + 1, q, q + 2
+    double rtol, neg_tol, f_floor;
+    int newest;                  // buffer of y_n
+};
+struct BdfResult {
+    unsigned long long err, err_lo, err_hi, relc;   // bit patterns of non-negative maxima
+    int bad;
+};
+// y_hat and g = c0 y_hat + sum_{j>=1} c_j y_j (Y: kBdfHist buffers of L*S)
+void launch_bdf_predict(long long N, const double *Y, const BdfStepArgs &a, double *yhat, double *g,
+                        cudaStream_t st);
+// y_new = y_hat + delta, its checks and error estimates into *res (cleared by the caller)
+void launch_bdf_check(const Col &c, const double *Y, const BdfStepArgs &a, const double *yhat, const double *delta,
+                      double *ynew, BdfResult *res, cudaStream_t st);
+// accepted: Y[slot] = max(y_new, 0) and the state n = the same
+void launch_bdf_accept(long long N, const double *ynew, double *Yslot, double *n, cudaStream_t st);
 
 // Lagrangian parcel scheme (Sec. 2, Fig. 2): buffers and state of one global iteration.
 struct ParcelState {

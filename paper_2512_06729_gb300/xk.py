@@ -61,6 +61,17 @@ class EquilibriumInfo(C.Structure):
     _fields_ = [("iters_max", C.c_int), ("layers_not_converged", C.c_int), ("layers_singular", C.c_int)]
 
 
+class BdfConfig(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("qmax", C.c_int), ("fixed_order", C.c_int), ("fixed_step", C.c_int),
+                ("grow", C.c_double)]
+
+
+class BdfInfo(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("accepted", C.c_longlong), ("rejected", C.c_longlong),
+                ("converged", C.c_int), ("order_steps", C.c_longlong * 6), ("t", C.c_double), ("h", C.c_double),
+                ("max_rel", C.c_double), ("q", C.c_int), ("solver_iters", C.c_longlong)]
+
+
 class XkError(RuntimeError):
     def __init__(self, where, code, msg):
         super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
@@ -121,6 +132,8 @@ SIGNATURES = {
     "xk_factor_work": (C.c_int, [_vp, _dp, _dp]),
     "xk_equilibrium": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_double, C.POINTER(EquilibriumInfo)]),
     "xk_reaction_fluxes": (C.c_int, [_vp, _vp, _vp]),
+    "xk_bdf_run": (C.c_int, [_vp, C.POINTER(BdfConfig), C.c_double, C.c_double, C.c_int, C.c_int,
+                             C.POINTER(BdfInfo)]),
     "xk_pathways": (C.c_int, [_vp, _vp, C.c_int, _ip, _vp, _vp, _vp, _vp, _vp]),
 }
 
@@ -375,6 +388,20 @@ class Column:
         lo, up = self._dev(self.L, self.S), self._dev(self.L, self.S)
         self._call("xk_eval_jacobian", self._ptr(n.contiguous()), float(dt), self._ptr(A), self._ptr(lo), self._ptr(up))
         return A, lo, up
+
+    # -- variable-order BDF (the DLSODES family, Sec. 2.1) ----------------------------
+    def bdf_run(self, h0=1e-8, t_end=1e30, stop_at_steady=False, max_steps=1000, rtol=1e-3, qmax=5,
+                fixed_order=0, fixed_step=0, grow=5.0, raise_on_noconv=False):
+        """Advances the state with xk_bdf_run; returns (BdfInfo, return code)."""
+        cfg = BdfConfig(rtol=float(rtol), qmax=int(qmax), fixed_order=int(fixed_order),
+                        fixed_step=int(fixed_step), grow=float(grow))
+        info = BdfInfo()
+        rc = lib().xk_bdf_run(self.h, C.byref(cfg), float(h0), float(t_end), int(bool(stop_at_steady)),
+                              int(max_steps), C.byref(info))
+        if rc != XK_OK and (raise_on_noconv or rc != -3):
+            msg = lib().xk_last_error(self.h)
+            raise XkError("xk_bdf_run", rc, msg.decode() if msg else "")
+        return info, rc
 
     # -- equilibrium initial state (Sec. 2.5) and pathway analyser (Sec. 4) --------
     def equilibrium(self, b=None, set_state=False, max_iter=300, tol=1e-12):

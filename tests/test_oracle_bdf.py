@@ -114,6 +114,30 @@ def test_error_falls_with_the_tolerance():
     assert errs[-1] < errs[0] / 1000
 
 
+def test_local_error_estimate_of_order_one():
+    """At order 1 with a linear predictor the estimate (y_new - y_hat) / 2 is the step's true local
+    error h^2 y''/2 (A <-> B: exact solution from the previous accepted state)."""
+    p = _ab_problem()
+    o = Oracle(p)
+    kf, kr = (x[0, 0] for x in o.rate_coefficients())
+    n0 = o.initial_state()
+    ntot = n0.sum()
+    neq = ntot * kr / (kf + kr)
+    ratios = []
+    prev = None
+    for N in range(1, 40):
+        m, info, rc = o.bdf_run(n0, h0=1e-2, t_end=1e5, max_steps=N, rtol=1e-4, fixed_order=1)
+        if prev is not None and info.accepted == prev[1].accepted + 1 and N > 5:
+            h = info.t - prev[1].t
+            xa = neq + (prev[0][0, 0] - neq) * np.exp(-(kf + kr) * h)
+            exact = np.array([xa, ntot - xa])
+            true = np.max(np.abs(m[0] - exact) / m[0])
+            ratios.append(info.err * 1e-4 / true)
+        prev = (m, info)
+    assert len(ratios) > 10
+    assert 0.7 < np.median(ratios) < 1.4, ratios
+
+
 def test_fixed_order_converges_at_its_order():
     """Fixed steps at order 1 and 2 (order 2 starts with one backward-Euler step, itself of local
     order 2): halving h divides the error at T by about 2^q."""
