@@ -525,7 +525,7 @@ def run_ours(args):
             errs = err_vs_oracle(prob, tuning)
         if not args.no_steady:
             steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
-    batch = serving_obj = parcel = analysis = radiation = None
+    batch = serving_obj = parcel = analysis = radiation = bdf = None
     if rank == 0 and ws == 1:
         if not args.no_batch:
             batch = batch_object(args.columns, steps=5, warmup=3, tune=not args.no_tune)
@@ -536,6 +536,7 @@ def run_ours(args):
         if not args.no_analysis:
             analysis = analysis_object(live, cpu=not args.no_cpu)
             radiation = radiation_object(live, cpu=not args.no_cpu)
+            bdf = bdf_object(cpu=not args.no_cpu)
     if rank == 0:
         ph = {k: {"ms_total": v[0], "calls": v[1]} for k, v in mixed["phases"].items() if v[1]}
         ph64 = {k: {"ms_total": v[0], "calls": v[1]} for k, v in fp64["phases"].items() if v[1]}
@@ -571,6 +572,7 @@ def run_ours(args):
             "parcel": parcel,
             "analysis": analysis,
             "radiation": radiation,
+            "bdf": bdf,
             "traced": {"ms_per_step": mixed["ms_traced"] / mixed["steps_traced"],
                        "note": "the next steps with every kernel launched from the host between CUDA event "
                                "pairs (phases_ms comes from this run)"},
@@ -989,6 +991,62 @@ def run_radiation(args):
     return 0
 
 
+def bdf_object(attempts=40, cpu=True):
+    """The variable-order BDF integrator (the DLSODES family of Sec. 2.1) from the initial state:
+    wall time per attempt on the 594-species, 150-layer column (mixed precision; every attempt is
+    one block-tridiagonal solve plus the predictor and error kernels, synchronised with the host
+    controller), the orders it reaches, and on the 96-species column the end state after the same
+    number of attempts against the oracle's BDF."""
+    import numpy as np
+    import torch
+    from paper_2512_06729_gb300 import synth, xk
+    out = {}
+    prob = synth.full_column()
+    col = xk.Column(prob, "mixed")
+    col.set_mixing_ratios(prob.f0)
+    col.bdf_run(h0=1e-8, max_steps=3)                      # warm-up (rates, plans)
+    col.set_mixing_ratios(prob.f0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, rc = col.bdf_run(h0=1e-8, max_steps=attempts, rtol=1e-3)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out["full_mixed"] = {"attempts": int(info.steps), "accepted": int(info.accepted), "rejected": int(info.rejected),
+                         "order_steps": [int(x) for x in info.order_steps], "t_reached_s": info.t,
+                         "ms_per_attempt": 1e3 * wall / max(int(info.steps), 1),
+                         "solver_iters": int(info.solver_iters)}
+    col.close()
+    small = synth.chons_column()
+    c2 = xk.Column(small, "fp64")
+    c2.set_mixing_ratios(small.f0)
+    n0 = c2.get_state()
+    gi, _ = c2.bdf_run(h0=1e-8, max_steps=attempts, rtol=1e-3)
+    res = {"attempts": int(gi.steps), "order_steps": [int(x) for x in gi.order_steps], "t_reached_s": gi.t}
+    if cpu:
+        from oracle.oracle import Oracle
+        o = Oracle(small)
+        t0 = time.perf_counter()
+        ref, ri, _ = o.bdf_run(n0, h0=1e-8, max_steps=attempts, rtol=1e-3)
+        res["cpu_oracle_s"] = time.perf_counter() - t0
+        ngas = o.grid()[0]
+        g = c2.get_state()
+        keep = ref > 1e-20 * ngas[:, None]
+        res["same_steps_as_oracle"] = bool(ri.steps == gi.steps and ri.accepted == gi.accepted
+                                           and list(ri.order_steps) == list(gi.order_steps))
+        res["err_vs_oracle_max_rel"] = float(np.max(np.abs(g[keep] - ref[keep]) / ref[keep]))
+    out["chons_fp64"] = res
+    c2.close()
+    return out
+
+
+def run_bdf(args):
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    out = bdf_object(attempts=max(args.steps, 1), cpu=not args.no_cpu)
+    print(json.dumps({"mode": "bdf", "bdf": out}), flush=True)
+    return 0
+
+
 def run_steady(args):
     """Time to steady state of the 594 x 150 column: mixed path (FP64 factorization reused as the
     FGMRES preconditioner once steps go to FP64) against the plain FP64 path, the two end states
@@ -1116,7 +1174,7 @@ def main():
                     help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis", "radiation"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis", "radiation", "bdf"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
@@ -1147,6 +1205,8 @@ def main():
         return run_analysis(args)
     if args.mode == "radiation":
         return run_radiation(args)
+    if args.mode == "bdf":
+        return run_bdf(args)
     return run_ours(args)
 
 
