@@ -1015,6 +1015,17 @@ def bdf_object(attempts=40, cpu=True):
                          "order_steps": [int(x) for x in info.order_steps], "t_reached_s": info.t,
                          "ms_per_attempt": 1e3 * wall / max(int(info.steps), 1),
                          "solver_iters": int(info.solver_iters)}
+    # the same from the chemical-equilibrium initial state (Sec. 2.5 option (i)) of the same elements
+    col.set_mixing_ratios(prob.f0)
+    col.equilibrium(set_state=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, rc = col.bdf_run(h0=1e-8, max_steps=attempts, rtol=1e-3)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out["full_mixed_from_equilibrium"] = {"attempts": int(info.steps), "accepted": int(info.accepted),
+                                          "order_steps": [int(x) for x in info.order_steps], "t_reached_s": info.t,
+                                          "ms_per_attempt": 1e3 * wall / max(int(info.steps), 1)}
     col.close()
     small = synth.chons_column()
     c2 = xk.Column(small, "fp64")
@@ -1037,6 +1048,17 @@ def bdf_object(attempts=40, cpu=True):
     out["chons_fp64"] = res
     c2.close()
     return out
+
+
+def run_extras(args):
+    """The analysis and radiation objects in one process (the command behind their kernel profiles)."""
+    from paper_2512_06729_gb300 import build as xkbuild
+    xkbuild.build()
+    live = live_peaks()
+    out = {"analysis": analysis_object(live, calls=max(args.steps, 1), cpu=not args.no_cpu),
+           "radiation": radiation_object(live, calls=max(args.steps, 1), cpu=not args.no_cpu)}
+    print(json.dumps({"mode": "extras", **out}), flush=True)
+    return 0
 
 
 def run_bdf(args):
@@ -1174,7 +1196,7 @@ def main():
                     help="seconds each serving run (mixed, then FP64) may take in the default line")
     ap.add_argument("--no-tune", action="store_true",
                     help="library defaults instead of the autotuned factorization (shorter runs for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis", "radiation", "bdf"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serving", "steady", "kernels", "parcel", "analysis", "radiation", "bdf", "extras"],
                     help="step: one 594 x 150 column (the headline); batch: 64 uneven columns; serving: sweep "
                          "requests; steady: time to steady state of the 594 x 150 column")
     ap.add_argument("--max-steps", type=int, default=5000)
@@ -1207,6 +1229,8 @@ def main():
         return run_radiation(args)
     if args.mode == "bdf":
         return run_bdf(args)
+    if args.mode == "extras":
+        return run_extras(args)
     return run_ours(args)
 
 
