@@ -686,7 +686,8 @@ def run_batch(args):
     return 0
 
 
-def serving_object(requests=16, rate=0.25, slots=16, deadline=120.0, precisions=("mixed", "fp64"), seed=0):
+def serving_object(requests=16, rate=0.25, slots=16, deadline=120.0, precisions=("mixed", "fp64"), seed=0,
+                   equilibrium=True):
     """Config-4 serving: Poisson-arriving steady-state requests from the planet-parameter sweep
     (60/30/10 % of 96/250/594 species on 150 layers), admitted by HBM footprint and kept on the
     device, served once by the mixed path and once by the plain FP64 path on the same requests.
@@ -695,13 +696,18 @@ def serving_object(requests=16, rate=0.25, slots=16, deadline=120.0, precisions=
     import torch
     from paper_2512_06729_gb300 import serving
     reqs = serving.sweep_requests(requests, rate, seed=seed)
+    reqs_eq = serving.sweep_requests(requests, rate, seed=seed, initial="equilibrium")
     out = {"requests": requests, "rate_per_s": rate, "slots": slots, "deadline_s": deadline, "layers": 150,
            "species": [r.problem.S for r in reqs]}
-    for prec in precisions:
+    runs = [(prec, prec, reqs) for prec in precisions]
+    if equilibrium and "mixed" in precisions:
+        # the same sweep started from the chemical-equilibrium composition (Sec. 2.5 option (i))
+        runs.append(("mixed_from_equilibrium", "mixed", reqs_eq))
+    for name, prec, rq in runs:
         kw = dict(reuse_factorization=1) if prec == "mixed" else {}
         srv = serving.Server(200 << 30, slots, precision=prec, chunk=8, column_kw=kw)
         t0 = time.perf_counter()
-        res = srv.run(reqs, deadline=deadline)
+        res = srv.run(rq, deadline=deadline)
         wall = time.perf_counter() - t0
         srv.close()
         torch.cuda.empty_cache()
@@ -710,8 +716,8 @@ def serving_object(requests=16, rate=0.25, slots=16, deadline=120.0, precisions=
         summ["unfinished"] = summ["requests"] - summ["finished"]
         summ["per_request"] = [{"S": q.problem.S, "arrival_s": round(x.arrival, 3),
                                 "latency_s": None if x.finished is None else round(x.latency, 3),
-                                "steps": x.steps, "fp64_steps": x.fp64_steps} for q, x in zip(reqs, res)]
-        out[prec] = summ
+                                "steps": x.steps, "fp64_steps": x.fp64_steps} for q, x in zip(rq, res)]
+        out[name] = summ
     if "mixed" in out and "fp64" in out:
         fm, ff = out["mixed"]["solves_per_s"], out["fp64"]["solves_per_s"]
         out["solves_per_s_mixed_over_fp64"] = fm / ff if ff > 0 else None

@@ -23,6 +23,9 @@ class Request:
     arrival: float              # seconds after the start of the run
     problem: synth.Problem
     dt0: float = 1e-8
+    initial: str = "user"       # "user": the problem's mixing ratios; "equilibrium": the chemical-
+                                # equilibrium composition of the same elements (Sec. 2.5 option (i)),
+                                # computed on the device at admission
 
 
 @dataclasses.dataclass
@@ -41,7 +44,7 @@ class Result:
         return self.finished - self.arrival
 
 
-def sweep_requests(n, rate, seed=0, mix=((96, 0.6), (250, 0.3), (594, 0.1)), layers=150):
+def sweep_requests(n, rate, seed=0, mix=((96, 0.6), (250, 0.3), (594, 0.1)), layers=150, initial="user"):
     """Poisson arrivals (rate per second) from a planet-parameter sweep:
     T_eq U[800, 2500] K, metallicity log-U[1, 100] x solar, Kzz scale
     log-U[1e6, 1e11] / 1e8 (the profile's Kzz is 1e7 .. 1e10 cm^2/s), and the
@@ -59,7 +62,7 @@ def sweep_requests(n, rate, seed=0, mix=((96, 0.6), (250, 0.3), (594, 0.1)), lay
         met = 10.0 ** rng.uniform(0.0, 2.0)
         kzz = 10.0 ** rng.uniform(6.0, 11.0) / 1e8
         prob = synth.sweep_column(S, layers, T_eq, met, kzz, seed=1000 + i)
-        out.append(Request(i, t, prob))
+        out.append(Request(i, t, prob, initial=initial))
     return out
 
 
@@ -123,6 +126,8 @@ class Server:
                     break
                 col.allocate()
                 col.set_mixing_ratios(req.problem.f0)
+                if req.initial == "equilibrium":
+                    col.equilibrium(set_state=True)
                 slot = self.batch.add(col, req.dt0)
                 if slot is None:
                     col.close()

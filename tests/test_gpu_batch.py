@@ -26,9 +26,11 @@ def _problems():
             synth.sweep_column(96, 40, 1500.0, 3.0, 0.5, seed=4)]
 
 
-def _alone(p, precision, steps, **kw):
+def _alone(p, precision, steps, initial="user", **kw):
     c = xk.Column(p, precision, **kw)
     c.set_mixing_ratios(p.f0)
+    if initial == "equilibrium":
+        c.equilibrium(set_state=True)
     info = c.run_to_steady(1e-8, steps)
     return c.get_state(), info
 
@@ -101,6 +103,22 @@ def test_serving_results_equal_alone():
         assert r.finished >= r.admitted >= r.arrival - 1e-9
     s = serving.summarize(res, max(r.finished for r in res))
     assert s["requests"] == 4 and s["converged"] == 4 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_serving_from_equilibrium_equals_alone():
+    """Requests that start from the chemical-equilibrium composition (computed at admission on the
+    device) end where the same column started from it alone ends."""
+    reqs = [serving.Request(i, 0.002 * i, p, initial="equilibrium") for i, p in enumerate(_problems()[:3])]
+    srv = serving.Server(64 << 30, 2, precision="fp64", chunk=8, keep_states=True)
+    res = srv.run(reqs)
+    srv.close()
+    for r, q in zip(res, reqs):
+        assert r.converged
+        n_alone, info = _alone(q.problem, "fp64", r.steps, initial="equilibrium")
+        assert info.steps == r.steps
+        ng = n_alone.max(axis=1, keepdims=True)
+        mask = n_alone > 1e-20 * ng
+        assert np.max(np.abs(r.state[mask] - n_alone[mask]) / n_alone[mask]) <= 1e-9
 
 
 def test_batch_submit_query():
