@@ -243,6 +243,40 @@ __global__ void k_photo_J(Col c)
     }
 }
 
+// Direct beam only: one warp per wavelength.  Lane l takes a run of consecutive layers counted
+// from the top, sums their optical thicknesses, and a warp scan gives the optical depth above its
+// run; the lane then walks its run (32x the parallelism of a thread per wavelength, which left
+// 1,000 bins on 8 SMs).
+__global__ void k_photo_J_direct(Col c)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= c.W) return;
+    const int per = (c.L + 31) / 32;
+    const int i0 = lane * per, i1 = min(c.L, i0 + per);   // positions from the top: layer L-1-i
+    double run = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const int k = c.L - 1 - i;
+        const long long idx = (long long)k * c.W + w;
+        run += (c.alpha[idx] + c.alpha_s[idx]) * c.dz[k];
+    }
+    double incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    double above = __shfl_up_sync(0xffffffffu, incl, 1);   // sum over the runs above this one
+    if (lane == 0) above = 0.0;
+    const double J0 = c.J0[w], mu = c.mu;
+    for (int i = i0; i < i1; ++i) {
+        const int k = c.L - 1 - i;
+        const long long idx = (long long)k * c.W + w;
+        const double dt = (c.alpha[idx] + c.alpha_s[idx]) * c.dz[k];
+        c.Jw[idx] = J0 * exp(-(above + 0.5 * dt) / mu);
+        above += dt;
+    }
+}
+
 // k_ph = t_f sum_w J(k, w) sigma(w) dlambda(w); one warp per (layer, reaction), lanes striding
 // the wavelengths (coalesced), partial sums added in lane order
 __global__ void k_photo_k(Col c)
@@ -738,7 +772,9 @@ void launch_photolysis(const Col &c, const double *n, cudaStream_t st)
             dim3 grid(nblocks(c.W, 128), (c.L + kExtLayers - 1) / kExtLayers);
             k_photo_alpha<<<grid, 128, 0, st>>>(c, n);
         }
-        if ((c.W) > 0) { count_launches(1); k_photo_J<<<nblocks(c.W, 128), 128, 0, st>>>(c); }
+        count_launches(1);
+        if (c.diffuse) k_photo_J<<<nblocks(c.W, 128), 128, 0, st>>>(c);
+        else k_photo_J_direct<<<nblocks((long long)c.W * 32, 128), 128, 0, st>>>(c);
     }
     if (((long long)c.L * c.Rph * 32) > 0) { count_launches(1); k_photo_k<<<nblocks((long long)c.L * c.Rph * 32), kThreads, 0, st>>>(c); }
 }
