@@ -773,7 +773,7 @@ void launch_photolysis(const Col &c, const double *n, cudaStream_t st)
             k_photo_alpha<<<grid, 128, 0, st>>>(c, n);
         }
         count_launches(1);
-        if (c.diffuse) k_photo_J<<<nblocks(c.W, 128), 128, 0, st>>>(c);
+        if (c.diffuse) k_photo_J<<<nblocks(c.W, 64), 64, 0, st>>>(c);   // 10,000 bins: 157 CTAs, every SM
         else k_photo_J_direct<<<nblocks((long long)c.W * 32, 128), 128, 0, st>>>(c);
     }
     if (((long long)c.L * c.Rph * 32) > 0) { count_launches(1); k_photo_k<<<nblocks((long long)c.L * c.Rph * 32), kThreads, 0, st>>>(c); }
