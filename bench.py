@@ -316,11 +316,14 @@ def err_vs_oracle(prob, tuning, dt=1e-8):
 
 def steady_runs(prob, tuning, caps):
     """Time to steady state from the initial state (dt0 1e-8 s) for each path, in chunks of 50
-    steps, each path stopped at its time cap (then reported as not converged, with how far it got)."""
+    steps, each path stopped at its time cap (then reported as not converged, with how far it got).
+    A key "<path>_from_equilibrium" starts that path from the chemical-equilibrium composition of
+    the same elements (Sec. 2.5 option (i); computed on the device, its time included)."""
     import torch
     from paper_2512_06729_gb300 import xk
     out = {}
-    for prec, cap in caps.items():
+    for name, cap in caps.items():
+        prec = name.split("_")[0]
         kw = dict(tuning.get(prec, {}))
         if prec == "mixed":
             kw["reuse_factorization"] = 1
@@ -328,6 +331,8 @@ def steady_runs(prob, tuning, caps):
         col.set_mixing_ratios(prob.f0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        if name.endswith("_from_equilibrium"):
+            col.equilibrium(set_state=True)
         steps = fp64_steps = refactors = iters = 0
         t_model = 0.0
         info = None
@@ -342,7 +347,7 @@ def steady_runs(prob, tuning, caps):
                 break
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        out[prec] = {"s": round(wall, 2), "converged": bool(info and info.converged), "steps": steps,
+        out[name] = {"s": round(wall, 2), "converged": bool(info and info.converged), "steps": steps,
                      "steps_per_s": round(steps / wall, 2), "fp64_route_steps": fp64_steps,
                      "fp64_refactors": refactors, "fgmres_iters": iters, "t_model_s": t_model,
                      "dt_last": float(info.dt) if info else None, "time_cap_s": cap}
@@ -524,7 +529,8 @@ def run_ours(args):
                                              f"scaled by {L}/{SAMPLE_LAYERS}"}}
             errs = err_vs_oracle(prob, tuning)
         if not args.no_steady:
-            steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64})
+            steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64,
+                                                "mixed_from_equilibrium": args.steady_cap})
     batch = serving_obj = parcel = analysis = radiation = bdf = None
     if rank == 0 and ws == 1:
         if not args.no_batch:
@@ -1088,7 +1094,8 @@ def run_steady(args):
     stream = torch.cuda.current_stream()
     runs = {}
     extra = json.loads(args.column_kw) if args.column_kw else {}
-    variants = {"mixed": ("mixed", dict(reuse_factorization=1, **extra)), "fp64": ("fp64", {})}
+    variants = {"mixed": ("mixed", dict(reuse_factorization=1, **extra)), "fp64": ("fp64", {}),
+                "mixed_from_equilibrium": ("mixed", dict(reuse_factorization=1, **extra))}
     for name in args.variants.split(","):
         prec, kw = variants[name]
         col = xk.Column(prob, prec, **kw)
@@ -1097,6 +1104,8 @@ def run_steady(args):
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)
         t0 = time.perf_counter()
+        if name.endswith("_from_equilibrium"):
+            col.equilibrium(set_state=True)   # the chemical-equilibrium start (Sec. 2.5 option (i)), timed
         steps = acc = fp64_steps = iters = refactors = 0
         t_model = 0.0
         info = None
