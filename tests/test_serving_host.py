@@ -9,6 +9,7 @@ from paper_2512_06729_gb300 import serving
 
 
 ALLOCATED = []
+STARTS = []
 
 
 class FakeColumn:
@@ -26,7 +27,14 @@ class FakeColumn:
         ALLOCATED.append(self.prob.name)
 
     def set_mixing_ratios(self, f):
-        pass
+        self.start = "user"
+
+    def equilibrium(self, set_state=False):
+        assert self.allocated and self.start == "user"      # after the workspace and the user state
+        if set_state:
+            self.start = "equilibrium"
+        STARTS.append(self.prob.name)
+        return None, None
 
     def get_state(self):
         return np.zeros((1, 1))
@@ -149,3 +157,23 @@ def test_deadline_reports_unfinished(monkeypatch):
     assert res[2].finished is None and res[2].admitted is None         # never admitted
     s = serving.summarize(res, t[0])
     assert s["requests"] == 4 and s["finished"] == 1
+
+
+def test_equilibrium_start_is_set_before_admission(monkeypatch):
+    """A request marked to start from the equilibrium composition gets it on the device after its
+    workspace exists and before the batch admits it; the others keep their mixing ratios."""
+    monkeypatch.setattr(serving.xk, "Column", FakeColumn)
+    monkeypatch.setattr(serving.xk, "Batch", FakeBatch)
+    probs = [types.SimpleNamespace(name=f"r{i}", S=40, f0=None) for i in range(4)]
+    reqs = [serving.Request(i, 0.0, p, initial="equilibrium" if i % 2 else "user") for i, p in enumerate(probs)]
+    t = [0.0]
+
+    def clock():
+        t[0] += 0.001
+        return t[0]
+
+    STARTS.clear()
+    srv = serving.Server(budget_bytes=10 ** 9, max_slots=2, chunk=2)
+    res = srv.run(reqs, clock=clock)
+    assert STARTS == ["r1", "r3"]
+    assert all(r.converged for r in res)
