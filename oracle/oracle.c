@@ -1471,3 +1471,129 @@ int ora_bdf_run(const ora_problem *p, const ora_policy *pol, const ora_bdf_confi
     free(Y); free(yhat); free(kf); free(kph); free(F); free(A); free(ngas);
     return rc;
 }
+
+/* ------------------------------------- photolysis rates in the Jacobian */
+/*
+ * dk_ph / dn of the direct beam (Sec. 2.3.3): k_ph,q,k = t_f sum_w J_kw sigma_qw dlambda_w with
+ * J_kw = J0_w exp(-tau_kw / mu) and tau_kw = sum_{j>k} e_jw dz_j + e_kw dz_k / 2, e_jw =
+ * sum_i (sigma_a,iw + sigma_s,iw) n_ji.  So dk_ph,q,k / dn_ji = -(t_f / mu) sum_w J_kw sigma_qw
+ * dlambda_w (sigma_a,iw + sigma_s,iw) c_kj dz_j, with c_kj = 1 above k, 1/2 at k, 0 below: a
+ * species absorbs for every layer beneath it.  Written out for every (k, q) and (j, i):
+ * dk [(k Rph + q)][(j S + i)].  The diffuse field's derivative is not included.
+ */
+void ora_photolysis_dn(const ora_problem *p, const double *n, double *dk)
+{
+    int L = p->L, S = p->S, W = p->W, Rph = p->Rph;
+    size_t LS = (size_t)L * S;
+    memset(dk, 0, sizeof(double) * (size_t)L * Rph * LS);
+    if (Rph == 0 || W == 0)
+        return;
+    double *ngas = malloc(sizeof(double) * L * 4);
+    double *z = ngas + L, *dz = z + L, *dzi = dz + L;
+    ora_grid(p, ngas, z, dz, dzi);
+    double *J = malloc(sizeof(double) * (size_t)L * W), *ext = malloc(sizeof(double) * L);
+    for (int w = 0; w < W; ++w) {
+        for (int k = 0; k < L; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < S; ++i) {
+                double sg = p->sigma_abs[(size_t)i * W + w] + (p->sigma_s ? p->sigma_s[(size_t)i * W + w] : 0.0);
+                s += sg * n[(size_t)k * S + i];
+            }
+            ext[k] = s;
+        }
+        double above = 0.0;
+        for (int k = L - 1; k >= 0; --k) {
+            double tau = above + 0.5 * ext[k] * dz[k];
+            J[(size_t)k * W + w] = p->J0[w] * exp(-tau / p->mu);
+            above += ext[k] * dz[k];
+        }
+    }
+    for (int k = 0; k < L; ++k)
+        for (int q = 0; q < Rph; ++q) {
+            double *row = dk + ((size_t)k * Rph + q) * LS;
+            for (int j = k; j < L; ++j) {
+                double c = (j == k) ? 0.5 : 1.0;
+                for (int i = 0; i < S; ++i) {
+                    double s = 0.0;
+                    for (int w = 0; w < W; ++w) {
+                        double sg = p->sigma_abs[(size_t)i * W + w] + (p->sigma_s ? p->sigma_s[(size_t)i * W + w] : 0.0);
+                        if (sg == 0.0) continue;
+                        s += J[(size_t)k * W + w] * p->sigma[(size_t)q * W + w] * p->dlam[w] * sg;
+                    }
+                    row[(size_t)j * S + i] = -(p->tf / p->mu) * s * c * dz[j];
+                }
+            }
+        }
+    free(ext);
+    free(J);
+    free(ngas);
+}
+
+/* The linearly implicit step with the photolysis rates differentiated as well: (I/dt - J_full) delta
+ * = F(n), J_full = the block-tridiagonal Jacobian plus, for every photolysis reaction r (A -> ...)
+ * in layer k, nu_yr n_A,k dk_ph,r,k / dn (a coupling to every layer at and above k), solved as one
+ * dense system by Gaussian elimination with partial pivoting and FP64 iterative refinement.
+ * Returns 0, or -1 on a singular matrix. */
+int ora_step_delta_coupled(const ora_problem *p, const double *n, double dt, double *delta)
+{
+    int L = p->L, S = p->S, R = p->R, Rph = p->Rph;
+    size_t LS = (size_t)L * S;
+    double *kf = malloc(sizeof(double) * (size_t)L * R * 2), *kr = kf + (size_t)L * R;
+    double *kph = malloc(sizeof(double) * (size_t)L * (Rph > 0 ? Rph : 1));
+    double *F = malloc(sizeof(double) * LS * 3), *lo = F + LS, *up = lo + LS;
+    double *A = malloc(sizeof(double) * LS * S);
+    double *M = malloc(sizeof(double) * LS * LS), *LU = malloc(sizeof(double) * LS * LS);
+    double *dk = malloc(sizeof(double) * (size_t)L * (Rph > 0 ? Rph : 1) * LS);
+    double *r = malloc(sizeof(double) * LS * 2), *c = r + LS;
+    int *piv = malloc(sizeof(int) * LS);
+    ora_rate_coefficients(p, kf, kr);
+    ora_photolysis(p, n, kph);
+    ora_residual(p, kf, kr, kph, n, F);
+    ora_jacobian(p, kf, kr, kph, n, dt, A, lo, up);
+    ora_photolysis_dn(p, n, dk);
+    memset(M, 0, sizeof(double) * LS * LS);
+    for (int k = 0; k < L; ++k)
+        for (int y = 0; y < S; ++y) {
+            size_t row = (size_t)k * S + y;
+            for (int x = 0; x < S; ++x)
+                M[row * LS + (size_t)k * S + x] = A[((size_t)k * S + y) * S + x];
+            if (k > 0) M[row * LS + (size_t)(k - 1) * S + y] = lo[row];
+            if (k + 1 < L) M[row * LS + (size_t)(k + 1) * S + y] = up[row];
+        }
+    /* minus d(photolysis production - loss)/dn through the rates */
+    for (int rr = 0; rr < R; ++rr) {
+        if (p->rtype[rr] != 2) continue;
+        int q = p->prow[rr], a = p->reac[3 * rr];
+        for (int k = 0; k < L; ++k) {
+            const double *drow = dk + ((size_t)k * Rph + q) * LS;
+            double na = n[(size_t)k * S + a];
+            for (int s = 0; s < 3; ++s) {
+                int yr = p->reac[3 * rr + s], yp = p->prod[3 * rr + s];
+                for (size_t col = 0; col < LS; ++col) {
+                    double v = na * drow[col];
+                    if (v == 0.0) continue;
+                    if (yr >= 0) M[((size_t)k * S + yr) * LS + col] += v;   /* loss: -(-v) */
+                    if (yp >= 0) M[((size_t)k * S + yp) * LS + col] -= v;   /* production */
+                }
+            }
+        }
+    }
+    memcpy(LU, M, sizeof(double) * LS * LS);
+    int rc = lu_factor((int)LS, LU, piv);
+    if (rc == 0) {
+        lu_solve((int)LS, LU, piv, F, delta, 1);
+        for (int sweep = 0; sweep < ORA_REFINE_SWEEPS; ++sweep) {
+            for (size_t i = 0; i < LS; ++i) {
+                double s = F[i];
+                for (size_t j = 0; j < LS; ++j)
+                    s -= M[i * LS + j] * delta[j];
+                r[i] = s;
+            }
+            lu_solve((int)LS, LU, piv, r, c, 1);
+            for (size_t i = 0; i < LS; ++i)
+                delta[i] += c[i];
+        }
+    }
+    free(piv); free(r); free(dk); free(LU); free(M); free(A); free(F); free(kph); free(kf);
+    return rc;
+}

@@ -174,6 +174,13 @@ typedef struct {
 int ora_bdf_run(const ora_problem *p, const ora_policy *pol, const ora_bdf_config *cfg, double *n,
                 double h0, double t_end, int stop_at_steady, int max_steps, ora_bdf_info *info);
 
+/* Sec. 2.3.3: derivative of the direct-beam photolysis rates with respect to every density of the
+ * column: dk [L*Rph][L*S] (the diffuse field's derivative not included). */
+void ora_photolysis_dn(const ora_problem *p, const double *n, double *dk);
+/* The linearly implicit step with the photolysis rates differentiated too (every layer couples to
+ * the layers above it), one dense FP64 solve with iterative refinement: small columns only. */
+int ora_step_delta_coupled(const ora_problem *p, const double *n, double dt, double *delta);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,10 @@ def lib():
         l.ora_parcel_run.argtypes = [P, C.POINTER(Policy), C.c_int, C.c_int, C.c_double, _dp,
                                      C.POINTER(ParcelInfo), _ip]
         l.ora_parcel_run.restype = C.c_int
+        l.ora_photolysis_dn.argtypes = [P, _dp, _dp]
+        l.ora_photolysis_dn.restype = None
+        l.ora_step_delta_coupled.argtypes = [P, _dp, C.c_double, _dp]
+        l.ora_step_delta_coupled.restype = C.c_int
         l.ora_bdf_coeffs.argtypes = [C.c_int, _dp, _dp]
         l.ora_bdf_coeffs.restype = None
         l.ora_bdf_extrap.argtypes = [C.c_int, _dp, C.c_double, _dp]
@@ -341,6 +345,22 @@ class Oracle:
         lib().ora_pathways(C.byref(self.st), _d(np.ascontiguousarray(q_layer, np.float64)), int(src), _d(dist),
                            _i(pred_sp), _i(pred_edge), _i(lim_edge), _d(lim_w))
         return dict(dist=dist, pred_sp=pred_sp, pred_edge=pred_edge, lim_edge=lim_edge, lim_w=lim_w)
+
+    # -- photolysis rates in the Jacobian (Sec. 2.3.3) ----------------------------------
+    def photolysis_dn(self, n):
+        """d k_ph / d n of the direct beam: [L*Rph, L*S]."""
+        Rph = max(self.p.Rph, 1)
+        dk = np.zeros((self.L * Rph, self.L * self.S))
+        lib().ora_photolysis_dn(C.byref(self.st), _d(np.ascontiguousarray(n, np.float64)), _d(dk))
+        return dk[: self.L * self.p.Rph]
+
+    def step_delta_coupled(self, n, dt):
+        """The step with dk_ph/dn in the Jacobian (dense solve; small columns)."""
+        d = np.zeros((self.L, self.S))
+        rc = lib().ora_step_delta_coupled(C.byref(self.st), _d(np.ascontiguousarray(n, np.float64)), float(dt), _d(d))
+        if rc != 0:
+            raise ArithmeticError("singular coupled system")
+        return d
 
     # -- variable-order BDF (the DLSODES family, Sec. 2.1) -----------------------------
     def bdf_run(self, n, h0=1e-8, t_end=1e30, stop_at_steady=False, max_steps=1000, rtol=1e-3, qmax=5,

@@ -111,3 +111,90 @@ def test_scattering_off_is_the_direct_beam():
     base = o.photolysis(n)
     z = synth.with_scattering(p, diffuse=1).replace(sigma_s=np.zeros((p.S, p.W)))
     assert np.array_equal(Oracle(z).photolysis(n), base)
+
+
+# ------------------------------------------------ photolysis rates in the Jacobian
+
+def _relaxed_small():
+    p = synth.small_column(L=20)
+    o = Oracle(p)
+    n, info = o.run_to_steady(o.initial_state(), max_steps=300)
+    return p, o, n
+
+
+def _stoich(p):
+    nu = np.zeros((p.R, p.S))
+    for r in range(p.R):
+        for s in p.reac[r]:
+            if s >= 0:
+                nu[r, s] -= 1
+        for s in p.prod[r]:
+            if s >= 0:
+                nu[r, s] += 1
+    return nu
+
+
+def _full_matrix(p, o, n, dt):
+    """I/dt - J with the photolysis rates differentiated, assembled here from the block Jacobian
+    and the rate derivative (each pinned on its own)."""
+    from tests.helpers import full_matrix
+    A, lo, up = o.jacobian(n, dt)
+    M = full_matrix(A, lo, up)
+    dk = o.photolysis_dn(n)                       # [L*Rph, L*S]
+    nu = _stoich(p)
+    L, S = p.L, p.S
+    for r in np.flatnonzero(p.rtype == synth.RX_PHOTO):
+        q, a = p.prow[r], p.reac[r, 0]
+        for k in range(L):
+            g = n[k, a] * dk[k * p.Rph + q]       # d w_r,k / dn through k_ph
+            for y in np.flatnonzero(nu[r]):
+                M[k * S + y] -= nu[r, y] * g
+    return M
+
+
+def test_photolysis_rate_derivative_is_the_finite_difference():
+    p, o, n = _relaxed_small()
+    dk = o.photolysis_dn(n)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        v = rng.standard_normal(n.shape) * n
+        eps = 1e-6
+        fd = ((o.photolysis(n + eps * v) - o.photolysis(n - eps * v)) / (2 * eps)).ravel()
+        an = dk @ v.ravel()
+        assert np.max(np.abs(fd - an)) < 1e-7 * np.max(np.abs(an))
+    # a species absorbs only for the layers at and below it
+    k = p.L // 2
+    row = dk[k * p.Rph].reshape(p.L, p.S)
+    assert np.all(row[:k] == 0.0) and np.any(row[k + 1:] != 0.0)
+
+
+def test_coupled_jacobian_is_the_finite_difference_of_the_residual():
+    """(I/dt - M) v with the photolysis coupling equals the central difference of F along v with the
+    rates re-evaluated at the perturbed states."""
+    p, o, n = _relaxed_small()
+    dt = 1.0
+    M = _full_matrix(p, o, n, dt)
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal(n.shape) * n
+    eps = 1e-7
+    fd = (o.residual(n + eps * v) - o.residual(n - eps * v)).ravel() / (2 * eps)
+    Jv = (v.ravel() / dt) - M @ v.ravel()
+    scale = np.abs(fd) + np.abs(Jv) + 1e-300
+    big = scale > 1e-6 * scale.max()
+    assert np.max(np.abs(fd - Jv)[big] / scale[big]) < 1e-4
+
+
+def test_coupled_step_solves_the_full_system():
+    """The oracle's coupled step is the dense solve of the system assembled above (a numpy solve),
+    and differs from the lagged step by far more than the solve's error."""
+    p, o, n = _relaxed_small()
+    ngas = o.grid()[0]
+    s = np.maximum(n, 1e-20 * ngas[:, None])
+    dt = 1.0
+    M = _full_matrix(p, o, n, dt)
+    F = o.residual(n).ravel()
+    ref = np.linalg.solve(M, F).reshape(n.shape)
+    d = o.step_delta_coupled(n, dt)
+    assert np.max(np.abs(d - ref) / s) < 1e-8
+    lag = o.step_delta(n, dt)
+    assert np.max(np.abs(lag - d) / s) > 1e-4
