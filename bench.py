@@ -992,6 +992,25 @@ def radiation_object(live, calls=5, cpu=True):
             o["err_vs_oracle_max_rel"] = float(np.max(np.abs(g[m] - ref[m]) / ref[m]))
         out[name] = o
         col.close()
+    # one linear step of the mixed path with the direct beam's rates differentiated (photo_jacobian:
+    # FGMRES on the fully coupled operator, the block-tridiagonal factorization as preconditioner)
+    # beside the same step with lagged rates
+    prob = synth.full_column()
+    steps = {}
+    for flag in (0, 1):
+        col = xk.Column(prob, "mixed", photo_jacobian=flag)
+        col.set_mixing_ratios(prob.f0)
+        n = col.get_state(device=True)
+        col.step_delta(n, 1e-2)
+        torch.cuda.synchronize()
+        start.record(stream)
+        d, iters, res = col.step_delta(n, 1e-2)
+        end.record(stream)
+        torch.cuda.synchronize()
+        steps["coupled" if flag else "lagged"] = {"ms": start.elapsed_time(end), "fgmres_iters": int(iters),
+                                                  "residual": float(res)}
+        col.close()
+    out["step_photo_jacobian_594"] = dict(steps, dt_s=1e-2)
     return out
 
 

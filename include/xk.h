@@ -127,6 +127,13 @@ typedef struct {
                              gating of FGMRES iterations and of the FP64 route) in a CUDA graph once
                              and replay it, one graph launch per chunk; 0 launches every kernel from
                              the host.  Tracing (xk_profile) launches from the host either way. */
+    int photo_jacobian;   /* 1: the direct-beam photolysis rates are differentiated too (Sec. 2.3.3): the
+                             operator of FGMRES (mixed path; the refinement iterations of the FP64 path)
+                             includes dk_ph/dn, which couples every layer to the layers above it, so the
+                             step solves the fully linearised system while the block-tridiagonal
+                             factorization stays its preconditioner.  A direct FP64 solve
+                             (refine_max_iter = 0) ignores the coupling.  Not with the diffuse field
+                             (XK_EINVAL at xk_set_workspace).  0 (default): rates lagged. */
 } xk_config;
 
 typedef struct {

@@ -374,6 +374,10 @@ size_t layout(xk_ctx *c, char *base)
     t.sca_sp = b.take<int>(std::max(Ssca, 1));
     t.alpha_s = b.take<double>((size_t)L * std::max(W, 1));
     t.rt = b.take<double>(t.diffuse ? 4 * (size_t)L * W : 1);
+    t.photo_jac = (c->cfg.photo_jacobian && W > 0 && Rph > 0) ? 1 : 0;
+    t.pbeta = b.take<double>(t.photo_jac ? (size_t)L * W : 1);
+    t.pdJ = b.take<double>(t.photo_jac ? (size_t)L * W : 1);
+    t.pdk = b.take<double>(t.photo_jac ? (size_t)L * Rph : 1);
     t.P = b.take<double>(L); t.T = b.take<double>(L); t.Kzz = b.take<double>(L);
     t.g = c->g; t.mbar = c->mbar; t.alpha_T = c->alpha_T;
     t.ngas = b.take<double>(L); t.z = b.take<double>(L); t.dz = b.take<double>(L); t.dzi = b.take<double>(L);
@@ -894,6 +898,7 @@ int xk_config_init(xk_config *cfg)
     cfg->fp32_bcr = 1;
     cfg->wait_polls = 0;
     cfg->use_graphs = 1;
+    cfg->photo_jacobian = 0;
     return XK_OK;
 }
 
@@ -1082,6 +1087,8 @@ int xk_set_workspace(xk_ctx *c, void *dptr, size_t bytes)
     if (rc) return rc;
     if (!dptr || bytes < need) return fail(c, XK_ENOMEM, "workspace of %zu bytes, need %zu", bytes, need);
     if (((uintptr_t)dptr) & 255) return fail(c, XK_EINVAL, "workspace must be 256-byte aligned");
+    if (c->cfg.photo_jacobian && c->diffuse)
+        return fail(c, XK_EINVAL, "photo_jacobian differentiates the direct beam only: not with the diffuse field");
     cudaSetDevice(c->cfg.device);
     drop_graphs(c);
     c->ws = (char *)dptr;

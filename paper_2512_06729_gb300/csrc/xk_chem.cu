@@ -407,6 +407,100 @@ __global__ void k_jacobian(Col c, const double *n, const Ctl *ctl, double dt_ove
 // (d holds d(k_f prod n_reac)/dn and -d(k_r prod n_prod)/dn, so dw is the change of w_r);
 // then per species (J v)_i = sum_r nu_ir dw_r through the species-major stoichiometry, a warp
 // per row, plus the transport terms.
+// ---------------------------------------------------------------------------
+// photolysis rates in the Jacobian (cfg.photo_jacobian): the change of k_ph along the physical
+// direction v = s x of J v.  The direct beam J = J0 exp(-tau/mu) changes by -J dtau/mu, with dtau
+// the optical depth of the extinction change sum_i sigma_i v_i above the layer (half the layer's
+// own), so dk_ph = t_f sum_w dJ sigma dlambda; the rate w = k_ph n_A then changes by dk_ph n_A.
+// ---------------------------------------------------------------------------
+__global__ void k_photo_beta(Col c, const Ctl *ctl, const double *x, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0 = blockIdx.y * kExtLayers;
+    if (w >= c.W) return;
+    const int nk = min(kExtLayers, c.L - k0);
+    double sb[kExtLayers];
+#pragma unroll
+    for (int j = 0; j < kExtLayers; ++j) sb[j] = 0.0;
+    for (int i = 0; i < c.Sabs; ++i) {
+        const double sg = c.sig_abs[(long long)i * c.W + w];
+        const int y = c.abs_sp[i];
+#pragma unroll
+        for (int j = 0; j < kExtLayers; ++j)
+            if (j < nk) {
+                const long long e = (long long)(k0 + j) * c.S + y;
+                sb[j] += sg * c.s[e] * x[e];
+            }
+    }
+    for (int i = 0; i < c.Ssca; ++i) {
+        const double sg = c.sig_sca[(long long)i * c.W + w];
+        const int y = c.sca_sp[i];
+#pragma unroll
+        for (int j = 0; j < kExtLayers; ++j)
+            if (j < nk) {
+                const long long e = (long long)(k0 + j) * c.S + y;
+                sb[j] += sg * c.s[e] * x[e];
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < kExtLayers; ++j)
+        if (j < nk) c.pbeta[(long long)(k0 + j) * c.W + w] = sb[j];
+}
+
+// one warp per wavelength, the same run-and-scan layout as the direct beam
+__global__ void k_photo_dJ(Col c, const Ctl *ctl, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= c.W) return;
+    const int per = (c.L + 31) / 32;
+    const int i0 = lane * per, i1 = min(c.L, i0 + per);
+    double run = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const int k = c.L - 1 - i;
+        run += c.pbeta[(long long)k * c.W + w] * c.dz[k];
+    }
+    double incl = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    double above = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) above = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const int k = c.L - 1 - i;
+        const long long idx = (long long)k * c.W + w;
+        const double db = c.pbeta[idx] * c.dz[k];
+        c.pdJ[idx] = -c.Jw[idx] * (above + 0.5 * db) / c.mu;
+        above += db;
+    }
+}
+
+// dk_ph = t_f sum_w dJ sigma dlambda; one warp per (layer, reaction)
+__global__ void k_photo_dk(Col c, const Ctl *ctl, const int *skip)
+{
+    if ((ctl && ctl->finished) || (skip && *skip)) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= c.L * c.Rph) return;
+    const int k = warp / c.Rph, q = warp % c.Rph;
+    const double *dJ = c.pdJ + (long long)k * c.W;
+    const double *sg = c.sigma + (long long)q * c.W;
+    double s = 0.0;
+    for (int w = lane; w < c.W; w += 32) s += dJ[w] * sg[w] * c.dlam[w];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) c.pdk[(long long)k * c.Rph + q] = c.tf * s;
+}
+
+// the photolysis rate's extra change along v (0 unless photo_jacobian): dk_ph n_A
+__device__ __forceinline__ double photo_jv_term(const Col &c, int k, int r)
+{
+    if (!c.photo_jac || c.rtype[r] != XK_RX_PHOTO) return 0.0;
+    return c.pdk[(long long)k * c.Rph + c.prow[r]] * c.n[(long long)k * c.S + c.reac[3 * r]];
+}
+
 __global__ void k_jv_rates(Col c, const Ctl *ctl, const double *x, const int *skip)
 {
     if ((ctl && ctl->finished) || (skip && *skip)) return;
@@ -423,7 +517,7 @@ __global__ void k_jv_rates(Col c, const Ctl *ctl, const double *x, const int *sk
             const int j = c.prod[3 * r + q];
             if (j >= 0) acc += d[3 + q] * sk[j] * xk[j];
         }
-        c.dw[idx] = acc;
+        c.dw[idx] = acc + photo_jv_term(c, k, r);
     }
 }
 
@@ -455,7 +549,7 @@ __global__ void k_jv_layer(Col c, const Ctl *ctl, const double *x, double *y, co
                 const int b = c.prod[3 * r + q];
                 if (b >= 0) acc += d[3 + q] * sk[b] * xk[b];
             }
-            dws[r] = acc;
+            dws[r] = acc + photo_jv_term(c, k, r);
         }
         __syncthreads();
         for (int i = warp; i < S; i += nw) {
@@ -816,6 +910,13 @@ void launch_jv(const Col &c, const Ctl *ctl, const double *xs, double *ys, const
                cudaStream_t st)
 {
     if ((long long)c.L * c.S <= 0) return;
+    if (c.photo_jac) {
+        count_launches(3);
+        dim3 grid(nblocks(c.W, 128), (c.L + kExtLayers - 1) / kExtLayers);
+        k_photo_beta<<<grid, 128, 0, st>>>(c, ctl, xs, skip);
+        k_photo_dJ<<<nblocks((long long)c.W * 32, 128), 128, 0, st>>>(c, ctl, skip);
+        k_photo_dk<<<nblocks((long long)c.L * c.Rph * 32), kThreads, 0, st>>>(c, ctl, skip);
+    }
     const size_t sm = (size_t)std::max(c.R, 1) * sizeof(double);
     if (sm <= 160 * 1024) {
         static size_t attr = 0;

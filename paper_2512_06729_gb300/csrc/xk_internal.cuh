@@ -41,6 +41,10 @@ struct Col {
     // Ssca x W; the diffuse field (diffuse = 1) with lower-boundary albedo; alpha_s [L][W] the
     // scattering coefficient; rt [4][L][W] the two-stream recursion's coefficients
     int Ssca, diffuse;
+    // photolysis rates in the Jacobian (cfg.photo_jacobian): extinction along the J v direction
+    // [L][W], the beam's change [L][W] and the rates' change [L][Rph]
+    int photo_jac;
+    double *pbeta, *pdJ, *pdk;
     const double *sig_sca;
     const int *sca_sp;
     double albedo;

@@ -37,7 +37,7 @@ class Config(C.Structure):
         ("reuse_factorization", C.c_int), ("cluster_size", C.c_int), ("reuse_max_iters", C.c_int),
         ("twisted", C.c_int),
         ("fp64_panel", C.c_int), ("refine_max_iter", C.c_int), ("fp32_bcr", C.c_int),
-        ("wait_polls", C.c_longlong), ("use_graphs", C.c_int),
+        ("wait_polls", C.c_longlong), ("use_graphs", C.c_int), ("photo_jacobian", C.c_int),
     ]
 
 

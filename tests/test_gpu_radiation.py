@@ -84,3 +84,29 @@ def test_scattering_inputs_are_checked():
     sig[0, 0] = -1.0
     with pytest.raises(xk.XkError):
         xk.Column(neg.replace(sigma_s=sig), "fp64")
+
+
+def test_step_with_photolysis_jacobian_matches_coupled_oracle():
+    """With photo_jacobian the step solves the fully linearised system (dk_ph/dn couples every layer
+    to the layers above it) through FGMRES on the exact operator: it matches the oracle's dense
+    coupled step, and differs from the lagged step by far more than that tolerance."""
+    p = synth.small_column(L=20)
+    o = Oracle(p)
+    n, _ = o.run_to_steady(o.initial_state(), max_steps=300)
+    ngas = o.grid()[0]
+    s = np.maximum(n, 1e-20 * ngas[:, None])
+    dt = 1.0
+    ref = o.step_delta_coupled(n, dt)
+    lag = o.step_delta(n, dt)
+    assert np.max(np.abs(ref - lag) / s) > 1e-4
+    for prec in ("fp64", "mixed"):
+        c = xk.Column(p, prec, photo_jacobian=1)
+        d, iters, res = c.step_delta(dev(n), dt)
+        assert np.max(np.abs(cpu(d) - ref) / s) < 1e-6, (prec, iters, res)
+        c.close()
+
+
+def test_photolysis_jacobian_refuses_the_diffuse_field():
+    p = synth.with_scattering(synth.small_column(), diffuse=1)
+    with pytest.raises(xk.XkError):
+        xk.Column(p, "mixed", photo_jacobian=1)
