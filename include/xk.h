@@ -206,7 +206,8 @@ XK_API int xk_load_photo(xk_ctx *ctx, int W, int Rph, const int *prow, const dou
  * otherwise scattered (half back, half on) or absorbed; the lower boundary reflects the fraction
  * albedo (0..1) of the diffuse and direct light reaching it; nothing diffuse enters at the top.
  * J_up and J_down of a layer are the means of the fluxes through its two interfaces.  Photolysis
- * rates stay lagged (evaluated at the start of a step, not differentiated in the Jacobian).
+ * rates are evaluated at the start of a step; cfg.photo_jacobian adds the direct beam's derivative
+ * (not the diffuse field's, which it refuses) to the step's FGMRES operator.
  * XK_EINVAL on a grid mismatch, a negative or non-finite cross section, albedo outside [0, 1]. */
 XK_API int xk_load_scattering(xk_ctx *ctx, int W, const double *sigma_s, double albedo, int diffuse);
 
