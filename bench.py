@@ -528,6 +528,12 @@ def run_ours(args):
                                    "sample": f"one step on {SAMPLE_LAYERS} of {L} layers ({t:.1f} s), "
                                              f"scaled by {L}/{SAMPLE_LAYERS}"}}
             errs = err_vs_oracle(prob, tuning)
+            # the error leg runs the oracle's step on the whole 150-layer column once: its time is the
+            # unscaled single-core figure (rates, Jacobian, block solve and its refinement)
+            if errs and errs.get("oracle_step_s"):
+                cpu["single_core_full_column"] = {"value": 1.0 / errs["oracle_step_s"], "cores": 1,
+                                                  "sample": f"one step of the whole {L}-layer column "
+                                                            f"({errs['oracle_step_s']:.1f} s)"}
         if not args.no_steady:
             steady = steady_runs(prob, tuning, {"mixed": args.steady_cap, "fp64": args.steady_cap_fp64,
                                                 "mixed_from_equilibrium": args.steady_cap})
